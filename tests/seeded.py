@@ -1,0 +1,60 @@
+"""Seeded synthetic inputs shared by the oracle tests and the GPU parity tests.
+
+This module only draws random numbers; it holds none of the lattice Boltzmann arithmetic.  Callers
+turn the draws into populations themselves (f_i = w_i (1 + a * delta_i) with the oracle's weights).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.default_rng(np.random.SeedSequence(int(seed)))
+
+
+def relative_perturbation(seed: int, shape, amplitude: float) -> np.ndarray:
+    """Uniform draws in [-amplitude, amplitude] of the given shape (float64)."""
+    return rng(seed).uniform(-amplitude, amplitude, size=shape)
+
+
+def smooth_perturbation(seed: int, shape, amplitude: float, modes: int = 3) -> np.ndarray:
+    """A sum of a few random low Fourier modes along each lattice axis, per leading index, scaled to
+    peak |value| <= amplitude.  shape = (q, nz, ny, nx)."""
+    g = rng(seed)
+    q, nz, ny, nx = shape
+    z = np.arange(nz)[:, None, None]
+    y = np.arange(ny)[None, :, None]
+    x = np.arange(nx)[None, None, :]
+    out = np.zeros(shape)
+    for i in range(q):
+        acc = np.zeros((nz, ny, nx))
+        for _ in range(modes):
+            kx, ky, kz = g.integers(0, 3, size=3)
+            ph = g.uniform(0, 2 * np.pi, size=3)
+            acc += (np.cos(2 * np.pi * kx * x / nx + ph[0]) * np.cos(2 * np.pi * ky * y / ny + ph[1])
+                    * np.cos(2 * np.pi * kz * z / max(nz, 1) + ph[2]))
+        peak = np.abs(acc).max()
+        out[i] = acc * (amplitude / peak if peak > 0 else 0.0)
+    return out
+
+
+def block_maxima(seed: int, n: int, ties: int = 0, nans: int = 0, near=None) -> np.ndarray:
+    """float32 per-block maxima drawn log-uniformly in [1e-5, 1e-1], with `ties` entries repeated,
+    `nans` NaN entries and, if `near` = (T, count), `count` entries within 1 ulp-ish of T and T/2."""
+    g = rng(seed)
+    v = np.exp(g.uniform(np.log(1e-5), np.log(1e-1), size=n)).astype(np.float32)
+    if ties and n > 1:
+        src = g.integers(0, n, size=ties)
+        dst = g.integers(0, n, size=ties)
+        v[dst] = v[src]
+    if nans:
+        v[g.choice(n, size=min(nans, n), replace=False)] = np.nan
+    if near is not None:
+        T, count = near
+        idx = g.choice(n, size=min(count, n), replace=False)
+        for j, k in enumerate(idx):
+            base = np.float32(T if j % 2 == 0 else T / 2)
+            v[k] = np.nextafter(base, np.float32(np.inf if j % 4 < 2 else 0), dtype=np.float32)
+            if j % 3 == 0:
+                v[k] = base
+    return v
