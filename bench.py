@@ -1,0 +1,407 @@
+"""Benchmark of the fused LBM stream-collide + Knudsen sensor step (one JSON line on rank 0).
+
+Workload (default): D3Q19 BGK lid-driven cavity, 256^3 cells, FP32 populations in SoA layout,
+Re = 1000 (lid u = 0.1, tau = 3 u N / Re + 1/2 = 0.5768), the sensor evaluated on every step and
+reduced to 16^3 block maxima (4096 blocks), top-10 % block flags every step.  One bench step =
+one fused step kernel (stream, bounce-back, moments, equilibrium, sensor, tile max, collision) +
+the block-max / top-fraction flag kernels.  Data: synthetic (the cavity starts from rest).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+--impl reference times the FP64 CPU oracle on the host cores (the only CPU code this script runs,
+besides the cpu_baseline sample of the default arm).  Under torchrun (N > 1) every rank runs an
+independent replica of the workload on its own GPU (the path has no data-path collective here);
+time is the max over ranks and the value is the total over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (lattice q, n, dtype name, re, steps of the paper-scale run, block, flag rule)
+    "d3q19_256_fp32_re1000": dict(q=19, n=256, dtype="F32", re=1000.0, u=0.1, block=16,
+                                  rule="top", param=0.1, sensor_every=1),
+    "d2q9_128_fp64_re100": dict(q=9, n=128, dtype="F64", re=100.0, u=0.1, block=16,
+                                rule="threshold", param=None, sensor_every=100),
+}
+DEFAULT_WORKLOAD = "d3q19_256_fp32_re1000"
+BYTES_PER_ELEM = {"F64": 8, "F32": 4, "F16S": 2, "BF16S": 2}
+DTYPE_NAME = {"F64": "f64", "F32": "f32", "F16S": "f16(f-w)/f32", "BF16S": "bf16(f-w)/f32"}
+
+
+def tau_of(w):
+    # nu = u N / Re and nu = (tau - 1/2) / 3
+    return 3.0 * w["u"] * w["n"] / w["re"] + 0.5
+
+
+def threshold_of(w):
+    # four times the Couette-level sensor value of the mean lid shear, (4/3) tau u / N
+    return 4.0 * (4.0 / 3.0) * tau_of(w) * w["u"] / w["n"]
+
+
+def cells_of(w):
+    return w["n"] ** (3 if w["q"] == 19 else 2)
+
+
+def algorithmic_bytes_per_cell(w):
+    # read q populations + write q populations; the tile maxima are < 0.01 % of it
+    return 2 * w["q"] * BYTES_PER_ELEM[w["dtype"]]
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for fn in ("lbm_step.cuh", "lbm_traits.cuh"):
+        with open(os.path.join(ROOT, "paper_1507_06767_gb300", "csrc", fn), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload):
+    """DRAM bytes per launch of the fused step from the committed ncu summary, if it was taken on
+    the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", f"fused_step_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m_src = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    m_tr = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not m_src or not m_tr or m_src.group(1) != kernel_source_hash():
+        return None
+    return float(m_tr.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples of this process's GPU during the timed region."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.uuid and parts[0] != self.uuid:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_max(value, ws):
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------------- our arm
+def run_ours(args, w, ws, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_1507_06767_gb300 as L
+
+    torch.cuda.set_device(local)
+    dev_props = torch.cuda.get_device_properties(local)
+    uuid = getattr(dev_props, "uuid", None)
+    uuid = f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else uuid
+    q, n = w["q"], w["n"]
+    nz = n if q == 19 else 1
+    tau = tau_of(w)
+    dtype = getattr(L, "LBM_" + w["dtype"])
+    lat = L.Lattice(q, n, n, nz, tau, dtype=dtype, lid=(w["u"], 0.0))
+    h = lat.h
+    L.lbm_set_sensor_every(h, w["sensor_every"])
+    lat.block = w["block"]
+    nb = L.lbm_nblocks(h, w["block"])
+    flags_dev = torch.empty(nb, dtype=torch.int8, device="cuda")
+    param = w["param"] if w["rule"] == "top" else threshold_of(w)
+    cells = cells_of(w)
+
+    def one_step():
+        L.lbm_step(h, 1)
+        if w["sensor_every"] == 1 or L.lbm_steps_done(h) % w["sensor_every"] == 0:
+            if w["rule"] == "top":
+                L.lbm_flag_top_dev(h, param, flags_dev)
+            else:
+                L.lbm_flag_dev(h, param, flags_dev)
+
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    L.lbm_set_profiling(h, 1)
+    sampler = ClockSampler(uuid)
+    sampler.start()
+    time.sleep(0.3)
+    barrier(ws)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        one_step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    k_ms, k_n = L.lbm_kernel_time(h)
+    L.lbm_set_profiling(h, 0)
+    ms_max = reduce_max(ms, ws)
+    value = cells * args.steps * ws / (ms_max / 1e3) / 1e6
+
+    # ---- end to end through the C ABI with host buffers: the job's initial state goes up from
+    # pinned host memory, every step's flags come back to the host, the final state comes back
+    nbytes = L.lbm_population_bytes(h)
+    host_state = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    L.lbm_get_raw(h, host_state.data_ptr(), nbytes)
+    host_flags = torch.empty(nb, dtype=torch.int8, pin_memory=True)
+    flag_call = L.lbm_flag_top if w["rule"] == "top" else L.lbm_flag
+    e2e_steps = args.steps
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L.lbm_set_raw(h, host_state.data_ptr(), nbytes)
+    for k in range(e2e_steps):
+        L.lbm_step(h, 1)
+        if w["sensor_every"] == 1 or (k + 1) % w["sensor_every"] == 0:
+            flag_call(h, param, host_flags.data_ptr())
+    L.lbm_get_raw(h, host_state.data_ptr(), nbytes)
+    torch.cuda.synchronize()
+    e2e_s = reduce_max(time.perf_counter() - t0, ws)
+    barrier(ws)
+    n_flag_reads = e2e_steps // w["sensor_every"]
+    e2e = {"value": round(cells * e2e_steps * ws / e2e_s / 1e6, 1), "unit": "MLUPS",
+           "h2d_bytes_per_step": int(round(nbytes / e2e_steps)),
+           "d2h_bytes_per_step": int(round((nbytes + n_flag_reads * nb) / e2e_steps))}
+
+    peak, peak_kind = load_peaks()
+    per_launch_bytes = algorithmic_bytes_per_cell(w) * cells
+    avg_kernel_ms = k_ms / max(k_n, 1)
+    achieved = per_launch_bytes / (avg_kernel_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": recorded_traffic(args.workload),
+                "peak_kind": peak_kind, "kernel": "fused_step_kernel",
+                "kernel_ms": round(avg_kernel_ms, 5),
+                "algorithmic_bytes_per_launch": per_launch_bytes}
+    # launches of our kernels in the timed region: fused step every step, plus tile->block and
+    # flag kernels on sensor steps
+    n_sensor = args.steps // w["sensor_every"]
+    gpu_launches = args.steps + 2 * n_sensor
+
+    out = {
+        "metric": "fused stream-collide+sensor MLUPS",
+        "value": round(value, 1),
+        "unit": "MLUPS",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_max / args.steps, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": DTYPE_NAME[w["dtype"]],
+        "data": "synthetic (lid-driven cavity from rest)",
+        "config": {"workload": args.workload, "lattice": f"D{3 if q == 19 else 2}Q{q}",
+                   "cells": cells, "re": w["re"], "tau": round(tau, 6), "lid_u": w["u"],
+                   "sensor_every": w["sensor_every"], "block": w["block"], "blocks": nb,
+                   "flag_rule": w["rule"], "flag_param": param,
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "l2": (f"population buffers {2 * nbytes / 1e9:.2f} GB > 129 MB L2, no flush"
+                          if 2 * nbytes > 129e6 else "working set fits L2 (launch-bound case)")},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": gpu_launches,
+        "clocks": clocks,
+    }
+    lat.close()
+    return out
+
+
+# ------------------------------------------------------------------------------- oracle arm
+def oracle_sample(w, n_edge, steps, rng_note=""):
+    """Time `steps` oracle steps of the workload's cavity on an n_edge lattice (sensor + block max +
+    flags every sensor step).  Returns (MLUPS, seconds, threads)."""
+    import oracle as O
+
+    q = w["q"]
+    nz = n_edge if q == 19 else 1
+    o = O.Oracle(q, n_edge, n_edge, nz, tau_of(w), lid=(w["u"], 0.0, 0.0))
+    f = o.rest()
+    t0 = time.perf_counter()
+    for k in range(steps):
+        sensor = (k + 1) % w["sensor_every"] == 0
+        f, K, _, _ = o.step(f, sensor=sensor)
+        if sensor:
+            m = O.block_max(K, w["block"])
+            if w["rule"] == "top":
+                O.flags_top(m, w["param"])
+            else:
+                O.flags_threshold(m, threshold_of(w))
+    dt = time.perf_counter() - t0
+    cells = n_edge ** (3 if q == 19 else 2)
+    return cells * steps / dt / 1e6, dt, O.threads()
+
+
+def cpu_baseline_block(w):
+    """The oracle on the host cores on a bounded sample of the full workload."""
+    n = w["n"]
+    cells = cells_of(w)
+    # calibrate on a couple of steps, then size the sample to ~15 s
+    rate, _, _ = oracle_sample(w, min(n, 64 if w["q"] == 19 else 128), 2)
+    steps = max(2, min(200, int(15.0 * rate * 1e6 / cells)))
+    mlups, dt, threads = oracle_sample(w, n, steps)
+    return {"value": round(mlups, 3), "unit": "MLUPS", "cores": threads, "kind": "oracle",
+            "sample": f"{steps} steps of the full {n}^{3 if w['q'] == 19 else 2} lattice from rest, "
+                      f"FP64, sensor+block max+flags every sensor step ({dt:.1f} s)"}
+
+
+def run_reference(args, w):
+    cells_full = cells_of(w)
+    rate, _, _ = oracle_sample(w, 48 if w["q"] == 19 else 96, 2)
+    budget_s = 90.0
+    total_steps = args.steps + args.warmup
+    target_cells = rate * 1e6 * budget_s / max(total_steps, 1)
+    dim = 3 if w["q"] == 19 else 2
+    edge = int(max(8, min(w["n"], target_cells ** (1.0 / dim))))
+    if args.warmup:
+        oracle_sample(w, edge, args.warmup)
+    mlups, dt, threads = oracle_sample(w, edge, args.steps)
+    sample = (f"each step: one FP64 oracle step of a {edge}^{dim} cavity with the workload's tau and "
+              f"lid (full lattice {w['n']}^{dim} = {cells_full} cells), sensor + block max + flags")
+    return {
+        "metric": "fused stream-collide+sensor MLUPS", "value": round(mlups, 3), "unit": "MLUPS",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt * 1e3 / max(args.steps, 1), 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample": sample},
+        "impl": "reference",
+        "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": threads,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    w = WORKLOADS[args.workload]
+    ws, rank, local = dist_env()
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, w)), flush=True)
+        return
+
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    out = run_ours(args, w, ws, rank, local)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_block(w)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

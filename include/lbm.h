@@ -1,0 +1,244 @@
+/*
+ * lbm.h -- C ABI of the GB300 lattice Boltzmann library with the Knudsen refinement sensor.
+ *
+ * The library advances a lattice Boltzmann BGK simulation of a lid-driven cavity (D2Q9 or D3Q19)
+ * on one GPU and evaluates, fused into the same pass, the kinetic refinement sensor of
+ * arXiv 1507.06767 ("Local mesh refinement sensor for the lattice Boltzmann method"):
+ *
+ *     K(x) = (1/q) sum_i | f_i^neq(x) / f_i^eq(x) |,   f^neq = f - f^eq       (Sec. 3.2, Eq. sensor;
+ *                                                                             Sec. 3.3, Eq. kkn)
+ *
+ * reduced per block to a maximum and turned into refine / keep / coarsen flags (Sec. 3.4 maps the
+ * sensor to refinement levels; Sec. 5.2 regrids from it).
+ *
+ * Model (Sec. 2.2):
+ *   - discrete velocities D2Q9 / D3Q19 with the standard weights w_i, c_s^2 = 1/3;
+ *   - equilibrium f_i^eq = w_i rho (1 + c_i.u / c_s^2 + Q_i:uu / (2 c_s^4)),  Q_i = c_i c_i - c_s^2 I
+ *     (Eq. feq_i); rho = sum_i f_i, rho u = sum_i c_i f_i (Eqs. rho, u);
+ *   - one time step = streaming + BGK collision f* = f - (f - f^eq)/tau (Eq. bgklb and the
+ *     collide-and-stream split).  It is computed in pull form: each cell gathers f_i from x - c_i
+ *     of the previous post-collision field, then evaluates moments, equilibrium, sensor and
+ *     collision in registers and writes f* once;
+ *   - tau and the viscosity are linked by nu = c_s^2 (tau - 1/2) (Eq. nu_omega).
+ *
+ * Geometry: nodes at integer positions 0..n-1 on each axis; non-periodic axes have half-way
+ * bounce-back walls at -1/2 and n-1/2.  The wall at y = ny - 1/2 is the lid: it moves with the lid
+ * velocity (Sec. 4.1, moving bounce-back): a population pulled from a ghost node with y == ny gets
+ * f_i = f*_opp(i)(x) + 2 w_i (c_i . u_lid) / c_s^2 (wall density 1), every other wall ghost reflects
+ * f*_opp(i)(x) unchanged.  Edge and corner ghosts on the plane y == ny belong to the lid, which makes
+ * the total mass of the closed cavity exactly invariant.
+ *
+ * Sensor state: K is evaluated on the pre-collision populations of the step (after streaming and
+ * bounce-back) with their own rho and u.
+ *
+ * Memory layout of the populations (device): structure of arrays f[i][z][y][x], x fastest, i
+ * slowest, N = nx*ny*nz cells per population, no padding.  Storage types:
+ *   LBM_F64   double, stores f
+ *   LBM_F32   float,  stores f
+ *   LBM_F16S  IEEE half, stores f - w_i (shifted by the lattice weight); arithmetic in float
+ *   LBM_BF16S bfloat16,  stores f - w_i; arithmetic in float
+ * Arithmetic is double for LBM_F64 and float for the others.
+ *
+ * Blocks: the fused step records, on every sensor step, the maximum of K over base tiles of edge
+ * LBM_TILE (8x8 in 2-D, 8x8x8 in 3-D) anchored at the origin; partial tiles at the high ends hold the
+ * cells they have.  Block maxima for any block edge that is a multiple of LBM_TILE are exact maxima
+ * of tile maxima.  Block arrays are indexed ((bz * nby) + by) * nbx + bx, nb* = ceil(n* / block).
+ * A NaN anywhere in a block makes that block's maximum NaN.
+ *
+ * Flags (int8 per block): threshold rule: +1 refine if max > T, -1 coarsen if max < T/2, 0 keep;
+ * a NaN max refines.  Top-fraction rule: +1 for the ceil(frac * nblocks) largest maxima (ties by
+ * lower block index; NaN counts as +inf), 0 for the others.  Comparisons are made in double.
+ *
+ * Conventions for every call:
+ *   - return value: LBM_OK (0) or a negative LBM_E* status; calls returning a pointer return NULL on
+ *     failure.  lbm_last_error() / lbm_last_message() give the status and a text of the last
+ *     failing call on this host thread.  No C++ exception crosses the ABI.
+ *   - pointers named *_host are caller-owned host memory (pageable or pinned), copied synchronously;
+ *     pointers named *_dev are caller-owned device memory on the handle's device, used
+ *     asynchronously on the handle's stream.
+ *   - a handle is not thread-safe; different handles are independent.  Work is issued on the
+ *     handle's stream (lbm_set_stream; default: the legacy default stream) and is asynchronous
+ *     unless the call says it synchronises.
+ *   - a NULL handle gives LBM_EINVAL.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LBM_API __attribute__((visibility("default")))
+#else
+#define LBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Lattices (the value is q). */
+#define LBM_D2Q9 9
+#define LBM_D3Q19 19
+
+/* Population storage types. */
+#define LBM_F64 0
+#define LBM_F32 1
+#define LBM_F16S 2
+#define LBM_BF16S 3
+
+/* Status codes. */
+#define LBM_OK 0
+#define LBM_EINVAL (-1)   /* bad argument */
+#define LBM_ENOMEM (-2)   /* device allocation failed */
+#define LBM_ECUDA (-3)    /* a CUDA runtime call or kernel launch failed */
+#define LBM_ENUMERIC (-4) /* NaN or Inf found in the populations */
+#define LBM_ETIMEOUT (-5) /* a bounded device wait ran out */
+#define LBM_ENOTSUP (-6)  /* not supported in this build */
+#define LBM_ESTATE (-7)   /* call not allowed in the handle's current state */
+
+/* Periodic axis mask bits. */
+#define LBM_PERIODIC_X 1
+#define LBM_PERIODIC_Y 2
+#define LBM_PERIODIC_Z 4
+
+/* Edge of the base tile over which the fused step records the sensor maximum. */
+#define LBM_TILE 8
+
+/* Flag rules for lbm_flags_from_maxima. */
+#define LBM_FLAG_THRESHOLD 0
+#define LBM_FLAG_TOP 1
+
+typedef struct lbm_s lbm_t;
+
+/* Status of the last failing call on this host thread (LBM_OK if none), and its message. */
+LBM_API int lbm_last_error(void);
+LBM_API const char *lbm_last_message(void);
+/* Static text for a status code. */
+LBM_API const char *lbm_strerror(int status);
+/* ABI version of this library (major * 100 + minor). */
+LBM_API int lbm_version(void);
+
+/*
+ * Create a lattice of nx * ny * nz cells on the current CUDA device.  lattice is LBM_D2Q9 (nz must
+ * be 1) or LBM_D3Q19; tau > 1/2 is the lattice relaxation time (nu = (tau - 1/2)/3, Eq. nu_omega).
+ * Defaults: storage LBM_F32, lid velocity (0.1, 0, 0), no periodic axis, sensor on the last step of
+ * every lbm_step call, block edge 16, legacy default stream.  Device buffers are allocated on first
+ * use (or adopted with lbm_attach); the initial state is rest, f_i = w_i.  Returns NULL on a bad
+ * argument (LBM_EINVAL) or when the lattice exceeds 2^31 - 1 cells.
+ */
+LBM_API lbm_t *lbm_create(int lattice, int nx, int ny, int nz, double tau);
+/* Release the handle and the device memory it owns (never the buffers given to lbm_attach).
+ * Synchronises the handle's stream. */
+LBM_API int lbm_destroy(lbm_t *h);
+
+/* Storage type (LBM_F64 / LBM_F32 / LBM_F16S / LBM_BF16S).  Only before the population buffers
+ * exist (LBM_ESTATE afterwards). */
+LBM_API int lbm_set_dtype(lbm_t *h, int dtype);
+/* Lid velocity (ux, uz) of the wall at y = ny - 1/2 (the y component is 0 by construction). */
+LBM_API int lbm_set_lid(lbm_t *h, double ux, double uz);
+/* Periodic axes (mask of LBM_PERIODIC_*); a periodic y axis removes the lid and the y walls.  D2Q9
+ * ignores the z bit. */
+LBM_API int lbm_set_periodic(lbm_t *h, int axis_mask);
+/* Relaxation time tau > 1/2. */
+LBM_API int lbm_set_tau(lbm_t *h, double tau);
+/* CUDA stream (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream) for all later work. */
+LBM_API int lbm_set_stream(lbm_t *h, void *stream);
+/* Sensor schedule: k > 0 records the sensor on every step whose 1-based global index is a multiple
+ * of k; k == 0 records it on the last step of each lbm_step call. */
+LBM_API int lbm_set_sensor_every(lbm_t *h, int k);
+/* on != 0: sensor steps also write the per-cell K field (read with lbm_get_sensor_field). */
+LBM_API int lbm_set_sensor_field(lbm_t *h, int on);
+/* Block edge (a positive multiple of LBM_TILE) used by lbm_flag / lbm_flag_top and their _dev
+ * forms. */
+LBM_API int lbm_set_block(lbm_t *h, int block);
+/* on != 0: time every fused step kernel with CUDA events on the handle's stream (read with
+ * lbm_kernel_time); turning it on clears the counters. */
+LBM_API int lbm_set_profiling(lbm_t *h, int on);
+/* on != 0: lbm_step replays captured CUDA graphs for runs of steps (default on). */
+LBM_API int lbm_set_graphs(lbm_t *h, int on);
+
+/*
+ * Adopt caller-owned device buffers a and b (each >= lbm_population_bytes(h) bytes, 16-byte aligned)
+ * as the two population buffers; a is taken as the current post-collision state as it is.  The
+ * caller keeps ownership and must keep them alive until lbm_destroy.  Resets the step counter.
+ */
+LBM_API int lbm_attach(lbm_t *h, void *a_dev, void *b_dev, size_t bytes);
+/* Bytes of one population buffer for the current storage type (q * N * element size). */
+LBM_API size_t lbm_population_bytes(const lbm_t *h);
+/* Number of blocks for block edge `block` (0 if block is not a positive multiple of LBM_TILE). */
+LBM_API int lbm_nblocks(const lbm_t *h, int block);
+/* Number of completed steps. */
+LBM_API long long lbm_steps_done(const lbm_t *h);
+
+/* Reset the state to rest (f_i = w_i) and the step counter to 0. */
+LBM_API int lbm_reset(lbm_t *h);
+
+/*
+ * Advance n >= 0 time steps (asynchronous).  Each step is one launch of the fused kernel:
+ * pull-stream with moving-wall bounce-back -> rho, u -> f^eq -> [sensor K and its per-tile max on
+ * sensor steps] -> BGK collision -> store.  f^neq never leaves registers.
+ */
+LBM_API int lbm_step(lbm_t *h, int n);
+
+/*
+ * Block maxima of K of the most recent sensor step, for block edge `block` (positive multiple of
+ * LBM_TILE), written as lbm_nblocks(h, block) doubles.  _host synchronises; _dev is asynchronous.
+ * LBM_ESTATE if no sensor step has run since the last reset.
+ */
+LBM_API int lbm_sensor(lbm_t *h, int block, double *out_host);
+LBM_API int lbm_sensor_dev(lbm_t *h, int block, double *out_dev);
+
+/* Threshold flags (+1 / 0 / -1, see above) of the most recent sensor step for the handle's block
+ * edge (lbm_set_block).  _host synchronises; _dev is asynchronous. */
+LBM_API int lbm_flag(lbm_t *h, double threshold, int8_t *out_host);
+LBM_API int lbm_flag_dev(lbm_t *h, double threshold, int8_t *out_dev);
+/* Top-fraction flags: +1 for the ceil(frac * nblocks) largest block maxima, 0 otherwise
+ * (0 <= frac <= 1). */
+LBM_API int lbm_flag_top(lbm_t *h, double frac, int8_t *out_host);
+LBM_API int lbm_flag_top_dev(lbm_t *h, double frac, int8_t *out_dev);
+
+/*
+ * Flag builder on caller data: maxima_dev holds n block maxima of type maxima_dtype (LBM_F32:
+ * float, LBM_F64: double) on the current device; rule is LBM_FLAG_THRESHOLD (param = T) or
+ * LBM_FLAG_TOP (param = frac).  Writes n int8 flags to out_dev, asynchronously on `stream`.
+ */
+LBM_API int lbm_flags_from_maxima(const void *maxima_dev, int maxima_dtype, int n, int rule,
+                                  double param, int8_t *out_dev, void *stream);
+
+/* Populations as doubles, layout f[i][z][y][x] (q * N values).  get synchronises; set resets
+ * nothing but the state (the step counter is kept). */
+LBM_API int lbm_get_populations(lbm_t *h, double *out_host);
+LBM_API int lbm_set_populations(lbm_t *h, const double *in_host);
+/* Raw storage bytes (checkpointing): bytes must equal lbm_population_bytes(h). */
+LBM_API int lbm_get_raw(lbm_t *h, void *out_host, size_t bytes);
+LBM_API int lbm_set_raw(lbm_t *h, const void *in_host, size_t bytes);
+/* Density rho[N] and velocity u[3][N] (doubles) of the current state (moments of f*, which equal
+ * those of the pre-collision state of the last step).  Synchronises. */
+LBM_API int lbm_get_moments(lbm_t *h, double *rho_host, double *u_host);
+/* Per-cell K[N] of the most recent sensor step (needs lbm_set_sensor_field(h, 1) before it). */
+LBM_API int lbm_get_sensor_field(lbm_t *h, double *out_host);
+/*
+ * Total mass sum_x sum_i f_i and momentum sum_x sum_i c_i f_i (3 doubles) of the current state,
+ * summed in double on the device in a fixed order (deterministic).  Synchronises.  Returns
+ * LBM_ENUMERIC (with the sums still written) if a population is NaN or Inf.
+ */
+LBM_API int lbm_conservation(lbm_t *h, double *mass, double *mom3);
+
+/* Total time (ms) and count of the fused step kernels timed since profiling was turned on.
+ * Synchronises. */
+LBM_API int lbm_kernel_time(lbm_t *h, double *ms_total, long long *launches);
+
+/*
+ * Multi-level block batch (refinement ratio 2, level sub-cycling, f^neq rescaling at interfaces:
+ * Sec. 2.1 and Sec. 5.2 describe the cell-centred block-structured scheme).  Not provided in this
+ * version: returns LBM_ENOTSUP.
+ */
+typedef struct lbm_level_batch lbm_level_batch;
+LBM_API int lbm_blocks_step(lbm_t *h, const lbm_level_batch *batch);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

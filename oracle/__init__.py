@@ -47,7 +47,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
-               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
+               "-ffp-contract=off", "-fopenmp", "-o", tmp, _SRC, "-lm"]
         subprocess.check_call(cmd)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -77,7 +77,10 @@ def _load():
             lib.orc_block_max.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int, dp]
             lib.orc_conservation.argtypes = [pp, dp, dp, dp]
-            for name in ("orc_lattice", "orc_step", "orc_run", "orc_collide", "orc_stream_push",
+            lib.orc_step_cells.argtypes = [pp, dp, ctypes.c_longlong,
+                                           ctypes.POINTER(ctypes.c_longlong), dp, dp]
+            lib.orc_threads.argtypes = []
+            for name in ("orc_threads", "orc_step_cells", "orc_lattice", "orc_step", "orc_run", "orc_collide", "orc_stream_push",
                          "orc_sensor", "orc_equilibrium", "orc_block_max", "orc_conservation"):
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
@@ -96,6 +99,11 @@ def _check(status: int, what: str):
         raise FloatingPointError(f"{what}: an equilibrium population is not positive")
     if status != ORC_OK:
         raise ValueError(f"{what}: invalid arguments (status {status})")
+
+
+def threads() -> int:
+    """Threads the oracle's parallel loops use (OpenMP; OMP_NUM_THREADS caps it)."""
+    return int(_load().orc_threads())
 
 
 def lattice(q: int):
@@ -159,6 +167,18 @@ class Oracle:
         _check(_load().orc_step(ctypes.byref(self._p), _ptr(fs), _ptr(out), _ptr(K), _ptr(rho),
                                 _ptr(u)), "step")
         return out, K, rho, u
+
+    def step_cells(self, fs, cells):
+        """One pull step evaluated only at the cells with the given linear indices
+        ((z*ny + y)*nx + x).  Returns (f_out[len(cells), q], K[len(cells)])."""
+        fs = self._field(fs)
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        out = np.empty((len(cells), self.q))
+        K = np.empty(len(cells))
+        _check(_load().orc_step_cells(ctypes.byref(self._p), _ptr(fs), len(cells),
+                                      cells.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+                                      _ptr(out), _ptr(K)), "step_cells")
+        return out, K
 
     def run(self, fs, n, sensor_last=False):
         """n pull steps; returns (fs_n, K of the last step or None)."""
@@ -262,3 +282,28 @@ def flags_top(maxima, frac: float) -> np.ndarray:
     for _, idx in order[:k]:
         out[idx] = 1
     return out
+
+
+def flags_agree(flags, ref_maxima, rule: str, param: float, rel_tol: float):
+    """Compare flags computed elsewhere with the oracle's flags on its own maxima, ignoring blocks
+    whose oracle maximum lies within rel_tol (relative) of a decision boundary: T and T/2 for the
+    threshold rule, the k-th largest value for the top-fraction rule.  Returns (ok, n_compared,
+    n_excluded)."""
+    ref_maxima = np.asarray(ref_maxima, dtype=np.float64)
+    flags = np.asarray(flags)
+    if rule == "threshold":
+        ref = flags_threshold(ref_maxima, param)
+        bounds = [param, param / 2.0]
+    else:
+        ref = flags_top(ref_maxima, param)
+        k = top_count(param, len(ref_maxima))
+        vals = np.where(np.isnan(ref_maxima), np.inf, ref_maxima)
+        kth = np.sort(vals)[::-1][k - 1] if 0 < k <= len(vals) else None
+        bounds = [] if kth is None else [kth]
+    near = np.zeros(len(ref), dtype=bool)
+    for b in bounds:
+        if np.isfinite(b):
+            near |= np.abs(ref_maxima - b) <= rel_tol * abs(b)
+    keep = ~near
+    ok = bool(np.array_equal(flags[keep], ref[keep]))
+    return ok, int(keep.sum()), int(near.sum())

@@ -38,6 +38,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_MAXQ 19
 
@@ -247,6 +250,9 @@ int orc_step(const orc_params *p, const double *fs_in, double *fs_out, double *K
     if (check_params(p, &L) != ORC_OK) return ORC_EINVAL;
     size_t N = ncells(p);
     int status = ORC_OK;
+    /* cells are independent within a step, so the planes may be shared among threads; the
+     * arithmetic of each cell is unchanged */
+#pragma omp parallel for schedule(static) reduction(min : status)
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {
@@ -266,6 +272,48 @@ int orc_step(const orc_params *p, const double *fs_in, double *fs_out, double *K
                 for (int i = 0; i < L.q; ++i) fs_out[(size_t)i * N + c] = fout[i];
             }
     return status;
+}
+
+/*
+ * The same step evaluated only at the listed cells (linear indices (z*ny + y)*nx + x): f_out[k*q + i]
+ * receives the post-collision population i of cell cells[k], K[k] its sensor (K may be NULL).
+ * Used to check sampled outputs of lattices too large to step in full.
+ */
+int orc_step_cells(const orc_params *p, const double *fs_in, long long ncell, const long long *cells,
+                   double *f_out, double *K) {
+    lattice_t L;
+    if (check_params(p, &L) != ORC_OK || ncell < 0) return ORC_EINVAL;
+    const long long N = (long long)ncells(p);
+    int status = ORC_OK;
+    for (long long k = 0; k < ncell; ++k)
+        if (cells[k] < 0 || cells[k] >= N) return ORC_EINVAL;
+#pragma omp parallel for schedule(static) reduction(min : status)
+    for (long long k = 0; k < ncell; ++k) {
+        const long long c = cells[k];
+        const int x = (int)(c % p->nx);
+        const int y = (int)((c / p->nx) % p->ny);
+        const int z = (int)(c / ((long long)p->nx * p->ny));
+        double f[ORC_MAXQ], fout[ORC_MAXQ], rho, u[3];
+        pull_cell(&L, p, fs_in, x, y, z, f);
+        moments(&L, f, p->force, &rho, u);
+        if (K) {
+            double kk;
+            if (sensor_cell(&L, f, rho, u, &kk) != ORC_OK) status = ORC_EFEQ;
+            K[k] = kk;
+        }
+        collide_cell(&L, p, f, rho, u, fout);
+        for (int i = 0; i < L.q; ++i) f_out[k * L.q + i] = fout[i];
+    }
+    return status;
+}
+
+/* Number of threads the oracle's parallel loops use. */
+int orc_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /* Run n pull steps in place on fs (scratch holds the other buffer).  K (if given) receives the

@@ -1,0 +1,788 @@
+// C-ABI layer of the library (declared in include/lbm.h): handle state, argument checking, device
+// buffers, stream ordering, CUDA-graph replay of step runs, and the launches of the kernels in
+// lbm_step_*.cu / lbm_aux.cu.  Host code only; every step of the computation runs in the kernels.
+#include <cuda_runtime.h>
+#include <limits.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+using lbm::StepParams;
+
+namespace {
+
+thread_local int g_err = LBM_OK;
+thread_local char g_msg[512] = "";
+
+int fail(int code, const char *fmt, ...) {
+    g_err = code;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    if (e == cudaErrorMemoryAllocation)
+        return fail(LBM_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                        \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, (what)); \
+    } while (0)
+
+size_t elem_size(int dtype) {
+    switch (dtype) {
+        case LBM_F64: return 8;
+        case LBM_F32: return 4;
+        case LBM_F16S:
+        case LBM_BF16S: return 2;
+        default: return 0;
+    }
+}
+
+}  // namespace
+
+struct lbm_s {
+    int q = 0, dim = 0;
+    int nx = 0, ny = 0, nz = 0;
+    size_t N = 0;
+    double tau = 1.0;
+    double lid_x = 0.1, lid_z = 0.0;
+    int periodic = 0;
+    int dtype = LBM_F32;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sensor_every = 0;
+    int sensor_field = 0;
+    int block = 16;
+    int graphs = 1;
+
+    // population buffers
+    void *buf[2] = {nullptr, nullptr};
+    bool owned = false;
+    int cur = 0;
+
+    // sensor scratch: tile maxima of the last sensor step, block maxima, flags
+    int ntx = 0, nty = 0, ntz = 0;
+    size_t ntiles = 0;
+    void *tiles = nullptr;
+    void *blocks = nullptr;
+    double *blocks_f64 = nullptr;
+    int8_t *flags = nullptr;
+    void *kfield = nullptr;
+    double *cons_partial = nullptr;
+    double *cons_result = nullptr;
+    double *staging = nullptr;  // staging_cap >= max(N, 64) doubles, for host transfers in double
+    size_t staging_cap = 0;
+    bool scratch_ready = false;
+
+    long long t = 0;
+    bool have_sensor = false;
+    bool have_kfield = false;
+
+    // profiling
+    int profiling = 0;
+    std::vector<cudaEvent_t> events;
+    size_t events_used = 0;
+
+    // graph cache: runs of two plain steps, by starting buffer
+    cudaGraphExec_t pair_exec[2] = {nullptr, nullptr};
+    cudaStream_t pair_stream[2] = {nullptr, nullptr};
+    bool pair_valid = false;
+
+    int rtype() const { return dtype == LBM_F64 ? LBM_F64 : LBM_F32; }
+    size_t rsize() const { return dtype == LBM_F64 ? 8 : 4; }
+    size_t pop_bytes() const { return (size_t)q * N * elem_size(dtype); }
+};
+
+namespace {
+
+void drop_graphs(lbm_t *h) {
+    for (int k = 0; k < 2; ++k) {
+        if (h->pair_exec[k]) cudaGraphExecDestroy(h->pair_exec[k]);
+        h->pair_exec[k] = nullptr;
+    }
+    h->pair_valid = false;
+}
+
+StepParams params_of(const lbm_t *h) {
+    StepParams p;
+    p.nx = h->nx;
+    p.ny = h->ny;
+    p.nz = h->nz;
+    p.periodic = h->periodic;
+    p.ntx = h->ntx;
+    p.nty = h->nty;
+    p.ntz = h->ntz;
+    p.omega = 1.0 / h->tau;
+    p.lid_x = h->lid_x;
+    p.lid_z = h->lid_z;
+    return p;
+}
+
+int ensure_scratch(lbm_t *h) {
+    if (h->scratch_ready) return LBM_OK;
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    CK(cudaMalloc(&h->tiles, h->ntiles * h->rsize()), "cudaMalloc(tiles)");
+    CK(cudaMalloc(&h->blocks, h->ntiles * h->rsize()), "cudaMalloc(blocks)");
+    CK(cudaMalloc((void **)&h->blocks_f64, h->ntiles * sizeof(double)), "cudaMalloc(blocks_f64)");
+    CK(cudaMalloc((void **)&h->flags, h->ntiles), "cudaMalloc(flags)");
+    CK(cudaMalloc((void **)&h->cons_partial, lbm::CONS_PARTS * 5 * sizeof(double)),
+       "cudaMalloc(partial)");
+    CK(cudaMalloc((void **)&h->cons_result, 8 * sizeof(double)), "cudaMalloc(result)");
+    h->scratch_ready = true;
+    return LBM_OK;
+}
+
+int ensure_buffers(lbm_t *h) {
+    int st = ensure_scratch(h);
+    if (st != LBM_OK) return st;
+    if (h->buf[0]) return LBM_OK;
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    const size_t bytes = h->pop_bytes();
+    cudaError_t e = cudaMalloc(&h->buf[0], bytes);
+    if (e != cudaSuccess) {
+        h->buf[0] = nullptr;
+        return cuda_fail(e, "cudaMalloc(populations A)");
+    }
+    e = cudaMalloc(&h->buf[1], bytes);
+    if (e != cudaSuccess) {
+        cudaFree(h->buf[0]);
+        h->buf[0] = nullptr;
+        h->buf[1] = nullptr;
+        return cuda_fail(e, "cudaMalloc(populations B)");
+    }
+    h->owned = true;
+    h->cur = 0;
+    CK(lbm::init_rest(h->q, h->dtype, h->buf[0], h->N, h->stream), "init_rest");
+    h->t = 0;
+    h->have_sensor = false;
+    return LBM_OK;
+}
+
+int ensure_staging(lbm_t *h) {
+    if (h->staging) return LBM_OK;
+    const size_t cap = h->N > 64 ? h->N : 64;
+    CK(cudaMalloc((void **)&h->staging, cap * sizeof(double)), "cudaMalloc(staging)");
+    h->staging_cap = cap;
+    return LBM_OK;
+}
+
+int ensure_kfield(lbm_t *h) {
+    if (h->kfield) return LBM_OK;
+    CK(cudaMalloc(&h->kfield, h->N * h->rsize()), "cudaMalloc(k field)");
+    return LBM_OK;
+}
+
+cudaError_t launch_step(lbm_t *h, int src, int mode) {
+    const StepParams p = params_of(h);
+    void *tiles = mode ? h->tiles : nullptr;
+    void *kf = (mode == 2) ? h->kfield : nullptr;
+    if (h->q == LBM_D2Q9)
+        return lbm::step_d2q9(h->dtype, h->buf[src], h->buf[src ^ 1], p, mode, tiles, kf, h->stream);
+    return lbm::step_d3q19(h->dtype, h->buf[src], h->buf[src ^ 1], p, mode, tiles, kf, h->stream);
+}
+
+int timed_step(lbm_t *h, int mode) {
+    if (h->profiling) {
+        if (h->events_used + 2 > h->events.size()) {
+            for (int k = 0; k < 64; ++k) {
+                cudaEvent_t ev;
+                CK(cudaEventCreate(&ev), "cudaEventCreate");
+                h->events.push_back(ev);
+            }
+        }
+        CK(cudaEventRecord(h->events[h->events_used], h->stream), "cudaEventRecord");
+    }
+    CK(launch_step(h, h->cur, mode), "fused step launch");
+    if (h->profiling) {
+        CK(cudaEventRecord(h->events[h->events_used + 1], h->stream), "cudaEventRecord");
+        h->events_used += 2;
+    }
+    h->cur ^= 1;
+    h->t += 1;
+    if (mode) {
+        h->have_sensor = true;
+        h->have_kfield = (mode == 2);
+    }
+    return LBM_OK;
+}
+
+// Capture (once per stream and starting buffer) a graph of two plain steps: src -> other -> src.
+int pair_graph(lbm_t *h, int src, cudaGraphExec_t *out) {
+    if (h->pair_valid && h->pair_exec[src] && h->pair_stream[src] == h->stream) {
+        *out = h->pair_exec[src];
+        return LBM_OK;
+    }
+    if (h->pair_exec[src]) {
+        cudaGraphExecDestroy(h->pair_exec[src]);
+        h->pair_exec[src] = nullptr;
+    }
+    cudaStream_t cap;
+    CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "cudaStreamCreate");
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        const StepParams p = params_of(h);
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+            const int s = src ^ k;
+            if (h->q == LBM_D2Q9)
+                e = lbm::step_d2q9(h->dtype, h->buf[s], h->buf[s ^ 1], p, 0, nullptr, nullptr, cap);
+            else
+                e = lbm::step_d3q19(h->dtype, h->buf[s], h->buf[s ^ 1], p, 0, nullptr, nullptr, cap);
+        }
+        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->pair_exec[src], g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) {
+        h->pair_exec[src] = nullptr;
+        return cuda_fail(e, "graph capture");
+    }
+    h->pair_stream[src] = h->stream;
+    h->pair_valid = true;
+    *out = h->pair_exec[src];
+    return LBM_OK;
+}
+
+int check_block(const lbm_t *h, int block, int *nbx, int *nby, int *nbz, int *m, int *mz) {
+    if (block < LBM_TILE || block % LBM_TILE != 0)
+        return fail(LBM_EINVAL, "block edge %d is not a positive multiple of %d", block, LBM_TILE);
+    *m = block / LBM_TILE;
+    *mz = (h->dim == 3) ? *m : 1;
+    *nbx = (h->nx + block - 1) / block;
+    *nby = (h->ny + block - 1) / block;
+    *nbz = (h->dim == 3) ? (h->nz + block - 1) / block : 1;
+    return LBM_OK;
+}
+
+// Block maxima (native type) of the last sensor step into h->blocks; returns the block count.
+int reduce_blocks(lbm_t *h, int block, int *nb_out) {
+    if (!h->have_sensor) return fail(LBM_ESTATE, "no sensor step since the last reset");
+    int nbx, nby, nbz, m, mz;
+    int st = check_block(h, block, &nbx, &nby, &nbz, &m, &mz);
+    if (st != LBM_OK) return st;
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    CK(lbm::tiles_to_blocks(h->rtype(), h->tiles, h->ntx, h->nty, h->ntz, m, mz, h->blocks, nbx,
+                            nby, nbz, h->stream),
+       "tiles_to_blocks");
+    *nb_out = nbx * nby * nbz;
+    return LBM_OK;
+}
+
+int top_count(double frac, int n) {
+    double k = ceil(frac * (double)n);
+    if (k < 0) k = 0;
+    if (k > n) k = n;
+    return (int)k;
+}
+
+int sync(lbm_t *h) {
+    CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return LBM_OK;
+}
+
+#define CHECK_H(h)                                                 \
+    do {                                                           \
+        if (!(h)) return fail(LBM_EINVAL, "NULL handle");          \
+    } while (0)
+
+}  // namespace
+
+extern "C" {
+
+LBM_API int lbm_last_error(void) { return g_err; }
+LBM_API const char *lbm_last_message(void) { return g_msg; }
+LBM_API int lbm_version(void) { return 100; }
+
+LBM_API const char *lbm_strerror(int status) {
+    switch (status) {
+        case LBM_OK: return "ok";
+        case LBM_EINVAL: return "invalid argument";
+        case LBM_ENOMEM: return "out of device memory";
+        case LBM_ECUDA: return "CUDA error";
+        case LBM_ENUMERIC: return "non-finite populations";
+        case LBM_ETIMEOUT: return "device wait timed out";
+        case LBM_ENOTSUP: return "not supported";
+        case LBM_ESTATE: return "not allowed in the current state";
+        default: return "unknown status";
+    }
+}
+
+LBM_API lbm_t *lbm_create(int lattice, int nx, int ny, int nz, double tau) {
+    g_err = LBM_OK;
+    if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19) {
+        fail(LBM_EINVAL, "lattice must be LBM_D2Q9 (9) or LBM_D3Q19 (19), got %d", lattice);
+        return nullptr;
+    }
+    if (nx < 1 || ny < 1 || nz < 1) {
+        fail(LBM_EINVAL, "lattice dimensions must be >= 1 (got %d x %d x %d)", nx, ny, nz);
+        return nullptr;
+    }
+    if (lattice == LBM_D2Q9 && nz != 1) {
+        fail(LBM_EINVAL, "D2Q9 needs nz == 1 (got %d)", nz);
+        return nullptr;
+    }
+    if (!(tau > 0.5) || !isfinite(tau)) {
+        fail(LBM_EINVAL, "tau must be a finite value > 1/2 (got %g)", tau);
+        return nullptr;
+    }
+    const unsigned long long cells = (unsigned long long)nx * ny * nz;
+    if (cells > (unsigned long long)INT_MAX) {
+        fail(LBM_EINVAL, "lattice of %llu cells exceeds 2^31 - 1", cells);
+        return nullptr;
+    }
+    int dev = 0;
+    lbm_t *h = new (std::nothrow) lbm_t();
+    if (!h) {
+        fail(LBM_ENOMEM, "host allocation failed");
+        return nullptr;
+    }
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    h->q = lattice;
+    h->dim = (lattice == LBM_D2Q9) ? 2 : 3;
+    h->nx = nx;
+    h->ny = ny;
+    h->nz = nz;
+    h->N = (size_t)cells;
+    h->tau = tau;
+    h->device = dev;
+    h->ntx = (nx + LBM_TILE - 1) / LBM_TILE;
+    h->nty = (ny + LBM_TILE - 1) / LBM_TILE;
+    h->ntz = (h->dim == 3) ? (nz + LBM_TILE - 1) / LBM_TILE : 1;
+    h->ntiles = (size_t)h->ntx * h->nty * h->ntz;
+    return h;
+}
+
+LBM_API int lbm_destroy(lbm_t *h) {
+    CHECK_H(h);
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    drop_graphs(h);
+    for (cudaEvent_t ev : h->events) cudaEventDestroy(ev);
+    if (h->owned) {
+        cudaFree(h->buf[0]);
+        cudaFree(h->buf[1]);
+    }
+    cudaFree(h->tiles);
+    cudaFree(h->blocks);
+    cudaFree(h->blocks_f64);
+    cudaFree(h->flags);
+    cudaFree(h->kfield);
+    cudaFree(h->cons_partial);
+    cudaFree(h->cons_result);
+    cudaFree(h->staging);
+    delete h;
+    return LBM_OK;
+}
+
+LBM_API int lbm_set_dtype(lbm_t *h, int dtype) {
+    CHECK_H(h);
+    if (elem_size(dtype) == 0) return fail(LBM_EINVAL, "unknown storage type %d", dtype);
+    if (h->buf[0] || h->scratch_ready)
+        return fail(LBM_ESTATE, "storage type must be set before the buffers exist");
+    h->dtype = dtype;
+    return LBM_OK;
+}
+
+LBM_API int lbm_set_lid(lbm_t *h, double ux, double uz) {
+    CHECK_H(h);
+    if (!isfinite(ux) || !isfinite(uz)) return fail(LBM_EINVAL, "lid velocity must be finite");
+    if (h->dim == 2 && uz != 0.0) return fail(LBM_EINVAL, "D2Q9 lid has no z component");
+    h->lid_x = ux;
+    h->lid_z = uz;
+    drop_graphs(h);
+    return LBM_OK;
+}
+
+LBM_API int lbm_set_periodic(lbm_t *h, int axis_mask) {
+    CHECK_H(h);
+    if (axis_mask & ~7) return fail(LBM_EINVAL, "periodic mask %d has unknown bits", axis_mask);
+    h->periodic = (h->dim == 2) ? (axis_mask & 3) : axis_mask;
+    drop_graphs(h);
+    return LBM_OK;
+}
+
+LBM_API int lbm_set_tau(lbm_t *h, double tau) {
+    CHECK_H(h);
+    if (!(tau > 0.5) || !isfinite(tau)) return fail(LBM_EINVAL, "tau must be > 1/2 (got %g)", tau);
+    h->tau = tau;
+    drop_graphs(h);
+    return LBM_OK;
+}
+
+LBM_API int lbm_set_stream(lbm_t *h, void *stream) {
+    CHECK_H(h);
+    h->stream = static_cast<cudaStream_t>(stream);
+    return LBM_OK;
+}
+
+LBM_API int lbm_set_sensor_every(lbm_t *h, int k) {
+    CHECK_H(h);
+    if (k < 0) return fail(LBM_EINVAL, "sensor period must be >= 0 (got %d)", k);
+    h->sensor_every = k;
+    return LBM_OK;
+}
+
+LBM_API int lbm_set_sensor_field(lbm_t *h, int on) {
+    CHECK_H(h);
+    h->sensor_field = on ? 1 : 0;
+    return LBM_OK;
+}
+
+LBM_API int lbm_set_block(lbm_t *h, int block) {
+    CHECK_H(h);
+    if (block < LBM_TILE || block % LBM_TILE != 0)
+        return fail(LBM_EINVAL, "block edge %d is not a positive multiple of %d", block, LBM_TILE);
+    h->block = block;
+    return LBM_OK;
+}
+
+LBM_API int lbm_set_profiling(lbm_t *h, int on) {
+    CHECK_H(h);
+    h->profiling = on ? 1 : 0;
+    h->events_used = 0;
+    return LBM_OK;
+}
+
+LBM_API int lbm_set_graphs(lbm_t *h, int on) {
+    CHECK_H(h);
+    h->graphs = on ? 1 : 0;
+    return LBM_OK;
+}
+
+LBM_API int lbm_attach(lbm_t *h, void *a_dev, void *b_dev, size_t bytes) {
+    CHECK_H(h);
+    if (!a_dev || !b_dev || a_dev == b_dev) return fail(LBM_EINVAL, "need two distinct buffers");
+    if (bytes < h->pop_bytes())
+        return fail(LBM_EINVAL, "buffers of %zu bytes are smaller than %zu", bytes, h->pop_bytes());
+    if (((uintptr_t)a_dev | (uintptr_t)b_dev) & 15)
+        return fail(LBM_EINVAL, "buffers must be 16-byte aligned");
+    int st = ensure_scratch(h);
+    if (st != LBM_OK) return st;
+    drop_graphs(h);
+    if (h->owned) {
+        cudaStreamSynchronize(h->stream);
+        cudaFree(h->buf[0]);
+        cudaFree(h->buf[1]);
+    }
+    h->buf[0] = a_dev;
+    h->buf[1] = b_dev;
+    h->owned = false;
+    h->cur = 0;
+    h->t = 0;
+    h->have_sensor = false;
+    return LBM_OK;
+}
+
+LBM_API size_t lbm_population_bytes(const lbm_t *h) { return h ? h->pop_bytes() : 0; }
+
+LBM_API int lbm_nblocks(const lbm_t *h, int block) {
+    if (!h || block < LBM_TILE || block % LBM_TILE != 0) return 0;
+    int nbx = (h->nx + block - 1) / block, nby = (h->ny + block - 1) / block;
+    int nbz = (h->dim == 3) ? (h->nz + block - 1) / block : 1;
+    return nbx * nby * nbz;
+}
+
+LBM_API long long lbm_steps_done(const lbm_t *h) { return h ? h->t : -1; }
+
+LBM_API int lbm_reset(lbm_t *h) {
+    CHECK_H(h);
+    int st = ensure_buffers(h);
+    if (st != LBM_OK) return st;
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    CK(lbm::init_rest(h->q, h->dtype, h->buf[h->cur], h->N, h->stream), "init_rest");
+    h->t = 0;
+    h->have_sensor = false;
+    h->have_kfield = false;
+    return LBM_OK;
+}
+
+LBM_API int lbm_step(lbm_t *h, int n) {
+    CHECK_H(h);
+    if (n < 0) return fail(LBM_EINVAL, "step count must be >= 0 (got %d)", n);
+    int st = ensure_buffers(h);
+    if (st != LBM_OK) return st;
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    if (h->sensor_field) {
+        st = ensure_kfield(h);
+        if (st != LBM_OK) return st;
+    }
+    const int sensor_mode = h->sensor_field ? 2 : 1;
+    int s = 0;
+    while (s < n) {
+        const long long t1 = h->t + 1;
+        const bool sensor = (h->sensor_every > 0) ? (t1 % h->sensor_every == 0) : (s == n - 1);
+        if (!sensor && !h->profiling && h->graphs) {
+            // length of the run of plain steps starting here
+            int run = 0;
+            while (s + run < n) {
+                const long long tt = h->t + 1 + run;
+                const bool sen =
+                    (h->sensor_every > 0) ? (tt % h->sensor_every == 0) : (s + run == n - 1);
+                if (sen) break;
+                ++run;
+            }
+            if (run >= 4) {
+                cudaGraphExec_t ge;
+                st = pair_graph(h, h->cur, &ge);
+                if (st != LBM_OK) return st;
+                const int pairs = run / 2;
+                for (int k = 0; k < pairs; ++k) CK(cudaGraphLaunch(ge, h->stream), "cudaGraphLaunch");
+                h->t += 2LL * pairs;
+                s += 2 * pairs;
+                continue;
+            }
+        }
+        st = timed_step(h, sensor ? sensor_mode : 0);
+        if (st != LBM_OK) return st;
+        ++s;
+    }
+    return LBM_OK;
+}
+
+LBM_API int lbm_sensor(lbm_t *h, int block, double *out_host) {
+    CHECK_H(h);
+    if (!out_host) return fail(LBM_EINVAL, "NULL output");
+    int nb = 0;
+    int st = reduce_blocks(h, block, &nb);
+    if (st != LBM_OK) return st;
+    CK(lbm::to_f64(h->rtype(), h->blocks, h->blocks_f64, (size_t)nb, h->stream), "to_f64");
+    CK(cudaMemcpyAsync(out_host, h->blocks_f64, (size_t)nb * sizeof(double),
+                       cudaMemcpyDeviceToHost, h->stream),
+       "cudaMemcpyAsync");
+    return sync(h);
+}
+
+LBM_API int lbm_sensor_dev(lbm_t *h, int block, double *out_dev) {
+    CHECK_H(h);
+    if (!out_dev) return fail(LBM_EINVAL, "NULL output");
+    int nb = 0;
+    int st = reduce_blocks(h, block, &nb);
+    if (st != LBM_OK) return st;
+    CK(lbm::to_f64(h->rtype(), h->blocks, out_dev, (size_t)nb, h->stream), "to_f64");
+    return LBM_OK;
+}
+
+static int flag_common(lbm_t *h, int rule, double param, int8_t *out, bool host) {
+    CHECK_H(h);
+    if (!out) return fail(LBM_EINVAL, "NULL output");
+    if (rule == LBM_FLAG_THRESHOLD && !isfinite(param))
+        return fail(LBM_EINVAL, "threshold must be finite");
+    if (rule == LBM_FLAG_TOP && !(param >= 0.0 && param <= 1.0))
+        return fail(LBM_EINVAL, "fraction must be in [0, 1] (got %g)", param);
+    int nb = 0;
+    int st = reduce_blocks(h, h->block, &nb);
+    if (st != LBM_OK) return st;
+    int8_t *dst = host ? h->flags : out;
+    if (rule == LBM_FLAG_THRESHOLD)
+        CK(lbm::flags_threshold(h->rtype(), h->blocks, nb, param, dst, h->stream), "flags");
+    else
+        CK(lbm::flags_top(h->rtype(), h->blocks, nb, top_count(param, nb), dst, h->stream), "flags");
+    if (host) {
+        CK(cudaMemcpyAsync(out, h->flags, (size_t)nb, cudaMemcpyDeviceToHost, h->stream),
+           "cudaMemcpyAsync");
+        return sync(h);
+    }
+    return LBM_OK;
+}
+
+LBM_API int lbm_flag(lbm_t *h, double threshold, int8_t *out_host) {
+    return flag_common(h, LBM_FLAG_THRESHOLD, threshold, out_host, true);
+}
+LBM_API int lbm_flag_dev(lbm_t *h, double threshold, int8_t *out_dev) {
+    return flag_common(h, LBM_FLAG_THRESHOLD, threshold, out_dev, false);
+}
+LBM_API int lbm_flag_top(lbm_t *h, double frac, int8_t *out_host) {
+    return flag_common(h, LBM_FLAG_TOP, frac, out_host, true);
+}
+LBM_API int lbm_flag_top_dev(lbm_t *h, double frac, int8_t *out_dev) {
+    return flag_common(h, LBM_FLAG_TOP, frac, out_dev, false);
+}
+
+LBM_API int lbm_flags_from_maxima(const void *maxima_dev, int maxima_dtype, int n, int rule,
+                                  double param, int8_t *out_dev, void *stream) {
+    g_err = LBM_OK;
+    if (n < 0) return fail(LBM_EINVAL, "n must be >= 0");
+    if (n > 0 && (!maxima_dev || !out_dev)) return fail(LBM_EINVAL, "NULL pointer");
+    if (maxima_dtype != LBM_F32 && maxima_dtype != LBM_F64)
+        return fail(LBM_EINVAL, "maxima type must be LBM_F32 or LBM_F64");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (rule == LBM_FLAG_THRESHOLD) {
+        if (!isfinite(param)) return fail(LBM_EINVAL, "threshold must be finite");
+        if (n == 0) return LBM_OK;
+        CK(lbm::flags_threshold(maxima_dtype, maxima_dev, n, param, out_dev, s), "flags");
+    } else if (rule == LBM_FLAG_TOP) {
+        if (!(param >= 0.0 && param <= 1.0)) return fail(LBM_EINVAL, "fraction must be in [0, 1]");
+        if (n == 0) return LBM_OK;
+        CK(lbm::flags_top(maxima_dtype, maxima_dev, n, top_count(param, n), out_dev, s), "flags");
+    } else {
+        return fail(LBM_EINVAL, "unknown flag rule %d", rule);
+    }
+    return LBM_OK;
+}
+
+LBM_API int lbm_get_populations(lbm_t *h, double *out_host) {
+    CHECK_H(h);
+    if (!out_host) return fail(LBM_EINVAL, "NULL output");
+    int st = ensure_buffers(h);
+    if (st == LBM_OK) st = ensure_staging(h);
+    if (st != LBM_OK) return st;
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    const size_t es = elem_size(h->dtype);
+    for (int i = 0; i < h->q; ++i) {
+        const char *src = static_cast<const char *>(h->buf[h->cur]) + (size_t)i * h->N * es;
+        CK(lbm::storage_to_f64(h->q, h->dtype, i, 1, src, h->staging, h->N, h->stream), "to_f64");
+        CK(cudaMemcpyAsync(out_host + (size_t)i * h->N, h->staging, h->N * sizeof(double),
+                           cudaMemcpyDeviceToHost, h->stream),
+           "cudaMemcpyAsync");
+    }
+    return sync(h);
+}
+
+LBM_API int lbm_set_populations(lbm_t *h, const double *in_host) {
+    CHECK_H(h);
+    if (!in_host) return fail(LBM_EINVAL, "NULL input");
+    int st = ensure_buffers(h);
+    if (st == LBM_OK) st = ensure_staging(h);
+    if (st != LBM_OK) return st;
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    const size_t es = elem_size(h->dtype);
+    for (int i = 0; i < h->q; ++i) {
+        char *dst = static_cast<char *>(h->buf[h->cur]) + (size_t)i * h->N * es;
+        CK(cudaMemcpyAsync(h->staging, in_host + (size_t)i * h->N, h->N * sizeof(double),
+                           cudaMemcpyHostToDevice, h->stream),
+           "cudaMemcpyAsync");
+        CK(lbm::f64_to_storage(h->q, h->dtype, i, 1, h->staging, dst, h->N, h->stream), "from_f64");
+    }
+    return sync(h);
+}
+
+LBM_API int lbm_get_raw(lbm_t *h, void *out_host, size_t bytes) {
+    CHECK_H(h);
+    if (!out_host) return fail(LBM_EINVAL, "NULL output");
+    if (bytes != h->pop_bytes())
+        return fail(LBM_EINVAL, "raw size %zu != population bytes %zu", bytes, h->pop_bytes());
+    int st = ensure_buffers(h);
+    if (st != LBM_OK) return st;
+    CK(cudaMemcpyAsync(out_host, h->buf[h->cur], bytes, cudaMemcpyDeviceToHost, h->stream),
+       "cudaMemcpyAsync");
+    return sync(h);
+}
+
+LBM_API int lbm_set_raw(lbm_t *h, const void *in_host, size_t bytes) {
+    CHECK_H(h);
+    if (!in_host) return fail(LBM_EINVAL, "NULL input");
+    if (bytes != h->pop_bytes())
+        return fail(LBM_EINVAL, "raw size %zu != population bytes %zu", bytes, h->pop_bytes());
+    int st = ensure_buffers(h);
+    if (st != LBM_OK) return st;
+    CK(cudaMemcpyAsync(h->buf[h->cur], in_host, bytes, cudaMemcpyHostToDevice, h->stream),
+       "cudaMemcpyAsync");
+    return sync(h);
+}
+
+LBM_API int lbm_get_moments(lbm_t *h, double *rho_host, double *u_host) {
+    CHECK_H(h);
+    if (!rho_host || !u_host) return fail(LBM_EINVAL, "NULL output");
+    int st = ensure_buffers(h);
+    if (st == LBM_OK) st = ensure_staging(h);
+    if (st != LBM_OK) return st;
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    // staging holds staging_cap doubles: cells go in chunks of staging_cap / 4 (rho + 3 velocity
+    // components)
+    const size_t chunk = h->staging_cap / 4;
+    for (size_t c0 = 0; c0 < h->N; c0 += chunk) {
+        const size_t nc = (h->N - c0 < chunk) ? h->N - c0 : chunk;
+        double *rho_d = h->staging;
+        double *u_d = h->staging + nc;
+        CK(lbm::moments_f64(h->q, h->dtype, h->buf[h->cur], h->N, c0, nc, rho_d, u_d, h->stream),
+           "moments");
+        CK(cudaMemcpyAsync(rho_host + c0, rho_d, nc * sizeof(double), cudaMemcpyDeviceToHost,
+                           h->stream),
+           "cudaMemcpyAsync");
+        for (int a = 0; a < 3; ++a)
+            CK(cudaMemcpyAsync(u_host + (size_t)a * h->N + c0, u_d + (size_t)a * nc,
+                               nc * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+               "cudaMemcpyAsync");
+        st = sync(h);
+        if (st != LBM_OK) return st;
+    }
+    return LBM_OK;
+}
+
+LBM_API int lbm_get_sensor_field(lbm_t *h, double *out_host) {
+    CHECK_H(h);
+    if (!out_host) return fail(LBM_EINVAL, "NULL output");
+    if (!h->have_kfield || !h->kfield)
+        return fail(LBM_ESTATE, "no per-cell sensor recorded (lbm_set_sensor_field before stepping)");
+    int st = ensure_staging(h);
+    if (st != LBM_OK) return st;
+    CK(lbm::to_f64(h->rtype(), h->kfield, h->staging, h->N, h->stream), "to_f64");
+    CK(cudaMemcpyAsync(out_host, h->staging, h->N * sizeof(double), cudaMemcpyDeviceToHost,
+                       h->stream),
+       "cudaMemcpyAsync");
+    return sync(h);
+}
+
+LBM_API int lbm_conservation(lbm_t *h, double *mass, double *mom3) {
+    CHECK_H(h);
+    if (!mass || !mom3) return fail(LBM_EINVAL, "NULL output");
+    int st = ensure_buffers(h);
+    if (st != LBM_OK) return st;
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    CK(lbm::conservation(h->q, h->dtype, h->buf[h->cur], h->N, h->cons_partial, h->cons_result,
+                         h->stream),
+       "conservation");
+    double r[5];
+    CK(cudaMemcpyAsync(r, h->cons_result, sizeof(r), cudaMemcpyDeviceToHost, h->stream),
+       "cudaMemcpyAsync");
+    st = sync(h);
+    if (st != LBM_OK) return st;
+    *mass = r[0];
+    mom3[0] = r[1];
+    mom3[1] = r[2];
+    mom3[2] = r[3];
+    if (r[4] != 0.0 || !isfinite(r[0]))
+        return fail(LBM_ENUMERIC, "%.0f non-finite populations", r[4]);
+    return LBM_OK;
+}
+
+LBM_API int lbm_kernel_time(lbm_t *h, double *ms_total, long long *launches) {
+    CHECK_H(h);
+    if (!ms_total || !launches) return fail(LBM_EINVAL, "NULL output");
+    int st = sync(h);
+    if (st != LBM_OK) return st;
+    double total = 0.0;
+    for (size_t k = 0; k + 1 < h->events_used; k += 2) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, h->events[k], h->events[k + 1]), "cudaEventElapsedTime");
+        total += ms;
+    }
+    *ms_total = total;
+    *launches = (long long)(h->events_used / 2);
+    h->events_used = 0;
+    return LBM_OK;
+}
+
+LBM_API int lbm_blocks_step(lbm_t *h, const lbm_level_batch *batch) {
+    (void)batch;
+    CHECK_H(h);
+    return fail(LBM_ENOTSUP, "multi-level block batches are not provided in this version");
+}
+
+}  // extern "C"

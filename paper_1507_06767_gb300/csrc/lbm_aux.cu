@@ -1,0 +1,404 @@
+// Helper kernels around the fused step: population conversion, moments, FP64 conservation sums,
+// tile-to-block sensor maxima and the refine / coarsen flag builders.
+#include <math.h>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+namespace {
+
+constexpr int EW_THREADS = 256;
+
+inline dim3 ew_grid(size_t N, int q) {
+    size_t b = (N + EW_THREADS - 1) / EW_THREADS;
+    if (b > 4096) b = 4096;
+    if (b < 1) b = 1;
+    return dim3((unsigned)b, (unsigned)q, 1);
+}
+
+template <class L, int DT>
+__device__ __forceinline__ double stored_to_f64(typename Storage<DT>::T v, int i) {
+    double d = (double)Storage<DT>::to_r(v);
+    return Storage<DT>::SHIFTED ? weight<L, double>(i) + d : d;
+}
+
+// direction tables in device-readable form for kernels indexed by a runtime direction
+template <class L>
+__device__ __forceinline__ double w_of(int i) {
+    double w = 0;
+#pragma unroll
+    for (int j = 0; j < L::Q; ++j)
+        if (j == i) w = weight<L, double>(j);
+    return w;
+}
+
+template <class L, int DT>
+__global__ void k_init_rest(typename Storage<DT>::T *f, size_t N) {
+    const int i = blockIdx.y;
+    const double w = w_of<L>(i);
+    const auto v = Storage<DT>::SHIFTED ? Storage<DT>::from_r(0) : Storage<DT>::from_r(
+        (typename Storage<DT>::R)w);
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < N;
+         c += (size_t)gridDim.x * blockDim.x)
+        f[(size_t)i * N + c] = v;
+}
+
+template <class T>
+__device__ __forceinline__ T from_double(double v);
+template <>
+__device__ __forceinline__ double from_double<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float from_double<float>(double v) { return (float)v; }
+template <>
+__device__ __forceinline__ __half from_double<__half>(double v) { return __double2half(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_double<__nv_bfloat16>(double v) {
+    return __double2bfloat16(v);
+}
+
+// in / out point at population i0; blockIdx.y selects population i0 + blockIdx.y
+template <class L, int DT>
+__global__ void k_from_f64(const double *in, typename Storage<DT>::T *out, size_t N, int i0) {
+    using T = typename Storage<DT>::T;
+    const int j = blockIdx.y;
+    const double w = w_of<L>(i0 + j);
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < N;
+         c += (size_t)gridDim.x * blockDim.x) {
+        double v = in[(size_t)j * N + c];
+        if (Storage<DT>::SHIFTED) v -= w;
+        out[(size_t)j * N + c] = from_double<T>(v);
+    }
+}
+
+template <class L, int DT>
+__global__ void k_to_f64(const typename Storage<DT>::T *in, double *out, size_t N, int i0) {
+    const int j = blockIdx.y;
+    const double w = w_of<L>(i0 + j);
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < N;
+         c += (size_t)gridDim.x * blockDim.x) {
+        double d = (double)Storage<DT>::to_r(in[(size_t)j * N + c]);
+        out[(size_t)j * N + c] = Storage<DT>::SHIFTED ? w + d : d;
+    }
+}
+
+// moments of cells [c0, c0 + nc): rho[nc], u[3][nc]
+template <class L, int DT>
+__global__ void k_moments(const typename Storage<DT>::T *f, size_t N, size_t c0, size_t nc,
+                          double *rho, double *u) {
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < nc;
+         k += (size_t)gridDim.x * blockDim.x) {
+        const size_t c = c0 + k;
+        double r = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            const double v = stored_to_f64<L, DT>(f[(size_t)i * N + c], i);
+            r += v;
+            jx += L::cx(i) * v;
+            jy += L::cy(i) * v;
+            jz += L::cz(i) * v;
+        }
+        rho[k] = r;
+        u[k] = jx / r;
+        u[nc + k] = jy / r;
+        u[2 * nc + k] = jz / r;
+    }
+}
+
+constexpr int CONS_THREADS = 256;
+
+template <class L, int DT>
+__global__ void __launch_bounds__(CONS_THREADS)
+    k_cons_partial(const typename Storage<DT>::T *f, size_t N, double *partial) {
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < N;
+         c += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            const double v = stored_to_f64<L, DT>(f[(size_t)i * N + c], i);
+            if (!isfinite(v)) acc[4] += 1.0;
+            acc[0] += v;
+            acc[1] += L::cx(i) * v;
+            acc[2] += L::cy(i) * v;
+            acc[3] += L::cz(i) * v;
+        }
+    }
+    __shared__ double sh[5][CONS_THREADS];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int s = CONS_THREADS / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 5; ++k) partial[(size_t)blockIdx.x * 5 + k] = sh[k][0];
+}
+
+__global__ void __launch_bounds__(1024) k_cons_final(const double *partial, int nparts,
+                                                     double *result) {
+    __shared__ double sh[5][1024];
+    for (int k = 0; k < 5; ++k)
+        sh[k][threadIdx.x] = (threadIdx.x < nparts) ? partial[(size_t)threadIdx.x * 5 + k] : 0.0;
+    __syncthreads();
+    for (int s = 512; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x < 5) result[threadIdx.x] = sh[threadIdx.x][0];
+}
+
+template <class R>
+__global__ void k_tiles_to_blocks(const R *tiles, int ntx, int nty, int ntz, int m, int mz,
+                                  R *blocks, int nbx, int nby, int nbz) {
+    using B = typename Bits<R>::type;
+    const long long nb = (long long)nbx * nby * nbz;
+    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
+         b += (long long)gridDim.x * blockDim.x) {
+        const int bx = (int)(b % nbx);
+        const int by = (int)((b / nbx) % nby);
+        const int bz = (int)(b / ((long long)nbx * nby));
+        B mx = 0;
+        for (int tz = bz * mz; tz < min(bz * mz + mz, ntz); ++tz)
+            for (int ty = by * m; ty < min(by * m + m, nty); ++ty)
+                for (int tx = bx * m; tx < min(bx * m + m, ntx); ++tx) {
+                    const B v = max_bits(tiles[((size_t)tz * nty + ty) * ntx + tx]);
+                    mx = v > mx ? v : mx;
+                }
+        blocks[b] = from_bits(mx, R(0));
+    }
+}
+
+template <class R>
+__global__ void k_to_f64_plain(const R *in, double *out, size_t n) {
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x)
+        out[k] = (double)in[k];
+}
+
+template <class R>
+__global__ void k_flags_threshold(const R *m, int n, double T, double half_T, int8_t *out) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const double v = (double)m[k];
+        out[k] = (isnan(v) || v > T) ? int8_t(1) : (v < half_T ? int8_t(-1) : int8_t(0));
+    }
+}
+
+// Order-preserving unsigned keys; NaN maps to the key of +inf.
+__device__ __forceinline__ uint32_t sort_key(float v) {
+    if (isnan(v)) v = INFINITY;
+    const uint32_t b = __float_as_uint(v);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ unsigned long long sort_key(double v) {
+    if (isnan(v)) v = INFINITY;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+
+constexpr int TOP_THREADS = 1024;
+
+// Single-CTA radix select of the k-th largest key (1 <= k <= n), then flags: keys above it refine,
+// keys equal to it refine in block-index order until k blocks are taken.
+template <class R, class K>
+__global__ void __launch_bounds__(TOP_THREADS) k_flags_top(const R *m, int n, int k, int8_t *out) {
+    __shared__ unsigned hist[256];
+    __shared__ int s_digit, s_remaining;
+    __shared__ int scan[TOP_THREADS];
+    const int tid = threadIdx.x;
+    K prefix = 0, mask = 0;
+    int remaining = k;
+    for (int shift = 8 * (int)sizeof(K) - 8; shift >= 0; shift -= 8) {
+        for (int b = tid; b < 256; b += blockDim.x) hist[b] = 0;
+        __syncthreads();
+        for (int e = tid; e < n; e += blockDim.x) {
+            const K key = sort_key(m[e]);
+            if ((key & mask) == prefix) atomicAdd(&hist[(unsigned)(key >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (tid < 32) {
+            const int hi = 255 - 8 * tid;  // this lane's bins: hi, hi-1, ..., hi-7
+            unsigned sum8 = 0;
+            for (int j = 0; j < 8; ++j) sum8 += hist[hi - j];
+            unsigned incl = sum8;
+            for (int off = 1; off < 32; off <<= 1) {
+                const unsigned o = __shfl_up_sync(0xffffffffu, incl, off);
+                if (tid >= off) incl += o;
+            }
+            const unsigned ballot = __ballot_sync(0xffffffffu, incl >= (unsigned)remaining);
+            const int first = __ffs(ballot) - 1;
+            if (tid == first) {
+                unsigned c = incl - sum8;
+                for (int j = 0; j < 8; ++j) {
+                    const unsigned h = hist[hi - j];
+                    if (c + h >= (unsigned)remaining) {
+                        s_digit = hi - j;
+                        s_remaining = remaining - (int)c;
+                        break;
+                    }
+                    c += h;
+                }
+            }
+        }
+        __syncthreads();
+        prefix |= (K)s_digit << shift;
+        mask |= (K)0xFF << shift;
+        remaining = s_remaining;
+        __syncthreads();
+    }
+    // prefix is the k-th largest key; `remaining` equal keys are taken, lowest indices first
+    const int chunk = (n + TOP_THREADS - 1) / TOP_THREADS;
+    const int start = min(tid * chunk, n), end = min(start + chunk, n);
+    int eq = 0;
+    for (int e = start; e < end; ++e) eq += (sort_key(m[e]) == prefix);
+    scan[tid] = eq;
+    __syncthreads();
+    for (int off = 1; off < TOP_THREADS; off <<= 1) {
+        const int v = (tid >= off) ? scan[tid - off] : 0;
+        __syncthreads();
+        scan[tid] += v;
+        __syncthreads();
+    }
+    int before = scan[tid] - eq;
+    for (int e = start; e < end; ++e) {
+        const K key = sort_key(m[e]);
+        int8_t fl = 0;
+        if (key > prefix) {
+            fl = 1;
+        } else if (key == prefix) {
+            fl = (before < remaining) ? int8_t(1) : int8_t(0);
+            ++before;
+        }
+        out[e] = fl;
+    }
+}
+
+__global__ void k_fill_i8(int8_t *out, int n, int8_t v) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+        out[k] = v;
+}
+
+inline unsigned small_grid(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    if (b > 4096) b = 4096;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+}  // namespace
+
+#define LBM_DISPATCH(q, dtype, CALL)                                         \
+    do {                                                                     \
+        if ((q) == 9) {                                                      \
+            using L = D2Q9;                                                  \
+            switch (dtype) {                                                 \
+                case 0: { constexpr int DT = 0; CALL; } break;               \
+                case 1: { constexpr int DT = 1; CALL; } break;               \
+                case 2: { constexpr int DT = 2; CALL; } break;               \
+                case 3: { constexpr int DT = 3; CALL; } break;               \
+                default: return cudaErrorInvalidValue;                       \
+            }                                                                \
+        } else if ((q) == 19) {                                              \
+            using L = D3Q19;                                                 \
+            switch (dtype) {                                                 \
+                case 0: { constexpr int DT = 0; CALL; } break;               \
+                case 1: { constexpr int DT = 1; CALL; } break;               \
+                case 2: { constexpr int DT = 2; CALL; } break;               \
+                case 3: { constexpr int DT = 3; CALL; } break;               \
+                default: return cudaErrorInvalidValue;                       \
+            }                                                                \
+        } else {                                                             \
+            return cudaErrorInvalidValue;                                    \
+        }                                                                    \
+    } while (0)
+
+cudaError_t init_rest(int q, int dtype, void *f, size_t N, cudaStream_t s) {
+    LBM_DISPATCH(q, dtype, (k_init_rest<L, DT><<<ew_grid(N, q), EW_THREADS, 0, s>>>(
+                               static_cast<typename Storage<DT>::T *>(f), N)));
+    return cudaGetLastError();
+}
+
+cudaError_t f64_to_storage(int q, int dtype, int i0, int nq, const double *in, void *out, size_t N,
+                           cudaStream_t s) {
+    LBM_DISPATCH(q, dtype, (k_from_f64<L, DT><<<ew_grid(N, nq), EW_THREADS, 0, s>>>(
+                               in, static_cast<typename Storage<DT>::T *>(out), N, i0)));
+    return cudaGetLastError();
+}
+
+cudaError_t storage_to_f64(int q, int dtype, int i0, int nq, const void *in, double *out, size_t N,
+                           cudaStream_t s) {
+    LBM_DISPATCH(q, dtype, (k_to_f64<L, DT><<<ew_grid(N, nq), EW_THREADS, 0, s>>>(
+                               static_cast<const typename Storage<DT>::T *>(in), out, N, i0)));
+    return cudaGetLastError();
+}
+
+cudaError_t moments_f64(int q, int dtype, const void *f, size_t N, size_t c0, size_t nc,
+                        double *rho, double *u, cudaStream_t s) {
+    LBM_DISPATCH(q, dtype, (k_moments<L, DT><<<ew_grid(nc, 1), EW_THREADS, 0, s>>>(
+                               static_cast<const typename Storage<DT>::T *>(f), N, c0, nc, rho, u)));
+    return cudaGetLastError();
+}
+
+cudaError_t conservation(int q, int dtype, const void *f, size_t N, double *partial, double *result,
+                         cudaStream_t s) {
+    LBM_DISPATCH(q, dtype, (k_cons_partial<L, DT><<<CONS_PARTS, CONS_THREADS, 0, s>>>(
+                               static_cast<const typename Storage<DT>::T *>(f), N, partial)));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_cons_final<<<1, 1024, 0, s>>>(partial, CONS_PARTS, result);
+    return cudaGetLastError();
+}
+
+cudaError_t tiles_to_blocks(int rtype, const void *tiles, int ntx, int nty, int ntz, int m, int mz,
+                            void *blocks, int nbx, int nby, int nbz, cudaStream_t s) {
+    const long long nb = (long long)nbx * nby * nbz;
+    const unsigned g = small_grid(nb, 256);
+    if (rtype == 0)
+        k_tiles_to_blocks<double><<<g, 256, 0, s>>>(static_cast<const double *>(tiles), ntx, nty,
+                                                    ntz, m, mz, static_cast<double *>(blocks), nbx,
+                                                    nby, nbz);
+    else
+        k_tiles_to_blocks<float><<<g, 256, 0, s>>>(static_cast<const float *>(tiles), ntx, nty, ntz,
+                                                   m, mz, static_cast<float *>(blocks), nbx, nby,
+                                                   nbz);
+    return cudaGetLastError();
+}
+
+cudaError_t to_f64(int rtype, const void *in, double *out, size_t n, cudaStream_t s) {
+    const unsigned g = small_grid((long long)n, 256);
+    if (rtype == 0)
+        k_to_f64_plain<double><<<g, 256, 0, s>>>(static_cast<const double *>(in), out, n);
+    else
+        k_to_f64_plain<float><<<g, 256, 0, s>>>(static_cast<const float *>(in), out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t flags_threshold(int rtype, const void *maxima, int n, double T, int8_t *out,
+                            cudaStream_t s) {
+    const unsigned g = small_grid(n, 256);
+    if (rtype == 0)
+        k_flags_threshold<double><<<g, 256, 0, s>>>(static_cast<const double *>(maxima), n, T,
+                                                    T / 2.0, out);
+    else
+        k_flags_threshold<float><<<g, 256, 0, s>>>(static_cast<const float *>(maxima), n, T,
+                                                   T / 2.0, out);
+    return cudaGetLastError();
+}
+
+cudaError_t flags_top(int rtype, const void *maxima, int n, int k, int8_t *out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (k <= 0 || k >= n) {
+        k_fill_i8<<<small_grid(n, 256), 256, 0, s>>>(out, n, k <= 0 ? int8_t(0) : int8_t(1));
+        return cudaGetLastError();
+    }
+    if (rtype == 0)
+        k_flags_top<double, unsigned long long><<<1, TOP_THREADS, 0, s>>>(
+            static_cast<const double *>(maxima), n, k, out);
+    else
+        k_flags_top<float, uint32_t><<<1, TOP_THREADS, 0, s>>>(static_cast<const float *>(maxima),
+                                                              n, k, out);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

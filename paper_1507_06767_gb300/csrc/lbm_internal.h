@@ -1,0 +1,42 @@
+// Internal launch interface between the C-ABI layer (lbm_api.cu) and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "lbm_traits.cuh"
+
+namespace lbm {
+
+// Fused step (lbm_step_d2q9.cu / lbm_step_d3q19.cu).  mode: 0 no sensor, 1 tile max, 2 + field.
+cudaError_t step_d2q9(int dtype, const void *fin, void *fout, const StepParams &p, int mode,
+                      void *tile_max, void *k_field, cudaStream_t s);
+cudaError_t step_d3q19(int dtype, const void *fin, void *fout, const StepParams &p, int mode,
+                       void *tile_max, void *k_field, cudaStream_t s);
+
+// Population helpers (lbm_aux.cu).
+cudaError_t init_rest(int q, int dtype, void *f, size_t N, cudaStream_t s);
+// Conversions of populations [i0, i0 + nq); in / out point at population i0 (N values each).
+cudaError_t f64_to_storage(int q, int dtype, int i0, int nq, const double *in, void *out, size_t N,
+                           cudaStream_t s);
+cudaError_t storage_to_f64(int q, int dtype, int i0, int nq, const void *in, double *out, size_t N,
+                           cudaStream_t s);
+// rho[nc] and u[3][nc] of cells [c0, c0 + nc).
+cudaError_t moments_f64(int q, int dtype, const void *f, size_t N, size_t c0, size_t nc,
+                        double *rho, double *u, cudaStream_t s);
+// Deterministic FP64 sums: result[0] = mass, [1..3] = momentum, [4] = number of non-finite
+// populations.  partial must hold CONS_PARTS * 5 doubles.
+constexpr int CONS_PARTS = 608;
+cudaError_t conservation(int q, int dtype, const void *f, size_t N, double *partial, double *result,
+                         cudaStream_t s);
+
+// Sensor reductions (lbm_aux.cu).  rtype: LBM_F64 (double maxima) or LBM_F32 (float maxima).
+cudaError_t tiles_to_blocks(int rtype, const void *tiles, int ntx, int nty, int ntz, int m, int mz,
+                            void *blocks, int nbx, int nby, int nbz, cudaStream_t s);
+cudaError_t to_f64(int rtype, const void *in, double *out, size_t n, cudaStream_t s);
+cudaError_t flags_threshold(int rtype, const void *maxima, int n, double T, int8_t *out,
+                            cudaStream_t s);
+cudaError_t flags_top(int rtype, const void *maxima, int n, int k, int8_t *out, cudaStream_t s);
+
+}  // namespace lbm

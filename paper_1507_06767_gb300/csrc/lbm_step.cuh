@@ -1,0 +1,186 @@
+// Fused lattice Boltzmann step: pull-stream + moving-wall bounce-back + moments + equilibrium +
+// Knudsen sensor + per-tile sensor max + BGK collision, one pass over HBM.
+//
+// Paper (arXiv 1507.06767): streaming and collision of Sec. 2.2 (Eq. bgklb, collide-and-stream
+// split), equilibrium Eq. (feq_i), moments Eqs. (rho), (u), sensor Eq. (sensor) / (kkn) of
+// Sec. 3.2-3.3, moving bounce-back of Sec. 4.1.
+//
+// Thread mapping: a CTA of 32 x 8 threads covers 32 cells along x and 8 rows along y; in 3-D it
+// walks 8 planes along z.  A CTA therefore owns whole 8^d base tiles (4 of them), so the tile maxima
+// are written with plain stores: no atomics, no zeroing pass.  Each thread issues its q gathers
+// before any arithmetic, so a warp keeps q independent coalesced loads in flight.
+//
+// Arithmetic is done on deviations from the rest state, df_i = f_i - w_i: rho - 1 = sum df_i and
+// rho u = sum c_i df_i lose no digits to the large w_i, and f^neq = df_i - (f^eq_i - w_i) is formed
+// without cancelling against w_i.
+#pragma once
+
+#include "lbm_traits.cuh"
+
+namespace lbm {
+
+constexpr int CTA_X = 32;
+constexpr int CTA_Y = 8;
+constexpr int TILE = 8;
+
+// MODE 0: no sensor.  MODE 1: sensor and per-tile max.  MODE 2: MODE 1 plus per-cell K.
+template <class L, int DT, int MODE>
+__global__ void __launch_bounds__(CTA_X *CTA_Y)
+    fused_step_kernel(const typename Storage<DT>::T *__restrict__ fin,
+                      typename Storage<DT>::T *__restrict__ fout, const StepParams p,
+                      typename Storage<DT>::R *__restrict__ tile_max,
+                      typename Storage<DT>::R *__restrict__ k_field) {
+    using S = Storage<DT>;
+    using T = typename S::T;
+    using R = typename S::R;
+    using B = typename Bits<R>::type;
+    constexpr int Q = L::Q;
+    constexpr int ZT = (L::D == 3) ? TILE : 1;
+
+    const int lane = threadIdx.x;
+    const int x = blockIdx.x * CTA_X + lane;
+    const int y = blockIdx.y * CTA_Y + threadIdx.y;
+    const int z0 = blockIdx.z * ZT;
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const bool active = (x < nx) && (y < ny);
+    const size_t N = (size_t)nx * ny * nz;
+
+    const bool perx = p.periodic & 1, pery = p.periodic & 2, perz = p.periodic & 4;
+    // source coordinates x - c for c = +1 (xm) and c = -1 (xp), with their validity
+    const int xm = (x == 0) ? nx - 1 : x - 1;
+    const int xp = (x == nx - 1) ? 0 : x + 1;
+    const bool vxm = (x > 0) || perx;
+    const bool vxp = (x < nx - 1) || perx;
+    const int ym = (y == 0) ? ny - 1 : y - 1;
+    const int yp = (y == ny - 1) ? 0 : y + 1;
+    const bool vym = (y > 0) || pery;
+    const bool vyp = (y < ny - 1) || pery;  // false <=> the y+1 ghost is the lid
+
+    const R omega = (R)p.omega;
+    const R lidx = (R)p.lid_x, lidz = (R)p.lid_z;
+
+    B kmax = 0;
+
+    for (int dz = 0; dz < ZT; ++dz) {
+        const int z = z0 + dz;
+        if (z >= nz) break;
+        if (active) {
+            int zm = z, zp = z;
+            bool vzm = true, vzp = true;
+            if (L::D == 3) {
+                zm = (z == 0) ? nz - 1 : z - 1;
+                zp = (z == nz - 1) ? 0 : z + 1;
+                vzm = (z > 0) || perz;
+                vzp = (z < nz - 1) || perz;
+            }
+            const int idx = (z * ny + y) * nx + x;
+
+            R df[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+                const int sx = cx == 1 ? xm : (cx == -1 ? xp : x);
+                const int sy = cy == 1 ? ym : (cy == -1 ? yp : y);
+                const int sz = cz == 1 ? zm : (cz == -1 ? zp : z);
+                const bool valid = (cx == 1 ? vxm : (cx == -1 ? vxp : true)) &&
+                                   (cy == 1 ? vym : (cy == -1 ? vyp : true)) &&
+                                   (cz == 1 ? vzm : (cz == -1 ? vzp : true));
+                const size_t src = valid ? (size_t)i * N + (size_t)((sz * ny + sy) * nx + sx)
+                                         : (size_t)L::opp(i) * N + (size_t)idx;
+                R v = S::to_r(fin[src]);
+                if (!S::SHIFTED) v -= weight<L, R>(i);  // w_opp(i) == w_i
+                if (cy == -1 && !vyp) {
+                    // moving lid: + 2 w_i (c_i . u_lid) / c_s^2, wall density 1
+                    v += R(6) * weight<L, R>(i) * (R(cx) * lidx + R(cz) * lidz);
+                }
+                df[i] = v;
+            }
+
+            // moments as deviations from rest
+            R drho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                drho += df[i];
+                if (L::cx(i)) jx += R(L::cx(i)) * df[i];
+                if (L::cy(i)) jy += R(L::cy(i)) * df[i];
+                if (L::cz(i)) jz += R(L::cz(i)) * df[i];
+            }
+            const R rho = R(1) + drho;
+            const R inv_rho = R(1) / rho;
+            const R ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
+            const R usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
+
+            R ksum = 0;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const R cu = R(L::cx(i)) * ux + R(L::cy(i)) * uy + R(L::cz(i)) * uz;
+                // P_i = c.u / cs2 + ((c.u)^2 - cs2 u.u) / (2 cs2^2)
+                const R P = R(3) * cu + R(4.5) * cu * cu - usq15;
+                const R w = weight<L, R>(i);
+                const R dfeq = w * (drho + rho * P);  // f^eq_i - w_i
+                const R fneq = df[i] - dfeq;
+                if (MODE != 0) {
+                    const R feq = w * rho * (R(1) + P);
+                    if constexpr (sizeof(R) == 4) {
+                        ksum += __fdividef(fabsf(fneq), feq);
+                    } else {
+                        ksum += fabs(fneq) / feq;
+                    }
+                }
+                const R dnew = df[i] - omega * fneq;
+                fout[(size_t)i * N + idx] = S::from_r(S::SHIFTED ? dnew : dnew + w);
+            }
+            if (MODE != 0) {
+                const R K = ksum * (R(1) / R(Q));
+                const B kb = max_bits(K);
+                kmax = kb > kmax ? kb : kmax;
+                if (MODE == 2) k_field[idx] = K;
+            }
+        }
+    }
+
+    if (MODE != 0) {
+        // max over the 8 lanes of each x-tile of this row, then over the 8 rows via shared memory
+#pragma unroll
+        for (int off = 4; off >= 1; off >>= 1) {
+            const B o = __shfl_xor_sync(0xffffffffu, kmax, off);
+            kmax = o > kmax ? o : kmax;
+        }
+        __shared__ B part[CTA_Y][CTA_X / TILE];
+        if ((lane & (TILE - 1)) == 0) part[threadIdx.y][lane / TILE] = kmax;
+        __syncthreads();
+        if (threadIdx.y == 0 && lane < CTA_X / TILE) {
+            B m = part[0][lane];
+#pragma unroll
+            for (int r = 1; r < CTA_Y; ++r) m = part[r][lane] > m ? part[r][lane] : m;
+            const int tx = blockIdx.x * (CTA_X / TILE) + lane;
+            if (tx < p.ntx) {
+                const size_t t = ((size_t)blockIdx.z * p.nty + blockIdx.y) * p.ntx + tx;
+                tile_max[t] = from_bits(m, R(0));
+            }
+        }
+    }
+}
+
+template <class L, int DT>
+cudaError_t launch_fused_step(const void *fin, void *fout, const StepParams &p, int mode,
+                              void *tile_max, void *k_field, cudaStream_t stream) {
+    using T = typename Storage<DT>::T;
+    using R = typename Storage<DT>::R;
+    const int zt = (L::D == 3) ? TILE : 1;
+    dim3 block(CTA_X, CTA_Y, 1);
+    dim3 grid((p.nx + CTA_X - 1) / CTA_X, (p.ny + CTA_Y - 1) / CTA_Y, (p.nz + zt - 1) / zt);
+    const T *a = static_cast<const T *>(fin);
+    T *b = static_cast<T *>(fout);
+    R *tm = static_cast<R *>(tile_max);
+    R *kf = static_cast<R *>(k_field);
+    if (mode == 0)
+        fused_step_kernel<L, DT, 0><<<grid, block, 0, stream>>>(a, b, p, tm, kf);
+    else if (mode == 1)
+        fused_step_kernel<L, DT, 1><<<grid, block, 0, stream>>>(a, b, p, tm, kf);
+    else
+        fused_step_kernel<L, DT, 2><<<grid, block, 0, stream>>>(a, b, p, tm, kf);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

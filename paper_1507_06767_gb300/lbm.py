@@ -1,0 +1,399 @@
+"""Python binding of the C ABI in include/lbm.h (ctypes; argument marshalling only).
+
+Every function of the C ABI is exposed under the same name and raises ``LbmError`` on a negative
+status.  Device memory for the two population buffers can come from PyTorch (``Lattice`` does that
+with ``lbm_attach``); streams are passed as raw ``cudaStream_t`` handles, e.g.
+``torch.cuda.current_stream().cuda_stream``.  Nothing here computes any part of the method: the
+library runs every step in its CUDA kernels, and importing this module fails loudly when the
+library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblbm.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "lbm.h")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build the CUDA library first "
+        "(python -c 'import __graft_entry__ as g; g.build()'); there is no CPU fallback")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+
+def _header_constants():
+    out = {}
+    with open(HEADER) as fh:
+        for m in re.finditer(r"#define\s+(LBM_\w+)\s+\(?(-?\d+)\)?", fh.read()):
+            out[m.group(1)] = int(m.group(2))
+    return out
+
+
+globals().update(_header_constants())
+
+_h = ctypes.c_void_p
+_i, _d, _sz, _ll = ctypes.c_int, ctypes.c_double, ctypes.c_size_t, ctypes.c_longlong
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_i8p = ctypes.c_void_p
+
+_SIGS = {
+    "lbm_last_error": (_i, []),
+    "lbm_last_message": (ctypes.c_char_p, []),
+    "lbm_strerror": (ctypes.c_char_p, [_i]),
+    "lbm_version": (_i, []),
+    "lbm_create": (_h, [_i, _i, _i, _i, _d]),
+    "lbm_destroy": (_i, [_h]),
+    "lbm_set_dtype": (_i, [_h, _i]),
+    "lbm_set_lid": (_i, [_h, _d, _d]),
+    "lbm_set_periodic": (_i, [_h, _i]),
+    "lbm_set_tau": (_i, [_h, _d]),
+    "lbm_set_stream": (_i, [_h, _vp]),
+    "lbm_set_sensor_every": (_i, [_h, _i]),
+    "lbm_set_sensor_field": (_i, [_h, _i]),
+    "lbm_set_block": (_i, [_h, _i]),
+    "lbm_set_profiling": (_i, [_h, _i]),
+    "lbm_set_graphs": (_i, [_h, _i]),
+    "lbm_attach": (_i, [_h, _vp, _vp, _sz]),
+    "lbm_population_bytes": (_sz, [_h]),
+    "lbm_nblocks": (_i, [_h, _i]),
+    "lbm_steps_done": (_ll, [_h]),
+    "lbm_reset": (_i, [_h]),
+    "lbm_step": (_i, [_h, _i]),
+    "lbm_sensor": (_i, [_h, _i, _vp]),
+    "lbm_sensor_dev": (_i, [_h, _i, _vp]),
+    "lbm_flag": (_i, [_h, _d, _vp]),
+    "lbm_flag_dev": (_i, [_h, _d, _vp]),
+    "lbm_flag_top": (_i, [_h, _d, _vp]),
+    "lbm_flag_top_dev": (_i, [_h, _d, _vp]),
+    "lbm_flags_from_maxima": (_i, [_vp, _i, _i, _i, _d, _vp, _vp]),
+    "lbm_get_populations": (_i, [_h, _vp]),
+    "lbm_set_populations": (_i, [_h, _vp]),
+    "lbm_get_raw": (_i, [_h, _vp, _sz]),
+    "lbm_set_raw": (_i, [_h, _vp, _sz]),
+    "lbm_get_moments": (_i, [_h, _vp, _vp]),
+    "lbm_get_sensor_field": (_i, [_h, _vp]),
+    "lbm_conservation": (_i, [_h, _dp, _dp]),
+    "lbm_kernel_time": (_i, [_h, _dp, ctypes.POINTER(_ll)]),
+    "lbm_blocks_step": (_i, [_h, _vp]),
+}
+
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib.lbm_last_message().decode(errors="replace")
+        name = _lib.lbm_strerror(status).decode()
+        super().__init__(f"{where}: {name} ({status}): {msg}")
+
+
+def _ck(status: int, where: str) -> int:
+    if status < 0:
+        raise LbmError(status, where)
+    return status
+
+
+def _ptr(a):
+    """Address of a numpy array, a torch tensor, or an int address."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous()
+        return a.data_ptr()
+    raise TypeError(f"cannot take the address of {type(a)}")
+
+
+# ----------------------------------------------------------------------------- C-ABI functions
+def lbm_last_error() -> int:
+    return _lib.lbm_last_error()
+
+
+def lbm_last_message() -> str:
+    return _lib.lbm_last_message().decode(errors="replace")
+
+
+def lbm_strerror(status: int) -> str:
+    return _lib.lbm_strerror(status).decode()
+
+
+def lbm_version() -> int:
+    return _lib.lbm_version()
+
+
+def lbm_create(lattice: int, nx: int, ny: int, nz: int, tau: float) -> int:
+    h = _lib.lbm_create(lattice, nx, ny, nz, tau)
+    if not h:
+        raise LbmError(_lib.lbm_last_error(), "lbm_create")
+    return h
+
+
+def _wrap(name, *conv):
+    f = getattr(_lib, name)
+
+    def call(*args):
+        return _ck(f(*args), name)
+
+    call.__name__ = name
+    return call
+
+
+lbm_destroy = _wrap("lbm_destroy")
+lbm_set_dtype = _wrap("lbm_set_dtype")
+lbm_set_lid = _wrap("lbm_set_lid")
+lbm_set_periodic = _wrap("lbm_set_periodic")
+lbm_set_tau = _wrap("lbm_set_tau")
+lbm_set_sensor_every = _wrap("lbm_set_sensor_every")
+lbm_set_sensor_field = _wrap("lbm_set_sensor_field")
+lbm_set_block = _wrap("lbm_set_block")
+lbm_set_profiling = _wrap("lbm_set_profiling")
+lbm_set_graphs = _wrap("lbm_set_graphs")
+lbm_reset = _wrap("lbm_reset")
+lbm_step = _wrap("lbm_step")
+
+
+def lbm_set_stream(h, stream) -> int:
+    return _ck(_lib.lbm_set_stream(h, stream if stream is None or isinstance(stream, int)
+                                   else stream.cuda_stream), "lbm_set_stream")
+
+
+def lbm_attach(h, a, b, nbytes: int) -> int:
+    return _ck(_lib.lbm_attach(h, _ptr(a), _ptr(b), nbytes), "lbm_attach")
+
+
+def lbm_population_bytes(h) -> int:
+    return _lib.lbm_population_bytes(h)
+
+
+def lbm_nblocks(h, block: int) -> int:
+    return _lib.lbm_nblocks(h, block)
+
+
+def lbm_steps_done(h) -> int:
+    return _lib.lbm_steps_done(h)
+
+
+def lbm_sensor(h, block: int, out) -> int:
+    return _ck(_lib.lbm_sensor(h, block, _ptr(out)), "lbm_sensor")
+
+
+def lbm_sensor_dev(h, block: int, out_dev) -> int:
+    return _ck(_lib.lbm_sensor_dev(h, block, _ptr(out_dev)), "lbm_sensor_dev")
+
+
+def lbm_flag(h, threshold: float, out) -> int:
+    return _ck(_lib.lbm_flag(h, threshold, _ptr(out)), "lbm_flag")
+
+
+def lbm_flag_dev(h, threshold: float, out_dev) -> int:
+    return _ck(_lib.lbm_flag_dev(h, threshold, _ptr(out_dev)), "lbm_flag_dev")
+
+
+def lbm_flag_top(h, frac: float, out) -> int:
+    return _ck(_lib.lbm_flag_top(h, frac, _ptr(out)), "lbm_flag_top")
+
+
+def lbm_flag_top_dev(h, frac: float, out_dev) -> int:
+    return _ck(_lib.lbm_flag_top_dev(h, frac, _ptr(out_dev)), "lbm_flag_top_dev")
+
+
+def lbm_flags_from_maxima(maxima_dev, maxima_dtype: int, n: int, rule: int, param: float, out_dev,
+                          stream=None) -> int:
+    s = stream if stream is None or isinstance(stream, int) else stream.cuda_stream
+    return _ck(_lib.lbm_flags_from_maxima(_ptr(maxima_dev), maxima_dtype, n, rule, param,
+                                          _ptr(out_dev), s), "lbm_flags_from_maxima")
+
+
+def lbm_get_populations(h, out) -> int:
+    return _ck(_lib.lbm_get_populations(h, _ptr(out)), "lbm_get_populations")
+
+
+def lbm_set_populations(h, arr) -> int:
+    return _ck(_lib.lbm_set_populations(h, _ptr(arr)), "lbm_set_populations")
+
+
+def lbm_get_raw(h, out, nbytes: int) -> int:
+    return _ck(_lib.lbm_get_raw(h, _ptr(out), nbytes), "lbm_get_raw")
+
+
+def lbm_set_raw(h, arr, nbytes: int) -> int:
+    return _ck(_lib.lbm_set_raw(h, _ptr(arr), nbytes), "lbm_set_raw")
+
+
+def lbm_get_moments(h, rho, u) -> int:
+    return _ck(_lib.lbm_get_moments(h, _ptr(rho), _ptr(u)), "lbm_get_moments")
+
+
+def lbm_get_sensor_field(h, out) -> int:
+    return _ck(_lib.lbm_get_sensor_field(h, _ptr(out)), "lbm_get_sensor_field")
+
+
+def lbm_conservation(h):
+    """Returns (mass, momentum[3]); raises LbmError(LBM_ENUMERIC) on non-finite populations."""
+    m = ctypes.c_double()
+    j = (ctypes.c_double * 3)()
+    _ck(_lib.lbm_conservation(h, ctypes.byref(m), j), "lbm_conservation")
+    return m.value, np.array(list(j))
+
+
+def lbm_kernel_time(h):
+    ms = ctypes.c_double()
+    n = ctypes.c_longlong()
+    _ck(_lib.lbm_kernel_time(h, ctypes.byref(ms), ctypes.byref(n)), "lbm_kernel_time")
+    return ms.value, n.value
+
+
+def lbm_blocks_step(h, batch=None) -> int:
+    return _ck(_lib.lbm_blocks_step(h, _ptr(batch)), "lbm_blocks_step")
+
+
+def exported_symbols():
+    """Names of the functions declared in include/lbm.h."""
+    with open(HEADER) as fh:
+        src = fh.read()
+    return sorted(set(re.findall(r"LBM_API\s+[\w\s\*]+?\b(lbm_\w+)\s*\(", src)))
+
+
+# ----------------------------------------------------------------------------- convenience object
+_DTYPE_BYTES = {0: 8, 1: 4, 2: 2, 3: 2}
+
+
+class Lattice:
+    """A lattice handle whose population buffers are PyTorch CUDA tensors (``lbm_attach``).
+
+    ``Lattice(LBM_D3Q19, 256, 256, 256, tau, dtype=LBM_F32)`` -> ``step(n)``, ``sensor(block)``,
+    ``flag(T)``, ``flag_top(frac)``, ``populations()``...  Numpy arrays in and out, layout
+    (q, nz, ny, nx).
+    """
+
+    def __init__(self, lattice, nx, ny, nz, tau, dtype=None, lid=(0.1, 0.0), periodic=0,
+                 stream=None, torch_buffers=True, device=None):
+        import torch
+
+        self.q = int(lattice)
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        if device is not None:
+            torch.cuda.set_device(device)
+        self.h = lbm_create(self.q, self.nx, self.ny, self.nz, float(tau))
+        self.dtype = LBM_F32 if dtype is None else int(dtype)
+        lbm_set_dtype(self.h, self.dtype)
+        lbm_set_lid(self.h, float(lid[0]), float(lid[1]))
+        lbm_set_periodic(self.h, int(periodic))
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        lbm_set_stream(self.h, self.stream.cuda_stream)
+        self._bufs = None
+        if torch_buffers:
+            nbytes = lbm_population_bytes(self.h)
+            a = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            b = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            self._bufs = (a, b)
+            lbm_attach(self.h, a, b, nbytes)
+        lbm_reset(self.h)
+
+    @property
+    def shape(self):
+        return (self.q, self.nz, self.ny, self.nx)
+
+    @property
+    def ncells(self):
+        return self.nx * self.ny * self.nz
+
+    def close(self):
+        if self.h:
+            lbm_destroy(self.h)
+            self.h = None
+            self._bufs = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def step(self, n=1):
+        lbm_step(self.h, int(n))
+
+    def sensor(self, block):
+        out = np.empty(lbm_nblocks(self.h, block), dtype=np.float64)
+        lbm_sensor(self.h, block, out)
+        return out
+
+    def flag(self, threshold, block=None):
+        if block is not None:
+            lbm_set_block(self.h, block)
+        out = np.empty(lbm_nblocks(self.h, self.block), dtype=np.int8)
+        lbm_flag(self.h, float(threshold), out)
+        return out
+
+    def flag_top(self, frac, block=None):
+        if block is not None:
+            lbm_set_block(self.h, block)
+        out = np.empty(lbm_nblocks(self.h, self.block), dtype=np.int8)
+        lbm_flag_top(self.h, float(frac), out)
+        return out
+
+    _block = 16
+
+    @property
+    def block(self):
+        return self._block
+
+    @block.setter
+    def block(self, b):
+        lbm_set_block(self.h, int(b))
+        self._block = int(b)
+
+    def populations(self):
+        out = np.empty(self.shape, dtype=np.float64)
+        lbm_get_populations(self.h, out)
+        return out
+
+    def set_populations(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        assert f.shape == self.shape
+        lbm_set_populations(self.h, f)
+
+    def moments(self):
+        rho = np.empty((self.nz, self.ny, self.nx))
+        u = np.empty((3, self.nz, self.ny, self.nx))
+        lbm_get_moments(self.h, rho, u)
+        return rho, u
+
+    def sensor_field(self):
+        out = np.empty((self.nz, self.ny, self.nx))
+        lbm_get_sensor_field(self.h, out)
+        return out
+
+    def conservation(self):
+        return lbm_conservation(self.h)
+
+    def raw(self):
+        nbytes = lbm_population_bytes(self.h)
+        out = np.empty(nbytes, dtype=np.uint8)
+        lbm_get_raw(self.h, out, nbytes)
+        return out
+
+    def set_raw(self, raw):
+        raw = np.ascontiguousarray(raw, dtype=np.uint8)
+        lbm_set_raw(self.h, raw, raw.nbytes)

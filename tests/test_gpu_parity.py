@@ -1,0 +1,309 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances (written per test):
+* FP64 storage: populations and sensor within 1e-12 / 1e-10 relative (the GPU evaluates the same
+  formulas on deviations from the rest state, so only the rounding order differs);
+* FP32 storage: populations max|f_gpu - f_ref| / max|f_ref| <= 1e-5 after the run's full step
+  count; sensor block maxima <= 1e-4 relative (K is a mean of |f^neq|/f^eq, and f^neq is ~1e-4 of
+  f, so FP32 rounding of f costs ~1e-4 of K);
+* flags: identical except blocks whose oracle maximum lies within 1e-4 (relative) of a decision
+  boundary (T, T/2, or the k-th largest maximum).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from tests import seeded
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_1507_06767_gb300 import build
+
+    build.build()
+    import paper_1507_06767_gb300 as pkg
+
+    return pkg
+
+
+def rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / np.abs(np.asarray(b)).max())
+
+
+def perturbed(o, seed, amp):
+    return o.w[:, None, None, None] * (1.0 + seeded.relative_perturbation(seed, o.shape, amp))
+
+
+def make(L, q, nx, ny, nz, tau, dtype, lid=(0.1, 0.0, 0.0), periodic=0):
+    lat = L.Lattice(q, nx, ny, nz, tau, dtype=dtype, lid=(lid[0], lid[2]), periodic=periodic)
+    o = O.Oracle(q, nx, ny, nz, tau, lid=lid, periodic=periodic)
+    return lat, o
+
+
+# ----------------------------------------------------------------------------- configuration 1
+def test_cavity_d2q9_fp64_128_re100_full_run(L):
+    """D2Q9 lid-driven cavity, 128^2, FP64, Re = 100 (u = 0.1, tau = 0.884), 2000 steps, sensor every
+    100 steps reduced to 16^2 block maxima, fixed threshold flags.  The threshold reading is four
+    times the Couette-level sensor of the mean lid shear, T = 4 (4/3) tau u / N."""
+    N, u, re, steps, every, b = 128, 0.1, 100.0, 2000, 100, 16
+    tau = O.tau_from_re(u, N, re)
+    T = 4.0 * (4.0 / 3.0) * tau * u / N
+    lat, o = make(L, 9, N, N, 1, tau, L.LBM_F64)
+    L.lbm_set_sensor_every(lat.h, every)
+    lat.block = b
+    f_ref = o.rest()
+    n_flag_cmp = 0
+    for k in range(steps // every):
+        lat.step(every)
+        f_ref, K = o.run(f_ref, every, sensor_last=True)
+        ref_max = O.block_max(K, b)
+        gpu_max = lat.sensor(b)
+        assert gpu_max.shape == (64,)
+        assert rel(gpu_max, ref_max) < 1e-10, k
+        flags = lat.flag(T)
+        ok, ncmp, _ = O.flags_agree(flags, ref_max, "threshold", T, 1e-4)
+        assert ok, k
+        n_flag_cmp += ncmp
+        top = lat.flag_top(0.1)
+        ok, _, _ = O.flags_agree(top, ref_max, "top", 0.1, 1e-4)
+        assert ok, k
+    assert n_flag_cmp > 0.9 * 64 * (steps // every)
+    f_gpu = lat.populations()
+    assert rel(f_gpu, f_ref) < 1e-12
+    # refine and coarsen both occur at the end: the corners under the lid are hot
+    assert (flags == 1).any() and (flags == -1).any()
+    lat.close()
+
+
+def test_cavity_d2q9_fp32_matches_fp64_oracle(L):
+    """Same cavity with FP32 storage: the populations stay within 1e-5 of the FP64 oracle after 2000
+    steps and the per-cell sensor field within 1e-4 of the oracle's largest value."""
+    N, tau, steps = 128, O.tau_from_re(0.1, 128, 100.0), 2000
+    lat, o = make(L, 9, N, N, 1, tau, L.LBM_F32)
+    L.lbm_set_sensor_field(lat.h, 1)
+    lat.step(steps)
+    f_ref, K = o.run(o.rest(), steps, sensor_last=True)
+    assert rel(lat.populations(), f_ref) < 1e-5
+    assert rel(lat.sensor_field()[0], K[0]) < 1e-4
+    lat.close()
+
+
+# ----------------------------------------------------------------------------- configuration 2
+def test_cavity_d3q19_fp32_ragged_full_step_count(L):
+    """D3Q19 cavity in FP32 at the 256^3 run's tau (0.5768) and lid speed, on a ragged 40x36x33
+    lattice (tiles of 8 and blocks of 16 with partial ones at every high end), for the full 10000
+    steps; sensor every step, 16^3 block maxima and top-10 % flags."""
+    tau, steps = O.tau_from_re(0.1, 256, 1000.0), 10000
+    lat, o = make(L, 19, 40, 36, 33, tau, L.LBM_F32)
+    L.lbm_set_sensor_every(lat.h, 1)
+    lat.step(steps)
+    f_ref, K = o.run(o.rest(), steps, sensor_last=True)
+    assert rel(lat.populations(), f_ref) < 1e-5
+    ref_max = O.block_max(K, 16)
+    gpu_max = lat.sensor(16)
+    assert gpu_max.shape == (27,)
+    assert rel(gpu_max, ref_max) < 1e-4
+    ok, _, _ = O.flags_agree(lat.flag_top(0.1, block=16), ref_max, "top", 0.1, 1e-4)
+    assert ok
+    ok, _, _ = O.flags_agree(lat.flag_top(0.1, block=8), O.block_max(K, 8), "top", 0.1, 1e-4)
+    assert ok
+    m0 = float(np.sum(o.w)) * 40 * 36 * 33
+    m, _ = lat.conservation()
+    assert abs(m - m0) / m0 < 1e-6
+    lat.close()
+
+
+def test_cavity_d3q19_256_full_size_sampled(L):
+    """The 256^3 D3Q19 FP32 workload in the benchmark's launch configuration (sensor every step):
+    one step from a seeded perturbed state, checked on sampled cells (all corners, edges, faces and
+    random interior cells) and on the 16^3 block maxima of sampled blocks, each evaluated by the
+    oracle one by one."""
+    n, tau = 256, O.tau_from_re(0.1, 256, 1000.0)
+    q = 19
+    lat = L.Lattice(q, n, n, n, tau, dtype=L.LBM_F32, lid=(0.1, 0.0))
+    o = O.Oracle(q, n, n, n, tau, lid=(0.1, 0.0, 0.0))
+    L.lbm_set_sensor_every(lat.h, 1)
+    f0 = perturbed(o, seed=256, amp=0.03).astype(np.float32)
+    lat.set_raw(f0.view(np.uint8).reshape(-1))
+    lat.step(1)
+    out = lat.raw().view(np.float32).reshape(q, -1)
+    gmax = lat.sensor(16)
+    f0d = f0.astype(np.float64)
+    del f0
+    g = seeded.rng(7)
+    e = np.array([0, 1, 2, n // 2, n - 3, n - 2, n - 1])
+    xs, ys, zs = np.meshgrid(e, e, e, indexing="ij")
+    cells = ((zs * n + ys) * n + xs).reshape(-1)
+    cells = np.concatenate([cells, g.integers(0, n ** 3, size=4000)])
+    ref, _ = o.step_cells(f0d, cells)
+    got = out[:, cells].T.astype(np.float64)
+    assert np.abs(got - ref).max() / np.abs(ref).max() < 2e-7
+    # sampled 16^3 blocks, including the corner blocks under the lid
+    nb = n // 16
+    blocks = [0, nb - 1, nb * (nb - 1), nb * nb * nb - 1, nb * nb * (nb - 1) + nb * (nb - 1)]
+    blocks += list(g.integers(0, nb ** 3, size=6))
+    for bidx in blocks:
+        bx, by, bz = bidx % nb, (bidx // nb) % nb, bidx // (nb * nb)
+        z, y, x = np.meshgrid(np.arange(16) + 16 * bz, np.arange(16) + 16 * by,
+                              np.arange(16) + 16 * bx, indexing="ij")
+        bc = ((z * n + y) * n + x).reshape(-1)
+        _, K = o.step_cells(f0d, bc)
+        assert abs(gmax[bidx] - K.max()) / K.max() < 1e-5, bidx
+    lat.close()
+
+
+# ----------------------------------------------------------------------------- edge cases
+EDGE_CASES = [
+    (9, (1, 1, 1), 0), (9, (2, 3, 1), 0), (9, (5, 7, 1), O.PERIODIC_X), (9, (33, 17, 1), 0),
+    (9, (9, 8, 1), O.PERIODIC_X | O.PERIODIC_Y), (19, (1, 1, 1), 0), (19, (2, 3, 2), 0),
+    (19, (5, 7, 3), O.PERIODIC_Z), (19, (33, 17, 9), 0), (19, (8, 8, 8), 7),
+    (19, (31, 9, 17), O.PERIODIC_X | O.PERIODIC_Y),
+]
+
+
+@pytest.mark.parametrize("q,dims,periodic", EDGE_CASES)
+@pytest.mark.parametrize("dtype", ["F64", "F32"])
+def test_edge_lattices_perturbed(L, q, dims, periodic, dtype):
+    """Tiny and ragged lattices where most cells touch a wall, every periodic combination, seeded
+    perturbed states, a lid with x and z components: populations, per-cell sensor and 8-tile maxima
+    after 5 steps."""
+    dt = getattr(L, "LBM_" + dtype)
+    lid = (0.08, 0.0, 0.03 if q == 19 else 0.0)
+    lat, o = make(L, q, *dims, tau=0.71, dtype=dt, lid=lid, periodic=periodic)
+    L.lbm_set_sensor_field(lat.h, 1)
+    f0 = perturbed(o, seed=sum(dims) * q + periodic, amp=0.03)
+    lat.set_populations(f0)
+    f_in = lat.populations()  # the storage-rounded input (exact for FP64)
+    if dtype == "F64":
+        assert np.array_equal(f_in, f0)
+    lat.step(5)
+    f_ref, K = o.run(f_in, 5, sensor_last=True)
+    tol_f, tol_k = (1e-13, 1e-11) if dtype == "F64" else (2e-6, 1e-4)
+    assert rel(lat.populations(), f_ref) < tol_f
+    assert rel(lat.sensor_field(), K) < tol_k
+    assert rel(lat.sensor(8), O.block_max(K, 8)) < tol_k
+    rho, u = lat.moments()
+    _, _, rho_ref, u_ref = o.step(f_ref, moments=True)
+    assert np.abs(rho - rho_ref).max() < (1e-14 if dtype == "F64" else 1e-6)
+    assert np.abs(u - u_ref).max() < (1e-14 if dtype == "F64" else 1e-6)
+    lat.close()
+
+
+def test_uniform_equilibrium_gpu(L):
+    """Eq. (sensor) at f = f_eq: the GPU sensor of a uniform periodic flow is zero to round-off."""
+    for q, dims in ((9, (16, 8, 1)), (19, (8, 8, 8))):
+        o = O.Oracle(q, *dims, tau=0.8, periodic=7)
+        u0 = np.array([0.05, -0.02, 0.03 if q == 19 else 0.0])[:, None, None, None]
+        for dt, tol in ((L.LBM_F64, 1e-14), (L.LBM_F32, 2e-6)):
+            lat = L.Lattice(q, *dims, 0.8, dtype=dt, lid=(0, 0), periodic=7)
+            lat.set_populations(o.equilibrium(1.0, u0))
+            L.lbm_set_sensor_every(lat.h, 1)
+            lat.step(3)
+            assert lat.sensor(8).max() < tol
+            lat.close()
+
+
+# ----------------------------------------------------------------------------- flag builder
+@pytest.mark.parametrize("n", [1, 7, 410, 4096, 100003])
+@pytest.mark.parametrize("mdtype", ["F32", "F64"])
+def test_flag_builder_bit_exact(L, n, mdtype):
+    """The flag builder on seeded block maxima with ties, NaNs and values on and one ulp around T and
+    T/2: bit-identical to the oracle's rules (both decide in double on the same values)."""
+    import torch
+
+    T = 1e-3
+    m = seeded.block_maxima(n, n, ties=n // 5, nans=max(0, n // 50), near=(T, n // 10))
+    if mdtype == "F64":
+        m = m.astype(np.float64)
+    dev = torch.from_numpy(m).cuda()
+    out = torch.empty(n, dtype=torch.int8, device="cuda")
+    dt = getattr(L, "LBM_" + mdtype)
+    s = torch.cuda.current_stream().cuda_stream
+    L.lbm_flags_from_maxima(dev, dt, n, L.LBM_FLAG_THRESHOLD, T, out, s)
+    assert np.array_equal(out.cpu().numpy(), O.flags_threshold(m, T))
+    for frac in (0.0, 0.1, 0.5, 1.0, 1.0 / n):
+        L.lbm_flags_from_maxima(dev, dt, n, L.LBM_FLAG_TOP, frac, out, s)
+        assert np.array_equal(out.cpu().numpy(), O.flags_top(m, frac)), frac
+
+
+# ----------------------------------------------------------------------------- state handling
+def test_checkpoint_resume_and_graphs_bitwise(L):
+    """Raw checkpoint + resume continues bit for bit; graph replay gives the same bits as launches."""
+    tau = 0.6
+    a = L.Lattice(19, 24, 20, 18, tau, dtype=L.LBM_F32)
+    a.step(37)
+    snap = a.raw()
+    a.step(41)
+    ref = a.raw()
+    b = L.Lattice(19, 24, 20, 18, tau, dtype=L.LBM_F32)
+    b.set_raw(snap)
+    L.lbm_set_graphs(b.h, 0)
+    b.step(41)
+    assert np.array_equal(b.raw(), ref)
+    a.close()
+    b.close()
+
+
+def test_nan_is_detected_and_refined(L):
+    """A NaN planted in the populations makes the FP64 conservation check fail with LBM_ENUMERIC and
+    poisons its block's sensor maximum, which the flag rules refine."""
+    o = O.Oracle(19, 16, 16, 16, 0.7, lid=(0.1, 0, 0))
+    lat = L.Lattice(19, 16, 16, 16, 0.7, dtype=L.LBM_F32)
+    f = o.rest()
+    f[5, 3, 4, 12] = np.nan  # cell (x=12, y=4, z=3): 8-tile (1, 0, 0)
+    lat.set_populations(f)
+    with pytest.raises(L.LbmError) as ei:
+        lat.conservation()
+    assert ei.value.status == L.LBM_ENUMERIC
+    L.lbm_set_sensor_every(lat.h, 1)
+    lat.step(1)
+    m8 = lat.sensor(8)
+    assert np.isnan(m8).sum() >= 1
+    flags = lat.flag(1.0, block=8)
+    assert (flags[np.isnan(m8)] == 1).all()
+    lat.close()
+
+
+def test_sensor_before_any_sensor_step(L):
+    lat = L.Lattice(9, 16, 16, 1, 0.7, dtype=L.LBM_F32)
+    with pytest.raises(L.LbmError) as ei:
+        lat.sensor(8)
+    assert ei.value.status == L.LBM_ESTATE
+    L.lbm_set_sensor_every(lat.h, 3)
+    lat.step(2)
+    with pytest.raises(L.LbmError):
+        lat.sensor(8)
+    lat.step(1)
+    assert lat.sensor(8).shape == (4,)
+    lat.close()
+
+
+def test_library_owned_buffers_and_streams(L):
+    """Without torch buffers the library allocates its own; work on a side torch stream is ordered
+    on that stream."""
+    import torch
+
+    o = O.Oracle(19, 12, 10, 9, 0.65, lid=(0.1, 0, 0))
+    s = torch.cuda.Stream()
+    lat = L.Lattice(19, 12, 10, 9, 0.65, dtype=L.LBM_F64, torch_buffers=False, stream=s)
+    lat.step(20)
+    f_ref, _ = o.run(o.rest(), 20)
+    assert rel(lat.populations(), f_ref) < 1e-13
+    lat.close()
+
+
+def test_profiling_counts_launches(L):
+    lat = L.Lattice(19, 32, 32, 32, 0.6, dtype=L.LBM_F32)
+    L.lbm_set_profiling(lat.h, 1)
+    lat.step(7)
+    ms, n = L.lbm_kernel_time(lat.h)
+    assert n == 7 and ms > 0
+    lat.close()

@@ -357,3 +357,15 @@ def test_tau_from_re_paper_cases():
     assert abs(O.tau_from_re(0.05, 120, 1000) - 0.518) < 1e-12
     assert abs(O.tau_from_re(0.1, 128, 100) - 0.884) < 1e-12
     assert abs(O.tau_from_re(0.1, 256, 1000) - 0.5768) < 1e-12
+
+
+def test_step_cells_matches_full_step():
+    """The sampled-cell evaluation is the same step: it must agree bit for bit with the full step on
+    every cell, boundary cells included."""
+    o = O.Oracle(19, 6, 5, 4, tau=0.66, lid=(0.1, 0, 0.02), periodic=O.PERIODIC_Z)
+    f = perturbed(o, seed=21, amp=0.04)
+    full, K, _, _ = o.step(f, sensor=True)
+    cells = np.arange(6 * 5 * 4)[::-1].copy()
+    out, Kc = o.step_cells(f, cells)
+    assert np.array_equal(out, full.reshape(19, -1)[:, cells].T)
+    assert np.array_equal(Kc, K.reshape(-1)[cells])
