@@ -1,7 +1,7 @@
 """Build the CUDA library liblbm.so in-tree (paper_1507_06767_gb300/_build/).
 
 Each .cu translation unit is compiled for sm_103a in parallel, then linked into one shared library
-with the CUDA runtime linked statically.  Only the lbm_* C-ABI symbols are exported.
+with the CUDA runtime linked shared.  Only the lbm_* C-ABI symbols are exported.
 """
 from __future__ import annotations
 
@@ -65,7 +65,11 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        run([cc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs])
+        # the CUDA runtime is linked shared, so a process that also loads PyTorch's runtime keeps a
+        # single runtime instance (same soname)
+        cudalib = os.path.join(os.path.dirname(os.path.dirname(cc)), "lib64")
+        run([cc, *ARCH, "-shared", "-cudart", "shared", "-Xlinker", f"-rpath,{cudalib}", "-o", tmp,
+             *objs])
         os.replace(tmp, LIB)
     return LIB
 

@@ -320,8 +320,11 @@ class Lattice:
             self._bufs = None
 
     def __del__(self):
+        # at interpreter shutdown the module globals may already be gone; the process exit then
+        # releases the device memory anyway
         try:
-            self.close()
+            if self.h and _lib is not None:
+                self.close()
         except Exception:
             pass
 
@@ -341,14 +344,14 @@ class Lattice:
 
     def flag(self, threshold, block=None):
         if block is not None:
-            lbm_set_block(self.h, block)
+            self.block = block
         out = np.empty(lbm_nblocks(self.h, self.block), dtype=np.int8)
         lbm_flag(self.h, float(threshold), out)
         return out
 
     def flag_top(self, frac, block=None):
         if block is not None:
-            lbm_set_block(self.h, block)
+            self.block = block
         out = np.empty(lbm_nblocks(self.h, self.block), dtype=np.int8)
         lbm_flag_top(self.h, float(frac), out)
         return out

@@ -13,9 +13,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def L():
-    from paper_1507_06767_gb300 import build
+    import __graft_entry__
 
-    build.build()
+    __graft_entry__.build()
     import paper_1507_06767_gb300 as pkg
 
     return pkg
