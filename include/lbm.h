@@ -230,6 +230,39 @@ LBM_API int lbm_conservation(lbm_t *h, double *mass, double *mom3);
 LBM_API int lbm_kernel_time(lbm_t *h, double *ms_total, long long *launches);
 
 /*
+ * One fused step with the sensor, for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a deployment variant of lbm_step + lbm_sensor_dev.
+ *
+ * Who needs it: applications that serve all device memory from their own pool and do not let a
+ * library call cudaMalloc, and latency-critical loops that cannot afford an allocation (which may
+ * synchronise the device) after set-up.  This call allocates nothing: its scratch (the per-tile
+ * sensor maxima and the block maxima before conversion) lives in one fixed device array of the
+ * library, 2 * LBM_NOALLOC_MAX_TILES doubles (4 MiB), which every GPU that loads the library holds
+ * until the process exits.
+ *
+ * Arguments: lattice, dtype, nx, ny, nz, tau, the lid velocity (lid_x, lid_z) and the periodic
+ * mask mean what they mean for lbm_create / lbm_set_*.  f_in_dev holds the post-collision
+ * populations of the previous step in the storage layout of lbm.h (f[i][z][y][x] of type dtype);
+ * the new populations go to f_out_dev (same size, must not alias f_in_dev).  block (a positive
+ * multiple of LBM_TILE) is the block edge; block_max_dev receives ceil(nx/block) * ceil(ny/block) *
+ * ceil(nz/block) doubles (nz term 1 for D2Q9), the block maxima of this step's sensor.  All
+ * pointers are device memory of the calling thread's current device, owned by the caller; the work
+ * is queued on `stream` (a cudaStream_t, NULL for the legacy default stream) and the call returns
+ * without waiting.
+ *
+ * Limit: at most LBM_NOALLOC_MAX_TILES tiles of 8^d cells (512^3 D3Q19, 4096^2 D2Q9); a larger
+ * lattice gets LBM_EINVAL and a message naming the limit.  The first call on a device looks up the
+ * array's device address (once per device, with that device current); make that first call before
+ * any stream capture on the device.  Calls share the array and it keeps the last call's contents;
+ * nothing in it needs clearing, since each call writes every tile it reads.  Calls whose kernels
+ * overlap on the GPU race on the array: serialise them (one stream per process, or synchronise).
+ */
+#define LBM_NOALLOC_MAX_TILES 262144
+LBM_API int lbm_step_noalloc(int lattice, int dtype, int nx, int ny, int nz, double tau,
+                             double lid_x, double lid_z, int periodic, const void *f_in_dev,
+                             void *f_out_dev, int block, double *block_max_dev, void *stream);
+
+/*
  * Multi-level block batch (refinement ratio 2, level sub-cycling, f^neq rescaling at interfaces:
  * Sec. 2.1 and Sec. 5.2 describe the cell-centred block-structured scheme).  Not provided in this
  * version: returns LBM_ENOTSUP.

@@ -303,6 +303,13 @@ int sync(lbm_t *h) {
 
 }  // namespace
 
+namespace lbm {
+// Error reporting for the other C-ABI translation units (same thread-local state as this file).
+int report_error(int code, const char *msg) { return fail(code, "%s", msg); }
+int report_cuda_error(cudaError_t e, const char *what) { return cuda_fail(e, what); }
+void clear_error() { g_err = LBM_OK; }
+}  // namespace lbm
+
 extern "C" {
 
 LBM_API int lbm_last_error(void) { return g_err; }

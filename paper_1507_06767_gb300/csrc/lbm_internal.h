@@ -39,4 +39,9 @@ cudaError_t flags_threshold(int rtype, const void *maxima, int n, double T, int8
                             cudaStream_t s);
 cudaError_t flags_top(int rtype, const void *maxima, int n, int k, int8_t *out, cudaStream_t s);
 
+// Error state shared by the C-ABI translation units (lbm_api.cu).
+int report_error(int code, const char *msg);
+int report_cuda_error(cudaError_t e, const char *what);
+void clear_error();
+
 }  // namespace lbm

@@ -82,6 +82,7 @@ _SIGS = {
     "lbm_conservation": (_i, [_h, _dp, _dp]),
     "lbm_kernel_time": (_i, [_h, _dp, ctypes.POINTER(_ll)]),
     "lbm_blocks_step": (_i, [_h, _vp]),
+    "lbm_step_noalloc": (_i, [_i, _i, _i, _i, _i, _d, _d, _d, _i, _vp, _vp, _i, _vp, _vp]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -260,6 +261,16 @@ def lbm_kernel_time(h):
 
 def lbm_blocks_step(h, batch=None) -> int:
     return _ck(_lib.lbm_blocks_step(h, _ptr(batch)), "lbm_blocks_step")
+
+
+def lbm_step_noalloc(lattice, dtype, nx, ny, nz, tau, lid_x, lid_z, periodic, f_in_dev, f_out_dev,
+                     block, block_max_dev, stream=None) -> int:
+    """One fused step + block sensor maxima that allocates nothing (for callers that may not call
+    cudaMalloc); see include/lbm.h."""
+    s = stream if stream is None or isinstance(stream, int) else stream.cuda_stream
+    return _ck(_lib.lbm_step_noalloc(lattice, dtype, nx, ny, nz, tau, lid_x, lid_z, periodic,
+                                     _ptr(f_in_dev), _ptr(f_out_dev), block, _ptr(block_max_dev),
+                                     s), "lbm_step_noalloc")
 
 
 def exported_symbols():
