@@ -37,6 +37,13 @@ WORKLOADS = {
                                   rule="top", param=0.1, sensor_every=1),
     "d2q9_128_fp64_re100": dict(q=9, n=128, dtype="F64", re=100.0, u=0.1, block=16,
                                 rule="threshold", param=None, sensor_every=100),
+    # mixed precision: populations stored as f - w_i in 16 bits, arithmetic in FP32
+    "d3q19_512_f16s_re1000": dict(q=19, n=512, dtype="F16S", re=1000.0, u=0.1, block=16,
+                                  rule="top", param=0.1, sensor_every=1),
+    "d3q19_512_bf16s_re1000": dict(q=19, n=512, dtype="BF16S", re=1000.0, u=0.1, block=16,
+                                   rule="top", param=0.1, sensor_every=1),
+    "d3q19_512_fp32_re1000": dict(q=19, n=512, dtype="F32", re=1000.0, u=0.1, block=16,
+                                  rule="top", param=0.1, sensor_every=1),
 }
 DEFAULT_WORKLOAD = "d3q19_256_fp32_re1000"
 BYTES_PER_ELEM = {"F64": 8, "F32": 4, "F16S": 2, "BF16S": 2}

@@ -155,6 +155,14 @@ LBM_API int lbm_set_block(lbm_t *h, int block);
 /* on != 0: time every fused step kernel with CUDA events on the handle's stream (read with
  * lbm_kernel_time); turning it on clears the counters. */
 LBM_API int lbm_set_profiling(lbm_t *h, int on);
+/* Kernel variant of the fused step: LBM_KERNEL_AUTO (default) picks the fastest measured kernel that
+ * applies, LBM_KERNEL_CELL forces the one-cell kernel, LBM_KERNEL_PAIR the two-cell kernel with
+ * packed FP32 arithmetic (storage other than LBM_F64 and an even nx; LBM_EINVAL otherwise).  All
+ * compute the same step; they differ in rounding order only. */
+#define LBM_KERNEL_AUTO 0
+#define LBM_KERNEL_CELL 1
+#define LBM_KERNEL_PAIR 2
+LBM_API int lbm_set_kernel_variant(lbm_t *h, int variant);
 /* on != 0: lbm_step replays captured CUDA graphs for runs of steps (default on). */
 LBM_API int lbm_set_graphs(lbm_t *h, int on);
 

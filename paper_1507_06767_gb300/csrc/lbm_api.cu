@@ -68,6 +68,7 @@ struct lbm_s {
     int sensor_field = 0;
     int block = 16;
     int graphs = 1;
+    int variant = 0;  // LBM_KERNEL_*
 
     // population buffers
     void *buf[2] = {nullptr, nullptr};
@@ -191,8 +192,10 @@ cudaError_t launch_step(lbm_t *h, int src, int mode) {
     void *tiles = mode ? h->tiles : nullptr;
     void *kf = (mode == 2) ? h->kfield : nullptr;
     if (h->q == LBM_D2Q9)
-        return lbm::step_d2q9(h->dtype, h->buf[src], h->buf[src ^ 1], p, mode, tiles, kf, h->stream);
-    return lbm::step_d3q19(h->dtype, h->buf[src], h->buf[src ^ 1], p, mode, tiles, kf, h->stream);
+        return lbm::step_d2q9(h->dtype, h->buf[src], h->buf[src ^ 1], p, mode, tiles, kf, h->stream,
+                              h->variant);
+    return lbm::step_d3q19(h->dtype, h->buf[src], h->buf[src ^ 1], p, mode, tiles, kf, h->stream,
+                           h->variant);
 }
 
 int timed_step(lbm_t *h, int mode) {
@@ -239,9 +242,11 @@ int pair_graph(lbm_t *h, int src, cudaGraphExec_t *out) {
         for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
             const int s = src ^ k;
             if (h->q == LBM_D2Q9)
-                e = lbm::step_d2q9(h->dtype, h->buf[s], h->buf[s ^ 1], p, 0, nullptr, nullptr, cap);
+                e = lbm::step_d2q9(h->dtype, h->buf[s], h->buf[s ^ 1], p, 0, nullptr, nullptr, cap,
+                                   h->variant);
             else
-                e = lbm::step_d3q19(h->dtype, h->buf[s], h->buf[s ^ 1], p, 0, nullptr, nullptr, cap);
+                e = lbm::step_d3q19(h->dtype, h->buf[s], h->buf[s ^ 1], p, 0, nullptr, nullptr, cap,
+                                    h->variant);
         }
         cudaError_t e2 = cudaStreamEndCapture(cap, &g);
         if (e == cudaSuccess) e = e2;
@@ -463,6 +468,17 @@ LBM_API int lbm_set_profiling(lbm_t *h, int on) {
     CHECK_H(h);
     h->profiling = on ? 1 : 0;
     h->events_used = 0;
+    return LBM_OK;
+}
+
+LBM_API int lbm_set_kernel_variant(lbm_t *h, int variant) {
+    CHECK_H(h);
+    if (variant < LBM_KERNEL_AUTO || variant > LBM_KERNEL_PAIR)
+        return fail(LBM_EINVAL, "unknown kernel variant %d", variant);
+    if (variant == LBM_KERNEL_PAIR && (h->dtype == LBM_F64 || h->nx % 2 != 0))
+        return fail(LBM_EINVAL, "the two-cell kernel needs FP32 arithmetic and an even nx");
+    h->variant = variant;
+    drop_graphs(h);
     return LBM_OK;
 }
 

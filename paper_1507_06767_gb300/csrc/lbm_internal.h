@@ -10,10 +10,15 @@
 namespace lbm {
 
 // Fused step (lbm_step_d2q9.cu / lbm_step_d3q19.cu).  mode: 0 no sensor, 1 tile max, 2 + field.
+// variant: KERNEL_AUTO / KERNEL_CELL: the one-cell kernel; KERNEL_PAIR: the two-cell packed one
+// (error if it does not apply).
+constexpr int KERNEL_AUTO = 0;
+constexpr int KERNEL_CELL = 1;
+constexpr int KERNEL_PAIR = 2;
 cudaError_t step_d2q9(int dtype, const void *fin, void *fout, const StepParams &p, int mode,
-                      void *tile_max, void *k_field, cudaStream_t s);
+                      void *tile_max, void *k_field, cudaStream_t s, int variant = KERNEL_AUTO);
 cudaError_t step_d3q19(int dtype, const void *fin, void *fout, const StepParams &p, int mode,
-                       void *tile_max, void *k_field, cudaStream_t s);
+                       void *tile_max, void *k_field, cudaStream_t s, int variant = KERNEL_AUTO);
 
 // Population helpers (lbm_aux.cu).
 cudaError_t init_rest(int q, int dtype, void *f, size_t N, cudaStream_t s);

@@ -60,6 +60,7 @@ _SIGS = {
     "lbm_set_block": (_i, [_h, _i]),
     "lbm_set_profiling": (_i, [_h, _i]),
     "lbm_set_graphs": (_i, [_h, _i]),
+    "lbm_set_kernel_variant": (_i, [_h, _i]),
     "lbm_attach": (_i, [_h, _vp, _vp, _sz]),
     "lbm_population_bytes": (_sz, [_h]),
     "lbm_nblocks": (_i, [_h, _i]),
@@ -164,6 +165,7 @@ lbm_set_sensor_field = _wrap("lbm_set_sensor_field")
 lbm_set_block = _wrap("lbm_set_block")
 lbm_set_profiling = _wrap("lbm_set_profiling")
 lbm_set_graphs = _wrap("lbm_set_graphs")
+lbm_set_kernel_variant = _wrap("lbm_set_kernel_variant")
 lbm_reset = _wrap("lbm_reset")
 lbm_step = _wrap("lbm_step")
 

@@ -308,3 +308,46 @@ def test_profiling_counts_launches(L):
     ms, n = L.lbm_kernel_time(lat.h)
     assert n == 7 and ms > 0
     lat.close()
+
+
+# ----------------------------------------------------------------------------- kernel variants
+STORAGE_TOL = {  # populations (max|df|/max|f| after 3 steps), sensor field (relative to max K)
+    "F32": (2e-6, 1e-4),
+    "F16S": (1e-4, 2e-3),
+    "BF16S": (1e-3, 2e-2),
+}
+
+
+@pytest.mark.parametrize("dtype", ["F32", "F16S", "BF16S"])
+@pytest.mark.parametrize("q,dims,periodic", [(19, (34, 20, 18), 0), (19, (40, 12, 10), O.PERIODIC_Z),
+                                             (9, (66, 30, 1), 0)])
+def test_cell_and_pair_kernels_match_oracle(L, dtype, q, dims, periodic):
+    """The one-cell kernel and the two-cell packed kernel compute the same step: each matches the
+    oracle from the same storage-rounded input within the storage type's tolerance, and the two
+    agree with each other to a few FP32 roundings.  Shifted FP16 / BF16 storage (f - w_i) rounds
+    the deviation from rest to 11 / 8 significant bits per step; the tolerances above are those
+    roundings over 3 steps."""
+    dt = getattr(L, "LBM_" + dtype)
+    lid = (0.1, 0.0, 0.02 if q == 19 else 0.0)
+    o = O.Oracle(q, *dims, tau=0.6, lid=lid, periodic=periodic)
+    f0 = perturbed(o, seed=77 + q, amp=0.02)
+    res = {}
+    for variant in (L.LBM_KERNEL_CELL, L.LBM_KERNEL_PAIR):
+        lat = L.Lattice(q, *dims, 0.6, dtype=dt, lid=(lid[0], lid[2]), periodic=periodic)
+        L.lbm_set_kernel_variant(lat.h, variant)
+        L.lbm_set_sensor_field(lat.h, 1)
+        lat.set_populations(f0)
+        f_in = lat.populations()
+        lat.step(3)
+        res[variant] = (f_in, lat.populations(), lat.sensor_field(), lat.sensor(8))
+        lat.close()
+    tol_f, tol_k = STORAGE_TOL[dtype]
+    f_in = res[L.LBM_KERNEL_CELL][0]
+    assert np.array_equal(f_in, res[L.LBM_KERNEL_PAIR][0])
+    f_ref, K = o.run(f_in, 3, sensor_last=True)
+    for variant, (_, f, k, m) in res.items():
+        assert rel(f, f_ref) < tol_f, variant
+        assert rel(k, K) < tol_k, variant
+        assert rel(m, O.block_max(K, 8)) < tol_k, variant
+    fa, fb = res[L.LBM_KERNEL_CELL][1], res[L.LBM_KERNEL_PAIR][1]
+    assert rel(fa, fb) < tol_f
