@@ -157,11 +157,16 @@ LBM_API int lbm_set_block(lbm_t *h, int block);
 LBM_API int lbm_set_profiling(lbm_t *h, int on);
 /* Kernel variant of the fused step: LBM_KERNEL_AUTO (default) picks the fastest measured kernel that
  * applies, LBM_KERNEL_CELL forces the one-cell kernel, LBM_KERNEL_PAIR the two-cell kernel with
- * packed FP32 arithmetic (storage other than LBM_F64 and an even nx; LBM_EINVAL otherwise).  All
- * compute the same step; they differ in rounding order only. */
+ * packed FP32 arithmetic (storage other than LBM_F64 and an even nx), LBM_KERNEL_TMA the kernel that
+ * stages the populations through shared memory with TMA copies (D3Q19, storage other than LBM_F64,
+ * nx times the element size a multiple of 16 bytes); LBM_EINVAL where a variant does not apply.
+ * All compute the same step; they differ in rounding order only.  The TMA kernel's waits are
+ * bounded: if one runs out (it should not), the next synchronising call returns LBM_ETIMEOUT until
+ * lbm_reset. */
 #define LBM_KERNEL_AUTO 0
 #define LBM_KERNEL_CELL 1
 #define LBM_KERNEL_PAIR 2
+#define LBM_KERNEL_TMA 3
 LBM_API int lbm_set_kernel_variant(lbm_t *h, int variant);
 /* on != 0: lbm_step replays captured CUDA graphs for runs of steps (default on). */
 LBM_API int lbm_set_graphs(lbm_t *h, int on);
@@ -213,6 +218,34 @@ LBM_API int lbm_flag_top_dev(lbm_t *h, double frac, int8_t *out_dev);
  */
 LBM_API int lbm_flags_from_maxima(const void *maxima_dev, int maxima_dtype, int n, int rule,
                                   double param, int8_t *out_dev, void *stream);
+
+/*
+ * Time-averaged sensor (Sec. 5.1 builds its static mesh from the sensor averaged over one
+ * dimensionless period).  on != 0 clears the running sums and, from then on, adds the tile maxima
+ * of every sensor step; on == 0 stops adding (the sums are kept).  lbm_sensor_average writes, per
+ * block of edge `block`, the maximum over its tiles of the time-averaged tile maxima, and the
+ * number of sensor steps averaged (count may be NULL).  Synchronises; LBM_ESTATE before the first
+ * averaged sensor step.
+ */
+LBM_API int lbm_set_sensor_average(lbm_t *h, int on);
+LBM_API int lbm_sensor_average(lbm_t *h, int block, double *out_host, long long *count);
+
+/*
+ * Refinement levels per block (Sec. 3.4, Eqs. phi and l): phi = log2 K_max and
+ * l = clamp(floor(a * phi + b), lmin, lmax).  The paper writes the integral part [a phi]; this
+ * library reads it as the floor and adds an offset b (b = 0 is the paper's form); a > 0.  A block
+ * with K_max <= 0 gets lmin, a NaN block lmax.  lbm_levels_fit chooses a and b from the blocks'
+ * own range (finite K_max > 0): phi normalised to [0, 1] -- the normalised phi of the paper's
+ * figures -- maps onto [lmin, lmax + 1), so l = lmin + floor(phi_n (lmax - lmin + 1)), clamped;
+ * with fewer than two distinct values every block gets lmin.  source is LBM_SENSOR_LAST (block
+ * maxima of the last sensor step) or LBM_SENSOR_AVERAGE (time-averaged, see above).  Writes
+ * lbm_nblocks(h, block) int8 levels; synchronises.  Requires -128 <= lmin <= lmax <= 127.
+ */
+#define LBM_SENSOR_LAST 0
+#define LBM_SENSOR_AVERAGE 1
+LBM_API int lbm_levels(lbm_t *h, int block, double a, double b, int lmin, int lmax, int source,
+                       int8_t *out_host);
+LBM_API int lbm_levels_fit(lbm_t *h, int block, int lmin, int lmax, int source, int8_t *out_host);
 
 /* Populations as doubles, layout f[i][z][y][x] (q * N values).  get synchronises; set resets
  * nothing but the state (the step counter is kept). */

@@ -307,3 +307,61 @@ def flags_agree(flags, ref_maxima, rule: str, param: float, rel_tol: float):
     keep = ~near
     ok = bool(np.array_equal(flags[keep], ref[keep]))
     return ok, int(keep.sum()), int(near.sum())
+
+
+def levels_affine(maxima, a: float, b: float, lmin: int, lmax: int) -> np.ndarray:
+    """Refinement level per block from its sensor maximum (Sec. 3.4, Eqs. phi and l):
+    phi = log2(K), l = clamp(floor(a * phi + b), lmin, lmax).  The paper writes [a phi] for the
+    integral part; the reading here is the floor, with an offset b (b = 0 is the paper's form).
+    K <= 0 gives lmin, NaN gives lmax (a NaN block is refined, as by the flag rules)."""
+    out = np.empty(len(maxima), dtype=np.int8)
+    for k, m in enumerate(maxima):
+        m = float(m)
+        if math.isnan(m):
+            out[k] = lmax
+        elif m <= 0.0:
+            out[k] = lmin
+        else:
+            v = math.floor(a * math.log2(m) + b)
+            out[k] = max(lmin, min(lmax, v))
+    return out
+
+
+def levels_fit_params(maxima, lmin: int, lmax: int):
+    """The scale a and offset b that map the encountered range of phi = log2(K) (blocks with a
+    finite K > 0) linearly onto [lmin, lmax + 1): the normalised phi of the paper's figures
+    (Sec. 4, 'normalized phi'), phi_n = (phi - phi_min) / (phi_max - phi_min), gives
+    l = lmin + floor(phi_n (lmax - lmin + 1)), clamped.  Returns (a, b) or None if fewer than two
+    distinct values exist (all blocks then get lmin)."""
+    phis = [math.log2(float(m)) for m in maxima if float(m) > 0.0 and math.isfinite(float(m))]
+    if not phis:
+        return None
+    lo, hi = min(phis), max(phis)
+    if not hi > lo:
+        return None
+    a = float(lmax - lmin + 1) / (hi - lo)
+    b = float(lmin) - a * lo
+    return a, b
+
+
+def levels_fit(maxima, lmin: int, lmax: int) -> np.ndarray:
+    ab = levels_fit_params(maxima, lmin, lmax)
+    if ab is None:
+        out = np.full(len(maxima), lmin, dtype=np.int8)
+        out[np.isnan(np.asarray(maxima, dtype=np.float64))] = lmax
+        return out
+    return levels_affine(maxima, ab[0], ab[1], lmin, lmax)
+
+
+def levels_agree(levels, maxima, a, b, rel_band: float):
+    """Compare levels computed elsewhere with levels_affine, ignoring blocks whose a*log2(K) + b lies
+    within rel_band of an integer (log2 implementations may differ in the last bit)."""
+    ref = levels_affine(maxima, a, b, -128, 127)
+    keep = np.ones(len(ref), dtype=bool)
+    for k, m in enumerate(maxima):
+        m = float(m)
+        if m > 0.0 and math.isfinite(m):
+            v = a * math.log2(m) + b
+            if abs(v - round(v)) <= rel_band * max(1.0, abs(v)):
+                keep[k] = False
+    return keep

@@ -78,13 +78,18 @@ struct lbm_s {
     // sensor scratch: tile maxima of the last sensor step, block maxima, flags
     int ntx = 0, nty = 0, ntz = 0;
     size_t ntiles = 0;
-    void *tiles = nullptr;
+    void *tiles = nullptr;        // tile maxima of the most recent sensor step (one of tilebuf)
+    void *tilebuf[2] = {nullptr, nullptr};
+    int tile_next = 0;            // buffer the next sensor step writes; it clears the other
     void *blocks = nullptr;
     double *blocks_f64 = nullptr;
     int8_t *flags = nullptr;
     void *kfield = nullptr;
     double *cons_partial = nullptr;
     double *cons_result = nullptr;
+    // error word of the kernels' bounded waits: pinned host memory mapped into the device
+    int *err_host = nullptr;
+    int *err_dev = nullptr;
     double *staging = nullptr;  // staging_cap >= max(N, 64) doubles, for host transfers in double
     size_t staging_cap = 0;
     bool scratch_ready = false;
@@ -92,6 +97,12 @@ struct lbm_s {
     long long t = 0;
     bool have_sensor = false;
     bool have_kfield = false;
+
+    // time average of the tile maxima over sensor steps
+    bool averaging = false;
+    long long avg_count = 0;
+    double *tile_sum = nullptr;
+    double *tile_avg = nullptr;
 
     // profiling
     int profiling = 0;
@@ -130,19 +141,29 @@ StepParams params_of(const lbm_t *h) {
     p.omega = 1.0 / h->tau;
     p.lid_x = h->lid_x;
     p.lid_z = h->lid_z;
+    p.err = h->err_dev;
+    p.tile_zero = nullptr;
     return p;
 }
 
 int ensure_scratch(lbm_t *h) {
     if (h->scratch_ready) return LBM_OK;
     CK(cudaSetDevice(h->device), "cudaSetDevice");
-    CK(cudaMalloc(&h->tiles, h->ntiles * h->rsize()), "cudaMalloc(tiles)");
+    CK(cudaMalloc(&h->tilebuf[0], h->ntiles * h->rsize()), "cudaMalloc(tiles)");
+    CK(cudaMalloc(&h->tilebuf[1], h->ntiles * h->rsize()), "cudaMalloc(tiles)");
+    CK(cudaMemset(h->tilebuf[0], 0, h->ntiles * h->rsize()), "cudaMemset(tiles)");
+    CK(cudaMemset(h->tilebuf[1], 0, h->ntiles * h->rsize()), "cudaMemset(tiles)");
+    h->tiles = h->tilebuf[0];
+    h->tile_next = 0;
     CK(cudaMalloc(&h->blocks, h->ntiles * h->rsize()), "cudaMalloc(blocks)");
     CK(cudaMalloc((void **)&h->blocks_f64, h->ntiles * sizeof(double)), "cudaMalloc(blocks_f64)");
     CK(cudaMalloc((void **)&h->flags, h->ntiles), "cudaMalloc(flags)");
     CK(cudaMalloc((void **)&h->cons_partial, lbm::CONS_PARTS * 5 * sizeof(double)),
        "cudaMalloc(partial)");
     CK(cudaMalloc((void **)&h->cons_result, 8 * sizeof(double)), "cudaMalloc(result)");
+    CK(cudaHostAlloc((void **)&h->err_host, sizeof(int), cudaHostAllocMapped), "cudaHostAlloc(err)");
+    *h->err_host = 0;
+    CK(cudaHostGetDevicePointer((void **)&h->err_dev, h->err_host, 0), "cudaHostGetDevicePointer");
     h->scratch_ready = true;
     return LBM_OK;
 }
@@ -188,8 +209,9 @@ int ensure_kfield(lbm_t *h) {
 }
 
 cudaError_t launch_step(lbm_t *h, int src, int mode) {
-    const StepParams p = params_of(h);
-    void *tiles = mode ? h->tiles : nullptr;
+    StepParams p = params_of(h);
+    void *tiles = mode ? h->tilebuf[h->tile_next] : nullptr;
+    if (mode) p.tile_zero = h->tilebuf[h->tile_next ^ 1];
     void *kf = (mode == 2) ? h->kfield : nullptr;
     if (h->q == LBM_D2Q9)
         return lbm::step_d2q9(h->dtype, h->buf[src], h->buf[src ^ 1], p, mode, tiles, kf, h->stream,
@@ -217,8 +239,15 @@ int timed_step(lbm_t *h, int mode) {
     h->cur ^= 1;
     h->t += 1;
     if (mode) {
+        h->tiles = h->tilebuf[h->tile_next];
+        h->tile_next ^= 1;
         h->have_sensor = true;
         h->have_kfield = (mode == 2);
+        if (h->averaging) {
+            CK(lbm::accumulate_tiles(h->rtype(), h->tiles, h->tile_sum, h->ntiles, h->stream),
+               "accumulate_tiles");
+            h->avg_count += 1;
+        }
     }
     return LBM_OK;
 }
@@ -298,6 +327,9 @@ int top_count(double frac, int n) {
 
 int sync(lbm_t *h) {
     CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    if (h->err_host && *(volatile int *)h->err_host)
+        return fail(LBM_ETIMEOUT, "a bounded wait in the fused step kernel ran out; results of the "
+                                  "steps since the last reset are not valid");
     return LBM_OK;
 }
 
@@ -390,7 +422,8 @@ LBM_API int lbm_destroy(lbm_t *h) {
         cudaFree(h->buf[0]);
         cudaFree(h->buf[1]);
     }
-    cudaFree(h->tiles);
+    cudaFree(h->tilebuf[0]);
+    cudaFree(h->tilebuf[1]);
     cudaFree(h->blocks);
     cudaFree(h->blocks_f64);
     cudaFree(h->flags);
@@ -398,6 +431,9 @@ LBM_API int lbm_destroy(lbm_t *h) {
     cudaFree(h->cons_partial);
     cudaFree(h->cons_result);
     cudaFree(h->staging);
+    cudaFree(h->tile_sum);
+    cudaFree(h->tile_avg);
+    if (h->err_host) cudaFreeHost(h->err_host);
     delete h;
     return LBM_OK;
 }
@@ -473,10 +509,16 @@ LBM_API int lbm_set_profiling(lbm_t *h, int on) {
 
 LBM_API int lbm_set_kernel_variant(lbm_t *h, int variant) {
     CHECK_H(h);
-    if (variant < LBM_KERNEL_AUTO || variant > LBM_KERNEL_PAIR)
+    if (variant < LBM_KERNEL_AUTO || variant > LBM_KERNEL_TMA)
         return fail(LBM_EINVAL, "unknown kernel variant %d", variant);
     if (variant == LBM_KERNEL_PAIR && (h->dtype == LBM_F64 || h->nx % 2 != 0))
         return fail(LBM_EINVAL, "the two-cell kernel needs FP32 arithmetic and an even nx");
+    if (variant == LBM_KERNEL_TMA &&
+        (h->q != LBM_D3Q19 || h->dtype == LBM_F64 ||
+         (long long)h->nx * (h->dtype == LBM_F32 ? 4 : 2) % 16 != 0))
+        return fail(LBM_EINVAL,
+                    "the TMA kernel needs D3Q19, 16- or 32-bit storage and rows of a multiple of "
+                    "16 bytes");
     h->variant = variant;
     drop_graphs(h);
     return LBM_OK;
@@ -532,6 +574,12 @@ LBM_API int lbm_reset(lbm_t *h) {
     h->t = 0;
     h->have_sensor = false;
     h->have_kfield = false;
+    CK(cudaMemsetAsync(h->tilebuf[0], 0, h->ntiles * h->rsize(), h->stream), "memset(tiles)");
+    CK(cudaMemsetAsync(h->tilebuf[1], 0, h->ntiles * h->rsize(), h->stream), "memset(tiles)");
+    h->tiles = h->tilebuf[0];
+    h->tile_next = 0;
+    CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    *h->err_host = 0;
     return LBM_OK;
 }
 
@@ -800,6 +848,92 @@ LBM_API int lbm_kernel_time(lbm_t *h, double *ms_total, long long *launches) {
     *launches = (long long)(h->events_used / 2);
     h->events_used = 0;
     return LBM_OK;
+}
+
+LBM_API int lbm_set_sensor_average(lbm_t *h, int on) {
+    CHECK_H(h);
+    int st = ensure_scratch(h);
+    if (st != LBM_OK) return st;
+    if (on) {
+        if (!h->tile_sum) {
+            CK(cudaMalloc((void **)&h->tile_sum, h->ntiles * sizeof(double)), "cudaMalloc(sum)");
+            CK(cudaMalloc((void **)&h->tile_avg, h->ntiles * sizeof(double)), "cudaMalloc(avg)");
+        }
+        CK(cudaMemsetAsync(h->tile_sum, 0, h->ntiles * sizeof(double), h->stream), "memset");
+        h->avg_count = 0;
+    }
+    h->averaging = on != 0;
+    return LBM_OK;
+}
+
+// Block maxima of the time-averaged tile maxima into h->blocks_f64.
+static int average_blocks(lbm_t *h, int block, int *nb_out) {
+    if (!h->tile_sum || h->avg_count == 0)
+        return fail(LBM_ESTATE, "no sensor step averaged (lbm_set_sensor_average, then step)");
+    int nbx, nby, nbz, m, mz;
+    int st = check_block(h, block, &nbx, &nby, &nbz, &m, &mz);
+    if (st != LBM_OK) return st;
+    CK(lbm::scale_f64(h->tile_sum, 1.0 / (double)h->avg_count, h->tile_avg, h->ntiles, h->stream),
+       "scale");
+    CK(lbm::tiles_to_blocks(LBM_F64, h->tile_avg, h->ntx, h->nty, h->ntz, m, mz, h->blocks_f64,
+                            nbx, nby, nbz, h->stream),
+       "tiles_to_blocks");
+    *nb_out = nbx * nby * nbz;
+    return LBM_OK;
+}
+
+LBM_API int lbm_sensor_average(lbm_t *h, int block, double *out_host, long long *count) {
+    CHECK_H(h);
+    if (!out_host) return fail(LBM_EINVAL, "NULL output");
+    int nb = 0;
+    int st = average_blocks(h, block, &nb);
+    if (st != LBM_OK) return st;
+    CK(cudaMemcpyAsync(out_host, h->blocks_f64, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost,
+                       h->stream),
+       "cudaMemcpyAsync");
+    if (count) *count = h->avg_count;
+    return sync(h);
+}
+
+static int levels_common(lbm_t *h, int block, bool fit, double a, double b, int lmin, int lmax,
+                         int source, int8_t *out_host) {
+    CHECK_H(h);
+    if (!out_host) return fail(LBM_EINVAL, "NULL output");
+    if (lmin < -128 || lmax > 127 || lmin > lmax)
+        return fail(LBM_EINVAL, "need -128 <= lmin <= lmax <= 127");
+    if (!fit && (!(a > 0.0) || !isfinite(a) || !isfinite(b)))
+        return fail(LBM_EINVAL, "scale a must be finite and > 0, offset b finite");
+    if (source != LBM_SENSOR_LAST && source != LBM_SENSOR_AVERAGE)
+        return fail(LBM_EINVAL, "unknown sensor source %d", source);
+    int nb = 0, st;
+    const void *maxima;
+    int rtype;
+    if (source == LBM_SENSOR_LAST) {
+        st = reduce_blocks(h, block, &nb);
+        maxima = h->blocks;
+        rtype = h->rtype();
+    } else {
+        st = average_blocks(h, block, &nb);
+        maxima = h->blocks_f64;
+        rtype = LBM_F64;
+    }
+    if (st != LBM_OK) return st;
+    if (fit)
+        CK(lbm::levels_fit(rtype, maxima, nb, lmin, lmax, h->flags, h->stream), "levels_fit");
+    else
+        CK(lbm::levels_affine(rtype, maxima, nb, a, b, lmin, lmax, h->flags, h->stream), "levels");
+    CK(cudaMemcpyAsync(out_host, h->flags, (size_t)nb, cudaMemcpyDeviceToHost, h->stream),
+       "cudaMemcpyAsync");
+    return sync(h);
+}
+
+LBM_API int lbm_levels(lbm_t *h, int block, double a, double b, int lmin, int lmax, int source,
+                       int8_t *out_host) {
+    return levels_common(h, block, false, a, b, lmin, lmax, source, out_host);
+}
+
+LBM_API int lbm_levels_fit(lbm_t *h, int block, int lmin, int lmax, int source, int8_t *out_host) {
+    return levels_common(h, block, true, 0.0, 0.0, lmin, lmax, source, out_host);
 }
 
 LBM_API int lbm_blocks_step(lbm_t *h, const lbm_level_batch *batch) {

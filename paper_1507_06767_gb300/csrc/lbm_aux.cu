@@ -274,6 +274,74 @@ __global__ void __launch_bounds__(TOP_THREADS) k_flags_top(const R *m, int n, in
     }
 }
 
+// Refinement level of one block maximum (Sec. 3.4): phi = log2 K, l = clamp(floor(a phi + b)).
+__device__ __forceinline__ int8_t level_of(double v, double a, double b, int lmin, int lmax) {
+    if (isnan(v)) return (int8_t)lmax;
+    if (!(v > 0.0)) return (int8_t)lmin;
+    double t = floor(a * log2(v) + b);
+    t = fmin(fmax(t, (double)lmin), (double)lmax);
+    return (int8_t)(int)t;
+}
+
+template <class R>
+__global__ void k_levels_affine(const R *m, int n, double a, double b, int lmin, int lmax,
+                                int8_t *out) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+        out[k] = level_of((double)m[k], a, b, lmin, lmax);
+}
+
+// Single CTA: fit a, b to the range of phi over the blocks with a finite K > 0, then map.
+template <class R>
+__global__ void __launch_bounds__(1024) k_levels_fit(const R *m, int n, int lmin, int lmax,
+                                                     int8_t *out) {
+    __shared__ double slo[1024], shi[1024];
+    double lo = INFINITY, hi = -INFINITY;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const double v = (double)m[k];
+        if (v > 0.0 && isfinite(v)) {
+            const double ph = log2(v);
+            lo = fmin(lo, ph);
+            hi = fmax(hi, ph);
+        }
+    }
+    slo[threadIdx.x] = lo;
+    shi[threadIdx.x] = hi;
+    __syncthreads();
+    for (int st = 512; st > 0; st >>= 1) {
+        if (threadIdx.x < st) {
+            slo[threadIdx.x] = fmin(slo[threadIdx.x], slo[threadIdx.x + st]);
+            shi[threadIdx.x] = fmax(shi[threadIdx.x], shi[threadIdx.x + st]);
+        }
+        __syncthreads();
+    }
+    lo = slo[0];
+    hi = shi[0];
+    const bool scale = hi > lo;
+    const double a = scale ? (double)(lmax - lmin + 1) / (hi - lo) : 0.0;
+    const double b = scale ? (double)lmin - a * lo : 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const double v = (double)m[k];
+        out[k] = scale ? level_of(v, a, b, lmin, lmax)
+                       : (isnan(v) ? (int8_t)lmax : (int8_t)lmin);
+    }
+}
+
+__global__ void k_accumulate_tiles_f(const float *t, double *sum, size_t n) {
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x)
+        sum[k] += (double)t[k];
+}
+__global__ void k_accumulate_tiles_d(const double *t, double *sum, size_t n) {
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x)
+        sum[k] += t[k];
+}
+__global__ void k_scale(const double *sum, double inv, double *out, size_t n) {
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x)
+        out[k] = sum[k] * inv;
+}
+
 __global__ void k_fill_i8(int8_t *out, int n, int8_t v) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
         out[k] = v;
@@ -398,6 +466,43 @@ cudaError_t flags_top(int rtype, const void *maxima, int n, int k, int8_t *out, 
     else
         k_flags_top<float, uint32_t><<<1, TOP_THREADS, 0, s>>>(static_cast<const float *>(maxima),
                                                               n, k, out);
+    return cudaGetLastError();
+}
+
+cudaError_t levels_affine(int rtype, const void *maxima, int n, double a, double b, int lmin,
+                          int lmax, int8_t *out, cudaStream_t s) {
+    const unsigned g = small_grid(n, 256);
+    if (rtype == 0)
+        k_levels_affine<double><<<g, 256, 0, s>>>(static_cast<const double *>(maxima), n, a, b, lmin,
+                                                  lmax, out);
+    else
+        k_levels_affine<float><<<g, 256, 0, s>>>(static_cast<const float *>(maxima), n, a, b, lmin,
+                                                 lmax, out);
+    return cudaGetLastError();
+}
+
+cudaError_t levels_fit(int rtype, const void *maxima, int n, int lmin, int lmax, int8_t *out,
+                       cudaStream_t s) {
+    if (rtype == 0)
+        k_levels_fit<double><<<1, 1024, 0, s>>>(static_cast<const double *>(maxima), n, lmin, lmax,
+                                                out);
+    else
+        k_levels_fit<float><<<1, 1024, 0, s>>>(static_cast<const float *>(maxima), n, lmin, lmax,
+                                               out);
+    return cudaGetLastError();
+}
+
+cudaError_t accumulate_tiles(int rtype, const void *tiles, double *sum, size_t n, cudaStream_t s) {
+    const unsigned g = small_grid((long long)n, 256);
+    if (rtype == 0)
+        k_accumulate_tiles_d<<<g, 256, 0, s>>>(static_cast<const double *>(tiles), sum, n);
+    else
+        k_accumulate_tiles_f<<<g, 256, 0, s>>>(static_cast<const float *>(tiles), sum, n);
+    return cudaGetLastError();
+}
+
+cudaError_t scale_f64(const double *in, double factor, double *out, size_t n, cudaStream_t s) {
+    k_scale<<<small_grid((long long)n, 256), 256, 0, s>>>(in, factor, out, n);
     return cudaGetLastError();
 }
 

@@ -10,11 +10,12 @@
 namespace lbm {
 
 // Fused step (lbm_step_d2q9.cu / lbm_step_d3q19.cu).  mode: 0 no sensor, 1 tile max, 2 + field.
-// variant: KERNEL_AUTO / KERNEL_CELL: the one-cell kernel; KERNEL_PAIR: the two-cell packed one
-// (error if it does not apply).
+// variant: KERNEL_AUTO / KERNEL_CELL: the one-cell kernel; KERNEL_PAIR: the two-cell packed one;
+// KERNEL_TMA: the TMA-staged one (D3Q19 only); the last two are errors where they do not apply.
 constexpr int KERNEL_AUTO = 0;
 constexpr int KERNEL_CELL = 1;
 constexpr int KERNEL_PAIR = 2;
+constexpr int KERNEL_TMA = 3;
 cudaError_t step_d2q9(int dtype, const void *fin, void *fout, const StepParams &p, int mode,
                       void *tile_max, void *k_field, cudaStream_t s, int variant = KERNEL_AUTO);
 cudaError_t step_d3q19(int dtype, const void *fin, void *fout, const StepParams &p, int mode,
@@ -43,6 +44,15 @@ cudaError_t to_f64(int rtype, const void *in, double *out, size_t n, cudaStream_
 cudaError_t flags_threshold(int rtype, const void *maxima, int n, double T, int8_t *out,
                             cudaStream_t s);
 cudaError_t flags_top(int rtype, const void *maxima, int n, int k, int8_t *out, cudaStream_t s);
+
+// Level map (Sec. 3.4) of n block maxima, affine (a, b given) or fitted to their range.
+cudaError_t levels_affine(int rtype, const void *maxima, int n, double a, double b, int lmin,
+                          int lmax, int8_t *out, cudaStream_t s);
+cudaError_t levels_fit(int rtype, const void *maxima, int n, int lmin, int lmax, int8_t *out,
+                       cudaStream_t s);
+// Time average of the tile maxima: sum += tiles; out = sum * factor.
+cudaError_t accumulate_tiles(int rtype, const void *tiles, double *sum, size_t n, cudaStream_t s);
+cudaError_t scale_f64(const double *in, double factor, double *out, size_t n, cudaStream_t s);
 
 // Error state shared by the C-ABI translation units (lbm_api.cu).
 int report_error(int code, const char *msg);

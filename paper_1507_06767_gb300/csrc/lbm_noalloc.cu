@@ -101,10 +101,15 @@ extern "C" LBM_API int lbm_step_noalloc(int lattice, int dtype, int nx, int ny, 
     p.omega = 1.0 / tau;
     p.lid_x = lid_x;
     p.lid_z = lid_z;
+    p.err = nullptr;
+    p.tile_zero = nullptr;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the one-cell kernel writes every tile maximum with a plain store, so the scratch needs no
+    // clearing between calls
     e = (lattice == LBM_D2Q9)
-            ? lbm::step_d2q9(dtype, f_in_dev, f_out_dev, p, 1, tiles, nullptr, s)
-            : lbm::step_d3q19(dtype, f_in_dev, f_out_dev, p, 1, tiles, nullptr, s);
+            ? lbm::step_d2q9(dtype, f_in_dev, f_out_dev, p, 1, tiles, nullptr, s, lbm::KERNEL_CELL)
+            : lbm::step_d3q19(dtype, f_in_dev, f_out_dev, p, 1, tiles, nullptr, s,
+                              lbm::KERNEL_CELL);
     if (e != cudaSuccess) return lbm::report_cuda_error(e, "fused step launch");
     const int m = block / LBM_TILE, mz = (dim == 3) ? m : 1;
     const int nbx = (nx + block - 1) / block, nby = (ny + block - 1) / block;

@@ -61,6 +61,102 @@ __device__ __forceinline__ void store_pop(T *p, T v) {
 #endif
 }
 
+// Pull-gather of cell (x, y, z) in the general case (walls with moving-lid bounce-back, periodic
+// wrap): writes the deviations from rest df_i = f_i - w_i of the populations arriving at the cell.
+template <class L, int DT>
+__device__ __forceinline__ void gather_cell(const typename Storage<DT>::T *__restrict__ fin,
+                                            const StepParams &p, size_t N, int x, int y, int z,
+                                            typename Storage<DT>::R *df) {
+    using S = Storage<DT>;
+    using R = typename S::R;
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const bool perx = p.periodic & 1, pery = p.periodic & 2, perz = p.periodic & 4;
+    // source coordinates x - c for c = +1 (xm) and c = -1 (xp), with their validity
+    const int xm = (x == 0) ? nx - 1 : x - 1;
+    const int xp = (x == nx - 1) ? 0 : x + 1;
+    const bool vxm = (x > 0) || perx;
+    const bool vxp = (x < nx - 1) || perx;
+    const int ym = (y == 0) ? ny - 1 : y - 1;
+    const int yp = (y == ny - 1) ? 0 : y + 1;
+    const bool vym = (y > 0) || pery;
+    const bool vyp = (y < ny - 1) || pery;  // false <=> the y+1 ghost is the lid
+    int zm = z, zp = z;
+    bool vzm = true, vzp = true;
+    if (L::D == 3) {
+        zm = (z == 0) ? nz - 1 : z - 1;
+        zp = (z == nz - 1) ? 0 : z + 1;
+        vzm = (z > 0) || perz;
+        vzp = (z < nz - 1) || perz;
+    }
+    const int idx = (z * ny + y) * nx + x;
+    const R lidx = (R)p.lid_x, lidz = (R)p.lid_z;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+        const int sx = cx == 1 ? xm : (cx == -1 ? xp : x);
+        const int sy = cy == 1 ? ym : (cy == -1 ? yp : y);
+        const int sz = cz == 1 ? zm : (cz == -1 ? zp : z);
+        const bool valid = (cx == 1 ? vxm : (cx == -1 ? vxp : true)) &&
+                           (cy == 1 ? vym : (cy == -1 ? vyp : true)) &&
+                           (cz == 1 ? vzm : (cz == -1 ? vzp : true));
+        const size_t src = valid ? (size_t)i * N + (size_t)((sz * ny + sy) * nx + sx)
+                                 : (size_t)L::opp(i) * N + (size_t)idx;
+        R v = S::to_r(load_pop(fin + src));
+        if (!S::SHIFTED) v -= weight<L, R>(i);  // w_opp(i) == w_i
+        if (cy == -1 && !vyp) {
+            // moving lid: + 2 w_i (c_i . u_lid) / c_s^2, wall density 1
+            v += R(6) * weight<L, R>(i) * (R(cx) * lidx + R(cz) * lidz);
+        }
+        df[i] = v;
+    }
+}
+
+// Moments, equilibrium, sensor and BGK collision of one cell from its gathered deviations df, and
+// the store of the post-collision populations at linear index idx.  Returns the sensor K (MODE != 0).
+template <class L, int DT, int MODE>
+__device__ __forceinline__ typename Storage<DT>::R relax_store_cell(
+    const typename Storage<DT>::R *df, typename Storage<DT>::R omega,
+    typename Storage<DT>::T *__restrict__ fout, size_t N, int idx) {
+    using S = Storage<DT>;
+    using R = typename S::R;
+    constexpr int Q = L::Q;
+    // moments as deviations from rest
+    R drho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        drho += df[i];
+        if (L::cx(i)) jx += R(L::cx(i)) * df[i];
+        if (L::cy(i)) jy += R(L::cy(i)) * df[i];
+        if (L::cz(i)) jz += R(L::cz(i)) * df[i];
+    }
+    const R rho = R(1) + drho;
+    const R inv_rho = R(1) / rho;
+    const R ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
+    const R usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
+
+    R ksum = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const R cu = R(L::cx(i)) * ux + R(L::cy(i)) * uy + R(L::cz(i)) * uz;
+        // P_i = c.u / cs2 + ((c.u)^2 - cs2 u.u) / (2 cs2^2)
+        const R P = R(3) * cu + R(4.5) * cu * cu - usq15;
+        const R w = weight<L, R>(i);
+        const R dfeq = w * (drho + rho * P);  // f^eq_i - w_i
+        const R fneq = df[i] - dfeq;
+        if (MODE != 0) {
+            const R feq = w * rho * (R(1) + P);
+            if constexpr (sizeof(R) == 4) {
+                ksum += __fdividef(fabsf(fneq), feq);
+            } else {
+                ksum += fabs(fneq) / feq;
+            }
+        }
+        const R dnew = df[i] - omega * fneq;
+        store_pop(fout + (size_t)i * N + idx, S::from_r(S::SHIFTED ? dnew : dnew + w));
+    }
+    return ksum * (R(1) / R(Q));
+}
+
 // MODE 0: no sensor.  MODE 1: sensor and per-tile max.  MODE 2: MODE 1 plus per-cell K.
 template <class L, int DT, int MODE>
 __global__ void __launch_bounds__(CTA_X *CTA_Y, LBM_STEP_MIN_BLOCKS)
@@ -69,7 +165,6 @@ __global__ void __launch_bounds__(CTA_X *CTA_Y, LBM_STEP_MIN_BLOCKS)
                       typename Storage<DT>::R *__restrict__ tile_max,
                       typename Storage<DT>::R *__restrict__ k_field) {
     using S = Storage<DT>;
-    using T = typename S::T;
     using R = typename S::R;
     using B = typename Bits<R>::type;
     constexpr int Q = L::Q;
@@ -82,20 +177,18 @@ __global__ void __launch_bounds__(CTA_X *CTA_Y, LBM_STEP_MIN_BLOCKS)
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const bool active = (x < nx) && (y < ny);
     const size_t N = (size_t)nx * ny * nz;
-
-    const bool perx = p.periodic & 1, pery = p.periodic & 2, perz = p.periodic & 4;
-    // source coordinates x - c for c = +1 (xm) and c = -1 (xp), with their validity
-    const int xm = (x == 0) ? nx - 1 : x - 1;
-    const int xp = (x == nx - 1) ? 0 : x + 1;
-    const bool vxm = (x > 0) || perx;
-    const bool vxp = (x < nx - 1) || perx;
-    const int ym = (y == 0) ? ny - 1 : y - 1;
-    const int yp = (y == ny - 1) ? 0 : y + 1;
-    const bool vym = (y > 0) || pery;
-    const bool vyp = (y < ny - 1) || pery;  // false <=> the y+1 ghost is the lid
-
     const R omega = (R)p.omega;
-    const R lidx = (R)p.lid_x, lidz = (R)p.lid_z;
+
+    // clear the other tile buffer for the next sensor step (kernels that combine tiles across
+    // CTAs with atomics need it zeroed)
+    if (MODE != 0 && p.tile_zero) {
+        const size_t nt = (size_t)p.ntx * p.nty * p.ntz;
+        const size_t nthreads = (size_t)gridDim.x * gridDim.y * gridDim.z * blockDim.x * blockDim.y;
+        const size_t me = (((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) *
+                              (blockDim.x * blockDim.y) +
+                          threadIdx.y * blockDim.x + threadIdx.x;
+        for (size_t k = me; k < nt; k += nthreads) static_cast<R *>(p.tile_zero)[k] = R(0);
+    }
 
     B kmax = 0;
 
@@ -103,73 +196,11 @@ __global__ void __launch_bounds__(CTA_X *CTA_Y, LBM_STEP_MIN_BLOCKS)
         const int z = z0 + dz;
         if (z >= nz) break;
         if (active) {
-            int zm = z, zp = z;
-            bool vzm = true, vzp = true;
-            if (L::D == 3) {
-                zm = (z == 0) ? nz - 1 : z - 1;
-                zp = (z == nz - 1) ? 0 : z + 1;
-                vzm = (z > 0) || perz;
-                vzp = (z < nz - 1) || perz;
-            }
             const int idx = (z * ny + y) * nx + x;
-
             R df[Q];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-                const int sx = cx == 1 ? xm : (cx == -1 ? xp : x);
-                const int sy = cy == 1 ? ym : (cy == -1 ? yp : y);
-                const int sz = cz == 1 ? zm : (cz == -1 ? zp : z);
-                const bool valid = (cx == 1 ? vxm : (cx == -1 ? vxp : true)) &&
-                                   (cy == 1 ? vym : (cy == -1 ? vyp : true)) &&
-                                   (cz == 1 ? vzm : (cz == -1 ? vzp : true));
-                const size_t src = valid ? (size_t)i * N + (size_t)((sz * ny + sy) * nx + sx)
-                                         : (size_t)L::opp(i) * N + (size_t)idx;
-                R v = S::to_r(load_pop(fin + src));
-                if (!S::SHIFTED) v -= weight<L, R>(i);  // w_opp(i) == w_i
-                if (cy == -1 && !vyp) {
-                    // moving lid: + 2 w_i (c_i . u_lid) / c_s^2, wall density 1
-                    v += R(6) * weight<L, R>(i) * (R(cx) * lidx + R(cz) * lidz);
-                }
-                df[i] = v;
-            }
-
-            // moments as deviations from rest
-            R drho = 0, jx = 0, jy = 0, jz = 0;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                drho += df[i];
-                if (L::cx(i)) jx += R(L::cx(i)) * df[i];
-                if (L::cy(i)) jy += R(L::cy(i)) * df[i];
-                if (L::cz(i)) jz += R(L::cz(i)) * df[i];
-            }
-            const R rho = R(1) + drho;
-            const R inv_rho = R(1) / rho;
-            const R ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
-            const R usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
-
-            R ksum = 0;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const R cu = R(L::cx(i)) * ux + R(L::cy(i)) * uy + R(L::cz(i)) * uz;
-                // P_i = c.u / cs2 + ((c.u)^2 - cs2 u.u) / (2 cs2^2)
-                const R P = R(3) * cu + R(4.5) * cu * cu - usq15;
-                const R w = weight<L, R>(i);
-                const R dfeq = w * (drho + rho * P);  // f^eq_i - w_i
-                const R fneq = df[i] - dfeq;
-                if (MODE != 0) {
-                    const R feq = w * rho * (R(1) + P);
-                    if constexpr (sizeof(R) == 4) {
-                        ksum += __fdividef(fabsf(fneq), feq);
-                    } else {
-                        ksum += fabs(fneq) / feq;
-                    }
-                }
-                const R dnew = df[i] - omega * fneq;
-                store_pop(fout + (size_t)i * N + idx, S::from_r(S::SHIFTED ? dnew : dnew + w));
-            }
+            gather_cell<L, DT>(fin, p, N, x, y, z, df);
+            const R K = relax_store_cell<L, DT, MODE>(df, omega, fout, N, idx);
             if (MODE != 0) {
-                const R K = ksum * (R(1) / R(Q));
                 const B kb = max_bits(K);
                 kmax = kb > kmax ? kb : kmax;
                 if (MODE == 2) k_field[idx] = K;

@@ -8,7 +8,7 @@ namespace lbm {
 cudaError_t step_d2q9(int dtype, const void *fin, void *fout, const StepParams &p, int mode,
                       void *tile_max, void *k_field, cudaStream_t s, int variant) {
     const bool pair = dtype != 0 && (p.nx % 2 == 0) && variant == KERNEL_PAIR;
-    if (variant == KERNEL_PAIR && !pair) return cudaErrorInvalidValue;
+    if ((variant == KERNEL_PAIR && !pair) || variant == KERNEL_TMA) return cudaErrorInvalidValue;
     switch (dtype) {
         case 0: return launch_fused_step<D2Q9, 0>(fin, fout, p, mode, tile_max, k_field, s);
         case 1:

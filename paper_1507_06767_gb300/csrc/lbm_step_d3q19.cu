@@ -1,23 +1,121 @@
-// D3Q19 instantiations of the fused step: the one-cell kernel (lbm_step.cuh) by default, the two-cell
-// packed kernel (lbm_step_pair.cuh) on request.
+// D3Q19 instantiations of the fused step: the TMA-staged kernel (lbm_step_tma.cuh), the one-cell
+// kernel (lbm_step.cuh) and the two-cell packed kernel (lbm_step_pair.cuh), chosen by `variant`.
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "lbm_internal.h"
 #include "lbm_step_pair.cuh"
+#include "lbm_step_tma.cuh"
 
 namespace lbm {
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    });
+    return fn;
+}
+
+int sm_count() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (!cache[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
+
+// Tensor map of a population buffer as a 4-D tensor (x, y, z, direction) with box (w, 1, 1, 1).
+template <int DT>
+bool encode_populations(CUtensorMap *map, const void *base, const StepParams &p, int w) {
+    using T = typename Storage<DT>::T;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return false;
+    const cuuint64_t es = sizeof(T);
+    const cuuint64_t dims[4] = {(cuuint64_t)p.nx, (cuuint64_t)p.ny, (cuuint64_t)p.nz, 19};
+    const cuuint64_t strides[3] = {(cuuint64_t)p.nx * es, (cuuint64_t)p.nx * p.ny * es,
+                                   (cuuint64_t)p.nx * p.ny * p.nz * es};
+    const cuuint32_t box[4] = {(cuuint32_t)w, 1, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUtensorMapDataType t = DT == 1   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                  : DT == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                            : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    return enc(map, t, 4, const_cast<void *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               (CUtensorMapL2promotion)LBM_TMA_L2_PROMO, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+template <int DT, int MODE>
+cudaError_t launch_tma_mode(const CUtensorMap &main_map, const CUtensorMap &halo_map,
+                            const void *fin, void *fout, const StepParams &p, void *tile_max,
+                            void *k_field, cudaStream_t s) {
+    using T = typename Storage<DT>::T;
+    using C = TmaCfg<DT>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(fused_step_tma_kernel<DT, MODE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             C::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const long long units = (long long)((p.nx + TMA_CHUNK - 1) / TMA_CHUNK) * p.ny *
+                            ((p.nz + TMA_UNIT_Z - 1) / TMA_UNIT_Z);
+    const int nsm = sm_count();
+    long long grid = (long long)TMA_CTAS_PER_SM * (nsm > 0 ? nsm : 1);
+    if (grid > units) grid = units;
+    fused_step_tma_kernel<DT, MODE><<<(unsigned)grid, TMA_THREADS, C::SMEM_BYTES, s>>>(
+        main_map, halo_map, static_cast<const T *>(fin), static_cast<T *>(fout), p,
+        static_cast<float *>(tile_max), static_cast<float *>(p.tile_zero),
+        static_cast<float *>(k_field));
+    return cudaGetLastError();
+}
+
+template <int DT>
+cudaError_t launch_fused_step_tma(const void *fin, void *fout, const StepParams &p, int mode,
+                                  void *tile_max, void *k_field, cudaStream_t s) {
+    CUtensorMap main_map, halo_map;
+    if (!encode_populations<DT>(&main_map, fin, p, TMA_CHUNK) ||
+        !encode_populations<DT>(&halo_map, fin, p, TmaCfg<DT>::H))
+        return cudaErrorInvalidValue;
+    if (mode == 0) return launch_tma_mode<DT, 0>(main_map, halo_map, fin, fout, p, tile_max, k_field, s);
+    if (mode == 1) return launch_tma_mode<DT, 1>(main_map, halo_map, fin, fout, p, tile_max, k_field, s);
+    return launch_tma_mode<DT, 2>(main_map, halo_map, fin, fout, p, tile_max, k_field, s);
+}
+
+}  // namespace
 
 cudaError_t step_d3q19(int dtype, const void *fin, void *fout, const StepParams &p, int mode,
-                      void *tile_max, void *k_field, cudaStream_t s, int variant) {
+                       void *tile_max, void *k_field, cudaStream_t s, int variant) {
     const bool pair = dtype != 0 && (p.nx % 2 == 0) && variant == KERNEL_PAIR;
-    if (variant == KERNEL_PAIR && !pair) return cudaErrorInvalidValue;
+    const bool tma = tma_applicable(dtype, p.nx) && variant == KERNEL_TMA;
+    if ((variant == KERNEL_PAIR && !pair) || (variant == KERNEL_TMA && !tma))
+        return cudaErrorInvalidValue;
     switch (dtype) {
         case 0: return launch_fused_step<D3Q19, 0>(fin, fout, p, mode, tile_max, k_field, s);
         case 1:
+            if (tma) return launch_fused_step_tma<1>(fin, fout, p, mode, tile_max, k_field, s);
             return pair ? launch_fused_step_pair<D3Q19, 1>(fin, fout, p, mode, tile_max, k_field, s)
                         : launch_fused_step<D3Q19, 1>(fin, fout, p, mode, tile_max, k_field, s);
         case 2:
+            if (tma) return launch_fused_step_tma<2>(fin, fout, p, mode, tile_max, k_field, s);
             return pair ? launch_fused_step_pair<D3Q19, 2>(fin, fout, p, mode, tile_max, k_field, s)
                         : launch_fused_step<D3Q19, 2>(fin, fout, p, mode, tile_max, k_field, s);
         case 3:
+            if (tma) return launch_fused_step_tma<3>(fin, fout, p, mode, tile_max, k_field, s);
             return pair ? launch_fused_step_pair<D3Q19, 3>(fin, fout, p, mode, tile_max, k_field, s)
                         : launch_fused_step<D3Q19, 3>(fin, fout, p, mode, tile_max, k_field, s);
         default: return cudaErrorInvalidValue;

@@ -50,46 +50,6 @@ struct PairIO<3> {  // bfloat16 pair, shifted storage
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
-// General per-cell gather (walls, lid, periodic wrap) of cell (x, y, z): deviations from rest.
-template <class L, int DT>
-__device__ __forceinline__ void gather_general(const typename Storage<DT>::T *__restrict__ fin,
-                                               const StepParams &p, size_t N, int x, int y, int z,
-                                               float *df) {
-    using S = Storage<DT>;
-    const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const bool perx = p.periodic & 1, pery = p.periodic & 2, perz = p.periodic & 4;
-    const int xm = (x == 0) ? nx - 1 : x - 1, xp = (x == nx - 1) ? 0 : x + 1;
-    const bool vxm = (x > 0) || perx, vxp = (x < nx - 1) || perx;
-    const int ym = (y == 0) ? ny - 1 : y - 1, yp = (y == ny - 1) ? 0 : y + 1;
-    const bool vym = (y > 0) || pery, vyp = (y < ny - 1) || pery;
-    int zm = z, zp = z;
-    bool vzm = true, vzp = true;
-    if (L::D == 3) {
-        zm = (z == 0) ? nz - 1 : z - 1;
-        zp = (z == nz - 1) ? 0 : z + 1;
-        vzm = (z > 0) || perz;
-        vzp = (z < nz - 1) || perz;
-    }
-    const int idx = (z * ny + y) * nx + x;
-    const float lidx = (float)p.lid_x, lidz = (float)p.lid_z;
-#pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-        const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-        const int sx = cx == 1 ? xm : (cx == -1 ? xp : x);
-        const int sy = cy == 1 ? ym : (cy == -1 ? yp : y);
-        const int sz = cz == 1 ? zm : (cz == -1 ? zp : z);
-        const bool valid = (cx == 1 ? vxm : (cx == -1 ? vxp : true)) &&
-                           (cy == 1 ? vym : (cy == -1 ? vyp : true)) &&
-                           (cz == 1 ? vzm : (cz == -1 ? vzp : true));
-        const size_t src = valid ? (size_t)i * N + (size_t)((sz * ny + sy) * nx + sx)
-                                 : (size_t)L::opp(i) * N + (size_t)idx;
-        float v = S::to_r(load_pop(fin + src));
-        if (!S::SHIFTED) v -= weight<L, float>(i);
-        if (cy == -1 && !vyp) v += 6.f * weight<L, float>(i) * ((float)cx * lidx + (float)cz * lidz);
-        df[i] = v;
-    }
-}
-
 template <class L, int DT, int MODE>
 __global__ void __launch_bounds__(CTA_X *CTA_Y, LBM_PAIR_MIN_BLOCKS)
     fused_step_pair_kernel(const typename Storage<DT>::T *__restrict__ fin,
@@ -112,6 +72,15 @@ __global__ void __launch_bounds__(CTA_X *CTA_Y, LBM_PAIR_MIN_BLOCKS)
     const float2 omega = f2((float)p.omega);
     const float2 one = f2(1.f);
     int kmax = 0;
+
+    if (MODE != 0 && p.tile_zero) {
+        const size_t nt = (size_t)p.ntx * p.nty * p.ntz;
+        const size_t nthreads = (size_t)gridDim.x * gridDim.y * gridDim.z * blockDim.x * blockDim.y;
+        const size_t me = (((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) *
+                              (blockDim.x * blockDim.y) +
+                          threadIdx.y * blockDim.x + threadIdx.x;
+        for (size_t k = me; k < nt; k += nthreads) static_cast<float *>(p.tile_zero)[k] = 0.f;
+    }
 
     for (int dz = 0; dz < ZT; ++dz) {
         const int z = z0 + dz;
@@ -142,10 +111,10 @@ __global__ void __launch_bounds__(CTA_X *CTA_Y, LBM_PAIR_MIN_BLOCKS)
             }
         } else {
             float a[Q];
-            gather_general<L, DT>(fin, p, N, x0, y, z, a);
+            gather_cell<L, DT>(fin, p, N, x0, y, z, a);
 #pragma unroll
             for (int i = 0; i < Q; ++i) df[i].x = a[i];
-            gather_general<L, DT>(fin, p, N, x0 + 1, y, z, a);
+            gather_cell<L, DT>(fin, p, N, x0 + 1, y, z, a);
 #pragma unroll
             for (int i = 0; i < Q; ++i) df[i].y = a[i];
         }

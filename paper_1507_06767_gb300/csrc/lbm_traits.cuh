@@ -128,6 +128,8 @@ struct StepParams {
     int ntx, nty, ntz; // base tiles per axis
     double omega;      // 1 / tau
     double lid_x, lid_z;
+    int *err;          // device-visible error word for bounded waits (may be null)
+    void *tile_zero;   // tile-maxima buffer a sensor step clears for the next one (may be null)
 };
 
 }  // namespace lbm

@@ -83,6 +83,10 @@ _SIGS = {
     "lbm_conservation": (_i, [_h, _dp, _dp]),
     "lbm_kernel_time": (_i, [_h, _dp, ctypes.POINTER(_ll)]),
     "lbm_blocks_step": (_i, [_h, _vp]),
+    "lbm_set_sensor_average": (_i, [_h, _i]),
+    "lbm_sensor_average": (_i, [_h, _i, _vp, ctypes.POINTER(_ll)]),
+    "lbm_levels": (_i, [_h, _i, _d, _d, _i, _i, _i, _vp]),
+    "lbm_levels_fit": (_i, [_h, _i, _i, _i, _i, _vp]),
     "lbm_step_noalloc": (_i, [_i, _i, _i, _i, _i, _d, _d, _d, _i, _vp, _vp, _i, _vp, _vp]),
 }
 
@@ -220,6 +224,24 @@ def lbm_flags_from_maxima(maxima_dev, maxima_dtype: int, n: int, rule: int, para
     s = stream if stream is None or isinstance(stream, int) else stream.cuda_stream
     return _ck(_lib.lbm_flags_from_maxima(_ptr(maxima_dev), maxima_dtype, n, rule, param,
                                           _ptr(out_dev), s), "lbm_flags_from_maxima")
+
+
+lbm_set_sensor_average = _wrap("lbm_set_sensor_average")
+
+
+def lbm_sensor_average(h, block: int, out):
+    """Writes the time-averaged block maxima into out; returns the number of averaged steps."""
+    n = ctypes.c_longlong()
+    _ck(_lib.lbm_sensor_average(h, block, _ptr(out), ctypes.byref(n)), "lbm_sensor_average")
+    return n.value
+
+
+def lbm_levels(h, block: int, a: float, b: float, lmin: int, lmax: int, source: int, out) -> int:
+    return _ck(_lib.lbm_levels(h, block, a, b, lmin, lmax, source, _ptr(out)), "lbm_levels")
+
+
+def lbm_levels_fit(h, block: int, lmin: int, lmax: int, source: int, out) -> int:
+    return _ck(_lib.lbm_levels_fit(h, block, lmin, lmax, source, _ptr(out)), "lbm_levels_fit")
 
 
 def lbm_get_populations(h, out) -> int:
@@ -379,6 +401,23 @@ class Lattice:
     def block(self, b):
         lbm_set_block(self.h, int(b))
         self._block = int(b)
+
+    def levels(self, block, a, b, lmin, lmax, average=False):
+        out = np.empty(lbm_nblocks(self.h, block), dtype=np.int8)
+        lbm_levels(self.h, block, float(a), float(b), int(lmin), int(lmax),
+                   LBM_SENSOR_AVERAGE if average else LBM_SENSOR_LAST, out)
+        return out
+
+    def levels_fit(self, block, lmin, lmax, average=False):
+        out = np.empty(lbm_nblocks(self.h, block), dtype=np.int8)
+        lbm_levels_fit(self.h, block, int(lmin), int(lmax),
+                       LBM_SENSOR_AVERAGE if average else LBM_SENSOR_LAST, out)
+        return out
+
+    def sensor_average(self, block):
+        out = np.empty(lbm_nblocks(self.h, block), dtype=np.float64)
+        n = lbm_sensor_average(self.h, block, out)
+        return out, n
 
     def populations(self):
         out = np.empty(self.shape, dtype=np.float64)

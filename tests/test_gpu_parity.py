@@ -319,20 +319,23 @@ STORAGE_TOL = {  # populations (max|df|/max|f| after 3 steps), sensor field (rel
 
 
 @pytest.mark.parametrize("dtype", ["F32", "F16S", "BF16S"])
-@pytest.mark.parametrize("q,dims,periodic", [(19, (34, 20, 18), 0), (19, (40, 12, 10), O.PERIODIC_Z),
+@pytest.mark.parametrize("q,dims,periodic", [(19, (40, 20, 18), 0), (19, (48, 12, 10), O.PERIODIC_Z),
+                                             (19, (64, 9, 17), O.PERIODIC_X | O.PERIODIC_Y),
                                              (9, (66, 30, 1), 0)])
-def test_cell_and_pair_kernels_match_oracle(L, dtype, q, dims, periodic):
-    """The one-cell kernel and the two-cell packed kernel compute the same step: each matches the
-    oracle from the same storage-rounded input within the storage type's tolerance, and the two
-    agree with each other to a few FP32 roundings.  Shifted FP16 / BF16 storage (f - w_i) rounds
-    the deviation from rest to 11 / 8 significant bits per step; the tolerances above are those
-    roundings over 3 steps."""
+def test_kernel_variants_match_oracle(L, dtype, q, dims, periodic):
+    """The one-cell kernel, the two-cell packed kernel and the TMA-staged kernel compute the same
+    step: each matches the oracle from the same storage-rounded input within the storage type's
+    tolerance, and they agree with each other to a few FP32 roundings.  The lattices are ragged
+    against the TMA work unit (32 x 8 x 8 cells) in every direction.  Shifted FP16 / BF16 storage
+    (f - w_i) rounds the deviation from rest to 11 / 8 significant bits per step; the tolerances
+    above are those roundings over 3 steps."""
     dt = getattr(L, "LBM_" + dtype)
     lid = (0.1, 0.0, 0.02 if q == 19 else 0.0)
     o = O.Oracle(q, *dims, tau=0.6, lid=lid, periodic=periodic)
-    f0 = perturbed(o, seed=77 + q, amp=0.02)
+    f0 = perturbed(o, seed=77 + q + dims[0], amp=0.02)
+    variants = [L.LBM_KERNEL_CELL, L.LBM_KERNEL_PAIR] + ([L.LBM_KERNEL_TMA] if q == 19 else [])
     res = {}
-    for variant in (L.LBM_KERNEL_CELL, L.LBM_KERNEL_PAIR):
+    for variant in variants:
         lat = L.Lattice(q, *dims, 0.6, dtype=dt, lid=(lid[0], lid[2]), periodic=periodic)
         L.lbm_set_kernel_variant(lat.h, variant)
         L.lbm_set_sensor_field(lat.h, 1)
@@ -343,11 +346,80 @@ def test_cell_and_pair_kernels_match_oracle(L, dtype, q, dims, periodic):
         lat.close()
     tol_f, tol_k = STORAGE_TOL[dtype]
     f_in = res[L.LBM_KERNEL_CELL][0]
-    assert np.array_equal(f_in, res[L.LBM_KERNEL_PAIR][0])
+    for v in variants:
+        assert np.array_equal(f_in, res[v][0])
     f_ref, K = o.run(f_in, 3, sensor_last=True)
     for variant, (_, f, k, m) in res.items():
         assert rel(f, f_ref) < tol_f, variant
         assert rel(k, K) < tol_k, variant
         assert rel(m, O.block_max(K, 8)) < tol_k, variant
-    fa, fb = res[L.LBM_KERNEL_CELL][1], res[L.LBM_KERNEL_PAIR][1]
-    assert rel(fa, fb) < tol_f
+    for v in variants[1:]:
+        assert rel(res[v][1], res[L.LBM_KERNEL_CELL][1]) < tol_f, v
+    if L.LBM_KERNEL_TMA in res:
+        # the TMA kernel shares the one-cell kernel's arithmetic: identical bits
+        assert np.array_equal(res[L.LBM_KERNEL_TMA][1], res[L.LBM_KERNEL_CELL][1])
+
+
+def test_tma_kernel_long_run_and_sensor_steps(L):
+    """The TMA kernel over many steps with mixed sensor / non-sensor steps and graph replay, on a
+    lattice with several work units per CTA: bit-identical to the one-cell kernel."""
+    dims, tau = (64, 40, 36), 0.58
+    out = {}
+    for variant in (L.LBM_KERNEL_CELL, L.LBM_KERNEL_TMA):
+        lat = L.Lattice(19, *dims, tau, dtype=L.LBM_F32)
+        L.lbm_set_kernel_variant(lat.h, variant)
+        L.lbm_set_sensor_every(lat.h, 7)
+        lat.step(50)
+        out[variant] = (lat.raw(), lat.sensor(8), lat.sensor(16))
+        lat.close()
+    a, b = out[L.LBM_KERNEL_CELL], out[L.LBM_KERNEL_TMA]
+    assert np.array_equal(a[0], b[0])
+    assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+
+
+# ----------------------------------------------------------------------------- level map
+@pytest.mark.parametrize("q,dims,dtype,kband", [(9, (128, 128, 1), "F64", 1e-10),
+                                               (19, (40, 36, 33), "F32", 2e-4)])
+def test_levels_and_time_average(L, q, dims, dtype, kband):
+    """Sec. 3.4 level map and the Sec. 5.1 time-averaged sensor: the average over 10 sensor steps of
+    the 8^d tile maxima (block max over tiles), and the affine and fitted level maps of the last and
+    the averaged block maxima, against the oracle.  Levels are compared outside a band around the
+    integer decision values whose width follows the sensor tolerance (kband relative in K)."""
+    tau, every, nsens, b = 0.6, 3, 10, 16
+    lat, o = make(L, q, *dims, tau, getattr(L, "LBM_" + dtype))
+    L.lbm_set_sensor_every(lat.h, every)
+    L.lbm_set_sensor_average(lat.h, 1)
+    # a seeded perturbed start gives every block a sensor value well above round-off (the fitted
+    # map is defined by the smallest block maximum)
+    lat.set_populations(perturbed(o, seed=5 + q, amp=0.01))
+    f = lat.populations()
+    tile_sum = None
+    for _ in range(nsens):
+        lat.step(every)
+        f, K = o.run(f, every, sensor_last=True)
+        t8 = O.block_max(K, 8)
+        tile_sum = t8 if tile_sum is None else tile_sum + t8
+    # block max over tiles of the averaged tile maxima
+    tiles = (tile_sum / nsens).reshape(-(-dims[2] // 8) if q == 19 else 1, -(-dims[1] // 8),
+                                       -(-dims[0] // 8))
+    ref_avg = O.block_max(tiles, 2)  # 2 x 2 (x 2) tiles per 16-block
+    got_avg, n = lat.sensor_average(b)
+    assert n == nsens
+    assert rel(got_avg, ref_avg) < max(kband, 1e-12)
+    ref_last = O.block_max(K, b)
+    for src, ref in ((False, ref_last), (True, ref_avg)):
+        a_, b_ = 0.75, 9.0
+        got = lat.levels(b, a_, b_, 0, 5, average=src)
+        keep = O.levels_agree(got, ref, a_, b_, 0.0)
+        near = np.array([abs(a_ * np.log2(m) + b_ - round(a_ * np.log2(m) + b_)) < 3 * a_ * kband
+                         for m in ref])
+        keep &= ~near
+        assert np.array_equal(got[keep], O.levels_affine(ref, a_, b_, 0, 5)[keep]), src
+        assert keep.sum() > 0.8 * len(ref)
+        fit = lat.levels_fit(b, 1, 3, average=src)
+        af, bf = O.levels_fit_params(ref, 1, 3)
+        near = np.array([abs(af * np.log2(m) + bf - round(af * np.log2(m) + bf)) < 3 * af * kband + 1e-9
+                         for m in ref])
+        assert np.array_equal(fit[~near], O.levels_fit(ref, 1, 3)[~near]), src
+        assert fit.min() == 1 and fit.max() == 3
+    lat.close()

@@ -369,3 +369,20 @@ def test_step_cells_matches_full_step():
     out, Kc = o.step_cells(f, cells)
     assert np.array_equal(out, full.reshape(19, -1)[:, cells].T)
     assert np.array_equal(Kc, K.reshape(-1)[cells])
+
+
+def test_level_map_cases():
+    """Sec. 3.4, Eqs. phi and l: phi = log2 K, l = clamp([a phi + b], lmin, lmax) with [.] read as
+    the floor.  Powers of two give integer phi, so these cases are exact by hand."""
+    m = np.array([2.0 ** -10, 2.0 ** -9, 2.0 ** -4, 2.0 ** -20, 0.0, np.nan, 3 * 2.0 ** -11])
+    # a = 0.5, b = 7: phi -10 -> 2, -9 -> 2.5 -> 2, -4 -> 5 -> clamp 4, -20 -> -3 -> clamp 0;
+    # log2(3 * 2^-11) = -9.415 -> 2.29 -> 2
+    assert list(O.levels_affine(m, 0.5, 7.0, 0, 4)) == [2, 2, 4, 0, 0, 4, 2]
+    # fitted: phi in [-20, -4] mapped onto [0, 3): a = 3/16, b = 3.75
+    a, b = O.levels_fit_params(m, 0, 2)
+    assert abs(a - 3.0 / 16.0) < 1e-15 and abs(b - 3.75) < 1e-15
+    # -10 -> 1.875 -> 1; -9 -> 2.0625 -> 2; -4 -> 3 -> clamp 2; -20 -> 0; 0 -> lmin; NaN -> lmax;
+    # -9.415 -> 1.985 -> 1
+    assert list(O.levels_fit(m, 0, 2)) == [1, 2, 2, 0, 0, 2, 1]
+    # one distinct value: nothing to scale, all lmin (NaN still refines)
+    assert list(O.levels_fit(np.array([0.25, 0.25, np.nan]), 1, 3)) == [1, 1, 3]
