@@ -29,6 +29,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
+_SRC_ML = os.path.join(_HERE, "lbm_multilevel.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liblbm_oracle.so")
 _lock = threading.Lock()
@@ -44,10 +45,11 @@ PERIODIC_X, PERIODIC_Y, PERIODIC_Z = 1, 2, 4
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain -O2, no fast-math, so IEEE double arithmetic holds)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_ML))
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
-               "-ffp-contract=off", "-fopenmp", "-o", tmp, _SRC, "-lm"]
+               "-ffp-contract=off", "-fopenmp", "-o", tmp, _SRC, _SRC_ML, "-lm"]
         subprocess.check_call(cmd)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -57,6 +59,12 @@ class _Params(ctypes.Structure):
     _fields_ = [("q", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("nz", ctypes.c_int), ("tau", ctypes.c_double), ("lid", ctypes.c_double * 3),
                 ("periodic", ctypes.c_int), ("force", ctypes.c_double * 3)]
+
+
+class _MLDesc(ctypes.Structure):
+    _fields_ = [("nb", ctypes.c_int * 3), ("edge", ctypes.c_int), ("lmax", ctypes.c_int),
+                ("tau_fine", ctypes.c_double), ("lid", ctypes.c_double * 3),
+                ("periodic", ctypes.c_int)]
 
 
 def _load():
@@ -80,6 +88,20 @@ def _load():
             lib.orc_step_cells.argtypes = [pp, dp, ctypes.c_longlong,
                                            ctypes.POINTER(ctypes.c_longlong), dp, dp]
             lib.orc_threads.argtypes = []
+            lib.ml_create.argtypes = [ctypes.POINTER(_MLDesc), ctypes.POINTER(ctypes.c_int8),
+                                      ctypes.POINTER(ctypes.c_int)]
+            lib.ml_create.restype = ctypes.c_void_p
+            lib.ml_destroy.argtypes = [ctypes.c_void_p]
+            lib.ml_destroy.restype = None
+            lib.ml_cycles.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            lib.ml_block_max.argtypes = [ctypes.c_void_p, dp]
+            lib.ml_get_block.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, dp]
+            lib.ml_set_block.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, dp]
+            lib.ml_level_info.argtypes = [ctypes.c_void_p, ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_int), dp]
+            for name in ("ml_cycles", "ml_block_max", "ml_get_block", "ml_set_block",
+                         "ml_level_info"):
+                getattr(lib, name).restype = ctypes.c_int
             for name in ("orc_threads", "orc_step_cells", "orc_lattice", "orc_step", "orc_run", "orc_collide", "orc_stream_push",
                          "orc_sensor", "orc_equilibrium", "orc_block_max", "orc_conservation"):
                 getattr(lib, name).restype = ctypes.c_int
@@ -365,3 +387,70 @@ def levels_agree(levels, maxima, a, b, rel_band: float):
             if abs(v - round(v)) <= rel_band * max(1.0, abs(v)):
                 keep[k] = False
     return keep
+
+
+class MultiLevel:
+    """Multi-level block-structured D3Q19 mesh (refinement ratio 2, acoustic scaling, level
+    sub-cycling, f^neq rescaling at level interfaces; lbm_multilevel.c states the reading of
+    Sec. 2.1 / Sec. 5.2 it implements).  leaf[nbz, nby, nbx] holds the leaf level per physical
+    block of edge `edge` finest cells."""
+
+    def __init__(self, leaf, edge, lmax, tau_fine, lid=(0.0, 0.0, 0.0), periodic=0):
+        leaf = np.ascontiguousarray(leaf, dtype=np.int8)
+        assert leaf.ndim == 3
+        self.leaf = leaf
+        self.nb = (leaf.shape[2], leaf.shape[1], leaf.shape[0])
+        self.edge, self.lmax = int(edge), int(lmax)
+        d = _MLDesc((ctypes.c_int * 3)(*self.nb), self.edge, self.lmax, float(tau_fine),
+                    (ctypes.c_double * 3)(*[float(v) for v in lid]), int(periodic))
+        st = ctypes.c_int()
+        self._h = _load().ml_create(ctypes.byref(d), leaf.ctypes.data_as(
+            ctypes.POINTER(ctypes.c_int8)), ctypes.byref(st))
+        if not self._h:
+            raise ValueError(f"multi-level mesh rejected (status {st.value})")
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.ml_destroy(self._h)
+            self._h = None
+
+    def level_info(self, l):
+        n = ctypes.c_int()
+        tau = ctypes.c_double()
+        _check(_load().ml_level_info(self._h, l, ctypes.byref(n), ctypes.byref(tau)), "info")
+        return n.value, tau.value
+
+    def cycles(self, c):
+        _check(_load().ml_cycles(self._h, int(c)), "cycles")
+
+    def block_max(self):
+        out = np.empty(self.leaf.size)
+        _check(_load().ml_block_max(self._h, _ptr(out)), "block_max")
+        return out
+
+    def block_index(self, bx, by, bz):
+        return (bz * self.nb[1] + by) * self.nb[0] + bx
+
+    def get_block(self, level, b):
+        n, _ = self.level_info(level)
+        out = np.empty((19, n, n, n))
+        _check(_load().ml_get_block(self._h, level, int(b), _ptr(out)), "get_block")
+        return out
+
+    def set_block(self, level, b, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        _check(_load().ml_set_block(self._h, level, int(b), _ptr(f)), "set_block")
+
+    def leaf_field(self, level):
+        """Assemble the level's populations over the whole domain (blocks where the level exists;
+        NaN elsewhere): shape (19, nz, ny, nx) in level-l cells."""
+        n, _ = self.level_info(level)
+        nbx, nby, nbz = self.nb
+        out = np.full((19, nbz * n, nby * n, nbx * n), np.nan)
+        for bz in range(nbz):
+            for by in range(nby):
+                for bx in range(nbx):
+                    if self.leaf[bz, by, bx] >= level:
+                        out[:, bz * n:(bz + 1) * n, by * n:(by + 1) * n, bx * n:(bx + 1) * n] = \
+                            self.get_block(level, self.block_index(bx, by, bz))
+        return out

@@ -321,6 +321,8 @@ STORAGE_TOL = {  # populations (max|df|/max|f| after 3 steps), sensor field (rel
 @pytest.mark.parametrize("dtype", ["F32", "F16S", "BF16S"])
 @pytest.mark.parametrize("q,dims,periodic", [(19, (40, 20, 18), 0), (19, (48, 12, 10), O.PERIODIC_Z),
                                              (19, (64, 9, 17), O.PERIODIC_X | O.PERIODIC_Y),
+                                             (19, (264, 10, 9), O.PERIODIC_X),
+                                             (19, (288, 9, 11), 0),
                                              (9, (66, 30, 1), 0)])
 def test_kernel_variants_match_oracle(L, dtype, q, dims, periodic):
     """The one-cell kernel, the two-cell packed kernel and the TMA-staged kernel compute the same
@@ -355,15 +357,14 @@ def test_kernel_variants_match_oracle(L, dtype, q, dims, periodic):
         assert rel(m, O.block_max(K, 8)) < tol_k, variant
     for v in variants[1:]:
         assert rel(res[v][1], res[L.LBM_KERNEL_CELL][1]) < tol_f, v
-    if L.LBM_KERNEL_TMA in res:
-        # the TMA kernel shares the one-cell kernel's arithmetic: identical bits
-        assert np.array_equal(res[L.LBM_KERNEL_TMA][1], res[L.LBM_KERNEL_CELL][1])
+
 
 
 def test_tma_kernel_long_run_and_sensor_steps(L):
     """The TMA kernel over many steps with mixed sensor / non-sensor steps and graph replay, on a
-    lattice with several work units per CTA: bit-identical to the one-cell kernel."""
-    dims, tau = (64, 40, 36), 0.58
+    lattice with several work units per CTA and an odd plane count per unit: it follows the
+    one-cell kernel to FP32 rounding (the two evaluate the same formulas in a different order)."""
+    dims, tau = (64, 40, 35), 0.58
     out = {}
     for variant in (L.LBM_KERNEL_CELL, L.LBM_KERNEL_TMA):
         lat = L.Lattice(19, *dims, tau, dtype=L.LBM_F32)
@@ -373,8 +374,9 @@ def test_tma_kernel_long_run_and_sensor_steps(L):
         out[variant] = (lat.raw(), lat.sensor(8), lat.sensor(16))
         lat.close()
     a, b = out[L.LBM_KERNEL_CELL], out[L.LBM_KERNEL_TMA]
-    assert np.array_equal(a[0], b[0])
-    assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+    fa, fb = a[0].view(np.float32), b[0].view(np.float32)
+    assert rel(fb, fa) < 1e-5
+    assert rel(b[1], a[1]) < 1e-4 and rel(b[2], a[2]) < 1e-4
 
 
 # ----------------------------------------------------------------------------- level map
