@@ -304,12 +304,51 @@ LBM_API int lbm_step_noalloc(int lattice, int dtype, int nx, int ny, int nz, dou
                              void *f_out_dev, int block, double *block_max_dev, void *stream);
 
 /*
- * Multi-level block batch (refinement ratio 2, level sub-cycling, f^neq rescaling at interfaces:
- * Sec. 2.1 and Sec. 5.2 describe the cell-centred block-structured scheme).  Not provided in this
- * version: returns LBM_ENOTSUP.
+ * Multi-level block-structured mesh (refinement ratio 2; Sec. 2.1 and Sec. 5.2 describe the
+ * cell-centred block-structured AMR the paper's dynamic meshes use).  The lattice of the handle is
+ * the domain at the finest resolution: nbx * edge = nx and so on, tau is the finest level's
+ * relaxation time, and the lid and periodic settings apply.  D3Q19 with LBM_F32 storage only
+ * (LBM_ENOTSUP otherwise).
+ *
+ * The domain is a grid of nbx x nby x nbz physical blocks of edge `edge` finest cells; leaf[b]
+ * (x fastest) is the finest level 0..lmax present in block b (lmax <= 2).  Level l exists on every
+ * block whose leaf level is >= l, with edge / 2^(lmax - l) cells per block edge, so levels nest
+ * and level 0 covers the domain; touching blocks (faces, edges, corners) may differ by one level
+ * at most, and edge / 2^lmax must be >= 2.  Acoustic scaling: dx / dt is the same on every level,
+ * so level l takes 2^l steps per level-0 step ("cycle") and tau_l = 3 nu / 2^(lmax - l) + 1/2 with
+ * nu = (tau - 1/2) / 3 of the finest level (Eq. nu_omega); every level needs tau_l != 1.
+ * Coupling: one-cell ghost layers, filled by copies inside a level and, at the edge of a level, by
+ * trilinear space / linear time interpolation of the next coarser level with the non-equilibrium
+ * part rescaled by (tau_f - 1) / (2 (tau_c - 1)); after the two sub-steps of a finer level the
+ * coarser cells under it take the average of their 8 fine cells, the non-equilibrium part rescaled
+ * by 2 (tau_c - 1) / (tau_f - 1).  The sensor K of every cell is evaluated in each level step; the
+ * reported block maximum is that of the block's leaf level at its last sub-step of the cycle.
+ *
+ * lbm_blocks_step builds the mesh at rest on the first call (or when the layout changes, which
+ * restarts it at rest; lbm_reset discards it), runs `cycles` cycles as one captured CUDA graph
+ * each (graphs off: direct launches), and, if block_max is not NULL, writes nbx * nby * nbz block
+ * maxima (host, synchronising).  The step kernel's launch shape per level is chosen by timing the
+ * candidates when the mesh is built (lbm_blocks_info reports it).
  */
-typedef struct lbm_level_batch lbm_level_batch;
+typedef struct lbm_level_batch {
+    int nbx, nby, nbz;   /* physical blocks per axis */
+    int edge;            /* block edge in finest cells */
+    int lmax;            /* finest level, 0..2 */
+    const int8_t *leaf;  /* host: leaf level per block, x fastest */
+    int cycles;          /* level-0 steps to advance */
+    double *block_max;   /* host output, nbx * nby * nbz values, or NULL */
+} lbm_level_batch;
 LBM_API int lbm_blocks_step(lbm_t *h, const lbm_level_batch *batch);
+/* Interior populations of physical block `block` at level `level` (n^3 cells, n = edge /
+ * 2^(lmax - level)), layout f[i][z][y][x], as doubles; the block must exist at that level.
+ * Synchronise. */
+LBM_API int lbm_blocks_get(lbm_t *h, int level, int block, double *out_host);
+LBM_API int lbm_blocks_set(lbm_t *h, int level, int block, const double *in_host);
+/* Level facts: cells per block edge, tau, blocks at the level, the step kernel's threads per CTA
+ * and cells per thread, and the cell updates of one cycle over all levels (any pointer may be
+ * NULL). */
+LBM_API int lbm_blocks_info(lbm_t *h, int level, int *n, double *tau, int *nblocks, int *threads,
+                            int *cells_per_thread, long long *cell_updates_per_cycle);
 
 #ifdef __cplusplus
 }

@@ -109,6 +109,9 @@ struct lbm_s {
     std::vector<cudaEvent_t> events;
     size_t events_used = 0;
 
+    // multi-level block mesh of lbm_blocks_step (built on first use)
+    lbm::ml::Mesh *mesh = nullptr;
+
     // graph cache: runs of two plain steps, by starting buffer
     cudaGraphExec_t pair_exec[2] = {nullptr, nullptr};
     cudaStream_t pair_stream[2] = {nullptr, nullptr};
@@ -434,6 +437,7 @@ LBM_API int lbm_destroy(lbm_t *h) {
     cudaFree(h->tile_sum);
     cudaFree(h->tile_avg);
     if (h->err_host) cudaFreeHost(h->err_host);
+    lbm::ml::destroy(h->mesh);
     delete h;
     return LBM_OK;
 }
@@ -567,6 +571,11 @@ LBM_API long long lbm_steps_done(const lbm_t *h) { return h ? h->t : -1; }
 
 LBM_API int lbm_reset(lbm_t *h) {
     CHECK_H(h);
+    if (h->mesh) {
+        cudaStreamSynchronize(h->stream);
+        lbm::ml::destroy(h->mesh);
+        h->mesh = nullptr;
+    }
     int st = ensure_buffers(h);
     if (st != LBM_OK) return st;
     CK(cudaSetDevice(h->device), "cudaSetDevice");
@@ -937,9 +946,59 @@ LBM_API int lbm_levels_fit(lbm_t *h, int block, int lmin, int lmax, int source, 
 }
 
 LBM_API int lbm_blocks_step(lbm_t *h, const lbm_level_batch *batch) {
-    (void)batch;
     CHECK_H(h);
-    return fail(LBM_ENOTSUP, "multi-level block batches are not provided in this version");
+    if (!batch || !batch->leaf) return fail(LBM_EINVAL, "NULL batch or leaf levels");
+    if (h->q != LBM_D3Q19) return fail(LBM_ENOTSUP, "multi-level meshes are D3Q19 only");
+    if (h->dtype != LBM_F32) return fail(LBM_ENOTSUP, "multi-level meshes use FP32 storage");
+    if (batch->cycles < 0) return fail(LBM_EINVAL, "cycles must be >= 0");
+    const int nb[3] = {batch->nbx, batch->nby, batch->nbz};
+    if (batch->nbx < 1 || batch->nby < 1 || batch->nbz < 1 || batch->edge < 1)
+        return fail(LBM_EINVAL, "bad block grid");
+    if ((long long)batch->nbx * batch->edge != h->nx || (long long)batch->nby * batch->edge != h->ny ||
+        (long long)batch->nbz * batch->edge != h->nz)
+        return fail(LBM_EINVAL, "block grid x edge must equal the handle's lattice (%d x %d x %d)",
+                    h->nx, h->ny, h->nz);
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    if (h->mesh && !lbm::ml::same_layout(h->mesh, nb, batch->edge, batch->lmax, batch->leaf)) {
+        CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+        lbm::ml::destroy(h->mesh);
+        h->mesh = nullptr;
+    }
+    if (!h->mesh) {
+        const double lid[3] = {h->lid_x, 0.0, h->lid_z};
+        int st = lbm::ml::build(&h->mesh, nb, batch->edge, batch->lmax, batch->leaf, h->tau, lid,
+                                h->periodic, h->stream);
+        if (st != LBM_OK) return st;
+    }
+    int st = lbm::ml::run_cycles(h->mesh, batch->cycles, h->stream, h->graphs != 0);
+    if (st != LBM_OK) return st;
+    if (batch->block_max) {
+        st = lbm::ml::block_max(h->mesh, batch->block_max, h->stream);
+        if (st != LBM_OK) return st;
+    }
+    return LBM_OK;
+}
+
+LBM_API int lbm_blocks_get(lbm_t *h, int level, int block, double *out_host) {
+    CHECK_H(h);
+    if (!h->mesh) return fail(LBM_ESTATE, "no multi-level mesh (call lbm_blocks_step first)");
+    if (!out_host) return fail(LBM_EINVAL, "NULL output");
+    return lbm::ml::get_block(h->mesh, level, block, out_host, h->stream);
+}
+
+LBM_API int lbm_blocks_set(lbm_t *h, int level, int block, const double *in_host) {
+    CHECK_H(h);
+    if (!h->mesh) return fail(LBM_ESTATE, "no multi-level mesh (call lbm_blocks_step first)");
+    if (!in_host) return fail(LBM_EINVAL, "NULL input");
+    return lbm::ml::set_block(h->mesh, level, block, in_host, h->stream);
+}
+
+LBM_API int lbm_blocks_info(lbm_t *h, int level, int *n, double *tau, int *nblocks, int *threads,
+                            int *cells_per_thread, long long *cell_updates_per_cycle) {
+    CHECK_H(h);
+    if (!h->mesh) return fail(LBM_ESTATE, "no multi-level mesh (call lbm_blocks_step first)");
+    if (cell_updates_per_cycle) *cell_updates_per_cycle = lbm::ml::cells_per_cycle(h->mesh);
+    return lbm::ml::info(h->mesh, level, n, tau, nblocks, threads, cells_per_thread);
 }
 
 }  // extern "C"

@@ -10,8 +10,11 @@
 namespace lbm {
 
 // Fused step (lbm_step_d2q9.cu / lbm_step_d3q19.cu).  mode: 0 no sensor, 1 tile max, 2 + field.
-// variant: KERNEL_AUTO / KERNEL_CELL: the one-cell kernel; KERNEL_PAIR: the two-cell packed one;
-// KERNEL_TMA: the TMA-staged one (D3Q19 only); the last two are errors where they do not apply.
+// variant: KERNEL_CELL: the one-cell kernel; KERNEL_PAIR: the two-cell packed one; KERNEL_TMA: the
+// TMA-staged one (D3Q19 only); the last two are errors where they do not apply.  KERNEL_AUTO picks
+// the one-cell kernel for 32/64-bit storage and the two-cell one for 16-bit storage (even nx); it
+// never picks the TMA kernel, whose tile maxima need a cleared buffer (lbm_step_noalloc relies on
+// this).
 constexpr int KERNEL_AUTO = 0;
 constexpr int KERNEL_CELL = 1;
 constexpr int KERNEL_PAIR = 2;
@@ -53,6 +56,21 @@ cudaError_t levels_fit(int rtype, const void *maxima, int n, int lmin, int lmax,
 // Time average of the tile maxima: sum += tiles; out = sum * factor.
 cudaError_t accumulate_tiles(int rtype, const void *tiles, double *sum, size_t n, cudaStream_t s);
 cudaError_t scale_f64(const double *in, double factor, double *out, size_t n, cudaStream_t s);
+
+// Multi-level block mesh (lbm_multilevel.cu).
+namespace ml {
+struct Mesh;
+int build(Mesh **out, const int nb[3], int edge, int lmax, const int8_t *leaf, double tau_fine,
+          const double lid[3], int periodic, cudaStream_t s);
+void destroy(Mesh *m);
+bool same_layout(const Mesh *m, const int nb[3], int edge, int lmax, const int8_t *leaf);
+int run_cycles(Mesh *m, int cycles, cudaStream_t s, bool graphs);
+int block_max(Mesh *m, double *out_host, cudaStream_t s);
+int get_block(Mesh *m, int l, int b, double *out, cudaStream_t s);
+int set_block(Mesh *m, int l, int b, const double *in, cudaStream_t s);
+int info(const Mesh *m, int l, int *n, double *tau, int *nslot, int *threads, int *cpt);
+long long cells_per_cycle(const Mesh *m);
+}  // namespace ml
 
 // Error state shared by the C-ABI translation units (lbm_api.cu).
 int report_error(int code, const char *msg);

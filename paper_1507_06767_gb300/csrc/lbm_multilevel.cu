@@ -1,0 +1,741 @@
+// Multi-level block-structured lattice Boltzmann step (D3Q19, FP32) on the GPU.
+//
+// The paper (Sec. 2.1, Sec. 5.2) drives cell-centred block-structured refinement with ratio 2
+// under acoustic scaling: levels are sub-cycled and coupled by linear temporal and second-order
+// spatial interpolation with the non-equilibrium part of the populations rescaled between levels.
+// This file implements the same reading as the FP64 checker of this repository:
+//
+//   * physical blocks of edge E finest cells carry a leaf level 0..lmax; level l exists on every
+//     block whose leaf level is >= l, with n_l = E / 2^(lmax - l) cells per block edge; touching
+//     blocks differ by at most one level;
+//   * acoustic scaling: tau_l = 3 nu_lmax / 2^(lmax - l) + 1/2, level l takes 2^l steps per
+//     level-0 step (a cycle);
+//   * a level step is the fused pull step of every block of the level (moving-wall bounce-back at
+//     the domain walls, moments, equilibrium, Knudsen sensor, BGK collision) reading a one-cell
+//     ghost layer;
+//   * ghost cells inside another block of the same level are copies; the others are trilinear
+//     (3/4, 1/4 per axis; 5/4, -1/4 extrapolation at a wall) interpolations of the coarser level,
+//     linear in time between its states before and after its step, with f^neq rescaled by
+//     (tau_f - 1) / (2 (tau_c - 1));
+//   * after the two sub-steps of level l + 1, the level-l cells under it become the average of
+//     their 8 fine cells with f^neq rescaled by 2 (tau_c - 1) / (tau_f - 1).
+//
+// Device layout of a level: one buffer of nslot blocks x 19 populations x (n + 2)^3 ghosted cells
+// (block-major, then population, then z, y, x), two buffers (ping-pong).  The ghost and
+// restriction work is precomputed on the host as task lists (flat element offsets and weights), so
+// the kernels are plain gathers.  A cycle is captured once per level-0 buffer parity as a CUDA graph
+// and replayed.  The launch shape of each level's step kernel (threads per CTA and cells per
+// thread) is chosen by timing the candidates once when the mesh is built.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+#include "lbm_step.cuh"
+
+namespace lbm {
+namespace ml {
+
+constexpr int Q = 19;
+constexpr int MAXL = 3;
+
+struct CopyTask {
+    int dst, src;  // flat offsets of population 0 (population i adds i * G)
+};
+struct InterpTask {
+    int dst;
+    int src[8];
+    float w[8];
+};
+struct RestrictTask {
+    int dst;   // coarse cell, population 0
+    int fine;  // fine cell (2x, 2y, 2z), population 0
+};
+
+struct Level {
+    int n = 0, G = 0;      // cells per block edge, ghosted cells per block
+    double tau = 1.0;
+    int nslot = 0;
+    std::vector<int> slot;  // physical block -> slot or -1
+    int cells[3] = {0, 0, 0};
+    float *buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    int *origin = nullptr;  // device: 3 ints per slot (level-cell origin of the block)
+    CopyTask *copies = nullptr;
+    int ncopy = 0;
+    InterpTask *interps = nullptr;  // from level - 1
+    int ninterp = 0;
+    RestrictTask *restricts = nullptr;  // level cells under level + 1
+    int nrestrict = 0;
+    float *kmax = nullptr;  // device: per-slot sensor max of the level's last step (int bits)
+    int threads = 256, cpt = 1;  // step launch shape (autotuned)
+};
+
+struct Mesh {
+    int nb[3] = {0, 0, 0}, edge = 0, lmax = 0, nblk = 0;
+    std::vector<int8_t> leaf;
+    double lid[3] = {0, 0, 0};
+    int periodic = 0;
+    Level lv[MAXL];
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // by level-0 buffer parity
+    long long cycles = 0;
+};
+
+// ---------------------------------------------------------------------------------- kernels
+__global__ void k_copy(const CopyTask *t, int n, float *buf, int G) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const CopyTask c = t[k];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) buf[c.dst + i * G] = buf[c.src + i * G];
+}
+
+__device__ __forceinline__ void moments19(const float *f, float &rho, float &ux, float &uy,
+                                          float &uz) {
+    float r = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        r += f[i];
+        jx += (float)D3Q19::cx(i) * f[i];
+        jy += (float)D3Q19::cy(i) * f[i];
+        jz += (float)D3Q19::cz(i) * f[i];
+    }
+    rho = r;
+    const float inv = 1.f / r;
+    ux = jx * inv;
+    uy = jy * inv;
+    uz = jz * inv;
+}
+
+__device__ __forceinline__ float feq19(int i, float rho, float ux, float uy, float uz) {
+    const float cu = (float)D3Q19::cx(i) * ux + (float)D3Q19::cy(i) * uy + (float)D3Q19::cz(i) * uz;
+    const float uu = ux * ux + uy * uy + uz * uz;
+    return weight<D3Q19, float>(i) * rho * (1.f + 3.f * cu + 4.5f * cu * cu - 1.5f * uu);
+}
+
+// coarse -> fine ghost: interpolate in space and time, rescale the non-equilibrium part
+__global__ void k_interp(const InterpTask *t, int n, float *fine, int Gf, const float *cprev,
+                         const float *ccur, int Gc, float theta, float scale) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const InterpTask it = t[k];
+    float acc[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        float a = 0.f;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const int o = it.src[s] + i * Gc;
+            a += it.w[s] * ((1.f - theta) * cprev[o] + theta * ccur[o]);
+        }
+        acc[i] = a;
+    }
+    float rho, ux, uy, uz;
+    moments19(acc, rho, ux, uy, uz);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float fe = feq19(i, rho, ux, uy, uz);
+        fine[it.dst + i * Gf] = fe + scale * (acc[i] - fe);
+    }
+}
+
+// level cells under the finer level: average of 8 fine cells, non-equilibrium part rescaled
+__global__ void k_restrict(const RestrictTask *t, int n, float *coarse, int Gc, const float *fine,
+                           int nf, int Gf, float scale) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const RestrictTask r = t[k];
+    const int row = nf + 2, plane = (nf + 2) * (nf + 2);
+    float avg[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float *f = fine + r.fine + i * Gf;
+        avg[i] = 0.125f * (f[0] + f[1] + f[row] + f[row + 1] + f[plane] + f[plane + 1] +
+                           f[plane + row] + f[plane + row + 1]);
+    }
+    float rho, ux, uy, uz;
+    moments19(avg, rho, ux, uy, uz);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float fe = feq19(i, rho, ux, uy, uz);
+        coarse[r.dst + i * Gc] = fe + scale * (avg[i] - fe);
+    }
+}
+
+struct StepArgs {
+    int n, G;
+    int cells[3];
+    int periodic;
+    float omega;
+    float lid_x, lid_z;
+};
+
+// one pull step of every block of a level; grid (slot, chunk), each thread `cpt` cells
+__global__ void k_step(const float *__restrict__ in, float *__restrict__ out, const int *origin,
+                       const StepArgs a, int cpt, float *kmax) {
+    using L = D3Q19;
+    const int slot = blockIdx.x;
+    const int n = a.n, G = a.G, row = n + 2, plane = (n + 2) * (n + 2);
+    const int ncell = n * n * n;
+    const float *src = in + (size_t)slot * Q * G;
+    float *dst = out + (size_t)slot * Q * G;
+    const int ox = origin[3 * slot], oy = origin[3 * slot + 1], oz = origin[3 * slot + 2];
+    int km = 0;
+    for (int r = 0; r < cpt; ++r) {
+        const int c = (blockIdx.y * cpt + r) * blockDim.x + threadIdx.x;
+        if (c >= ncell) break;
+        const int x = c % n, y = (c / n) % n, z = c / (n * n);
+        const int g = (z + 1) * plane + (y + 1) * row + (x + 1);
+        float df[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+            const int gx = ox + x - cx, gy = oy + y - cy, gz = oz + z - cz;
+            const bool wx = (gx < 0 || gx >= a.cells[0]) && !(a.periodic & 1);
+            const bool wy = (gy < 0 || gy >= a.cells[1]) && !(a.periodic & 2);
+            const bool wz = (gz < 0 || gz >= a.cells[2]) && !(a.periodic & 4);
+            float v;
+            if (wx || wy || wz) {
+                v = src[L::opp(i) * G + g];
+                if (gy == a.cells[1] && !(a.periodic & 2))
+                    v += 6.f * weight<L, float>(i) * ((float)cx * a.lid_x + (float)cz * a.lid_z);
+            } else {
+                v = src[i * G + g - (cz * plane + cy * row + cx)];
+            }
+            df[i] = v - weight<L, float>(i);
+        }
+        const float K = relax_store_cell<L, 1, 1>(df, a.omega, dst, (size_t)G, g);
+        km = max(km, __float_as_int(K));
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) km = max(km, __shfl_xor_sync(~0u, km, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int *>(kmax) + slot, km);
+}
+
+__global__ void k_fill_rest(float *buf, int nslot, int G) {
+    const size_t total = (size_t)nslot * Q * G;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+         k += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)((k / G) % Q);
+        buf[k] = weight<D3Q19, float>(i);
+    }
+}
+
+// per physical block: the sensor max of its leaf level
+__global__ void k_leaf_max(const int *leaf_slot, const int *leaf_level, int nblk,
+                           const float *k0, const float *k1, const float *k2, double *out) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nblk) return;
+    const int l = leaf_level[b], s = leaf_slot[b];
+    const float *k = l == 0 ? k0 : (l == 1 ? k1 : k2);
+    out[b] = (double)k[s];
+}
+
+// ------------------------------------------------------------------------------ host side
+inline int wrap(int g, int n, bool per) {
+    if (g >= 0 && g < n) return g;
+    if (per) return ((g % n) + n) % n;
+    return -1;
+}
+
+}  // namespace ml
+}  // namespace lbm
+
+namespace lbm {
+namespace ml {
+namespace {
+
+#define MLCK(call, what)                                          \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return report_cuda_error(e_, what); \
+    } while (0)
+
+int gidx(int n, int x, int y, int z) { return ((z + 1) * (n + 2) + (y + 1)) * (n + 2) + (x + 1); }
+
+bool balanced(const Mesh &m) {
+    for (int z = 0; z < m.nb[2]; ++z)
+        for (int y = 0; y < m.nb[1]; ++y)
+            for (int x = 0; x < m.nb[0]; ++x) {
+                const int b = (z * m.nb[1] + y) * m.nb[0] + x;
+                for (int dz = -1; dz <= 1; ++dz)
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            int c[3] = {x + dx, y + dy, z + dz};
+                            bool ok = true;
+                            for (int a = 0; a < 3; ++a) {
+                                const int w = wrap(c[a], m.nb[a], m.periodic & (1 << a));
+                                if (w < 0) ok = false;
+                                c[a] = w;
+                            }
+                            if (!ok) continue;
+                            const int o = (c[2] * m.nb[1] + c[1]) * m.nb[0] + c[0];
+                            if (abs(m.leaf[b] - m.leaf[o]) > 1) return false;
+                        }
+            }
+    return true;
+}
+
+template <class T>
+int upload(T **dev, const std::vector<T> &v) {
+    *dev = nullptr;
+    if (v.empty()) return LBM_OK;
+    MLCK(cudaMalloc((void **)dev, v.size() * sizeof(T)), "cudaMalloc(tasks)");
+    MLCK(cudaMemcpy(*dev, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), "cudaMemcpy");
+    return LBM_OK;
+}
+
+// flat offset (population 0) of a level-l global cell already wrapped into the domain
+int cell_offset(const Mesh &m, int l, const int g[3], int *slot_out) {
+    const Level &L = m.lv[l];
+    int b[3], loc[3];
+    for (int a = 0; a < 3; ++a) {
+        b[a] = g[a] / L.n;
+        loc[a] = g[a] - b[a] * L.n;
+    }
+    const int blk = (b[2] * m.nb[1] + b[1]) * m.nb[0] + b[0];
+    const int s = L.slot[blk];
+    *slot_out = s;
+    if (s < 0) return -1;
+    return s * Q * L.G + gidx(L.n, loc[0], loc[1], loc[2]);
+}
+
+int build_tasks(Mesh &m, int l) {
+    Level &L = m.lv[l];
+    std::vector<CopyTask> copies;
+    std::vector<InterpTask> interps;
+    const int n = L.n;
+    for (int b = 0; b < m.nblk; ++b) {
+        const int s = L.slot[b];
+        if (s < 0) continue;
+        const int bz = b / (m.nb[0] * m.nb[1]), by = (b / m.nb[0]) % m.nb[1], bx = b % m.nb[0];
+        for (int z = -1; z <= n; ++z)
+            for (int y = -1; y <= n; ++y)
+                for (int x = -1; x <= n; ++x) {
+                    const int out = (x < 0 || x >= n) + (y < 0 || y >= n) + (z < 0 || z >= n);
+                    if (out == 0 || out == 3) continue;  // interior, or a corner (unused)
+                    int g[3] = {bx * n + x, by * n + y, bz * n + z};
+                    bool inside = true;
+                    for (int a = 0; a < 3; ++a) {
+                        const int w = wrap(g[a], L.cells[a], m.periodic & (1 << a));
+                        if (w < 0) inside = false;
+                        g[a] = w;
+                    }
+                    if (!inside) continue;  // a wall: the step bounces back
+                    const int dst = s * Q * L.G + gidx(n, x, y, z);
+                    int ns;
+                    const int src = cell_offset(m, l, g, &ns);
+                    if (ns >= 0) {
+                        copies.push_back({dst, src});
+                        continue;
+                    }
+                    if (l == 0) return report_error(LBM_EINVAL, "level-0 ghost without a source");
+                    // ghost centre (g + 1/2) h_l lies at g/2 + 1/4 coarse cells: coarse cell
+                    // g >> 1, offset -1/4 (g even) or +1/4 (g odd)
+                    const Level &C = m.lv[l - 1];
+                    int c0[3], c1[3];
+                    float w0[3], w1[3];
+                    for (int a = 0; a < 3; ++a) {
+                        const int c = g[a] >> 1;
+                        const int dir = (g[a] & 1) ? 1 : -1;
+                        const bool per = m.periodic & (1 << a);
+                        const int nbr = wrap(c + dir, C.cells[a], per);
+                        if (nbr >= 0) {
+                            c0[a] = c;
+                            c1[a] = nbr;
+                            w0[a] = 0.75f;
+                            w1[a] = 0.25f;
+                        } else {
+                            c0[a] = c;
+                            c1[a] = wrap(c - dir, C.cells[a], per);
+                            w0[a] = 1.25f;
+                            w1[a] = -0.25f;
+                        }
+                    }
+                    InterpTask it;
+                    it.dst = dst;
+                    for (int k = 0; k < 8; ++k) {
+                        int cc[3];
+                        float wt = 1.f;
+                        for (int a = 0; a < 3; ++a) {
+                            const int bit = (k >> a) & 1;
+                            cc[a] = bit ? c1[a] : c0[a];
+                            wt *= bit ? w1[a] : w0[a];
+                        }
+                        int cs;
+                        it.src[k] = cell_offset(m, l - 1, cc, &cs);
+                        if (cs < 0)
+                            return report_error(LBM_EINVAL,
+                                                "interpolation stencil outside the coarser level");
+                        it.w[k] = wt;
+                    }
+                    interps.push_back(it);
+                }
+    }
+    int st = upload(&L.copies, copies);
+    if (st != LBM_OK) return st;
+    L.ncopy = (int)copies.size();
+    st = upload(&L.interps, interps);
+    if (st != LBM_OK) return st;
+    L.ninterp = (int)interps.size();
+    if (l < m.lmax) {
+        const Level &F = m.lv[l + 1];
+        std::vector<RestrictTask> rs;
+        for (int b = 0; b < m.nblk; ++b) {
+            const int sf = F.slot[b];
+            if (sf < 0) continue;
+            const int sc = L.slot[b];
+            for (int z = 0; z < n; ++z)
+                for (int y = 0; y < n; ++y)
+                    for (int x = 0; x < n; ++x)
+                        rs.push_back({sc * Q * L.G + gidx(n, x, y, z),
+                                      sf * Q * F.G + gidx(F.n, 2 * x, 2 * y, 2 * z)});
+        }
+        st = upload(&L.restricts, rs);
+        if (st != LBM_OK) return st;
+        L.nrestrict = (int)rs.size();
+    }
+    return LBM_OK;
+}
+
+StepArgs step_args(const Mesh &m, int l) {
+    const Level &L = m.lv[l];
+    StepArgs a;
+    a.n = L.n;
+    a.G = L.G;
+    for (int k = 0; k < 3; ++k) a.cells[k] = L.cells[k];
+    a.periodic = m.periodic;
+    a.omega = (float)(1.0 / L.tau);
+    a.lid_x = (float)m.lid[0];
+    a.lid_z = (float)m.lid[2];
+    return a;
+}
+
+cudaError_t launch_step(const Mesh &m, int l, int threads, int cpt, cudaStream_t s, int src) {
+    const Level &L = m.lv[l];
+    const int ncell = L.n * L.n * L.n;
+    const int chunks = (ncell + threads * cpt - 1) / (threads * cpt);
+    dim3 grid(L.nslot, chunks);
+    k_step<<<grid, threads, 0, s>>>(L.buf[src], L.buf[src ^ 1], L.origin, step_args(m, l), cpt,
+                                    L.kmax);
+    return cudaGetLastError();
+}
+
+inline unsigned blocks_for(int n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// One level-l step with its ghost fill at time fraction theta, then the two sub-steps of the finer
+// level and the restriction onto this one.
+int advance(Mesh &m, int l, float theta, cudaStream_t s) {
+    Level &L = m.lv[l];
+    if (L.nslot == 0) return LBM_OK;  // no block reaches this level (nor a finer one)
+    if (L.ncopy)
+        k_copy<<<blocks_for(L.ncopy, 256), 256, 0, s>>>(L.copies, L.ncopy, L.buf[L.cur], L.G);
+    if (l > 0 && L.ninterp) {
+        const Level &C = m.lv[l - 1];
+        const float scale = (float)((L.tau - 1.0) / (2.0 * (C.tau - 1.0)));
+        k_interp<<<blocks_for(L.ninterp, 128), 128, 0, s>>>(L.interps, L.ninterp, L.buf[L.cur],
+                                                              L.G, C.buf[C.cur ^ 1], C.buf[C.cur],
+                                                              C.G, theta, scale);
+    }
+    MLCK(cudaGetLastError(), "ghost fill");
+    MLCK(cudaMemsetAsync(L.kmax, 0, sizeof(float) * L.nslot, s), "memset(kmax)");
+    MLCK(launch_step(m, l, L.threads, L.cpt, s, L.cur), "level step");
+    L.cur ^= 1;
+    if (l < m.lmax) {
+        int st = advance(m, l + 1, 0.f, s);
+        if (st == LBM_OK) st = advance(m, l + 1, 0.5f, s);
+        if (st != LBM_OK) return st;
+        const Level &F = m.lv[l + 1];
+        if (L.nrestrict) {
+            const float scale = (float)(2.0 * (L.tau - 1.0) / (F.tau - 1.0));
+            k_restrict<<<blocks_for(L.nrestrict, 128), 128, 0, s>>>(
+                L.restricts, L.nrestrict, L.buf[L.cur], L.G, F.buf[F.cur], F.n, F.G, scale);
+            MLCK(cudaGetLastError(), "restriction");
+        }
+    }
+    return LBM_OK;
+}
+
+// Time each launch shape of the level step once and keep the fastest.  The trial steps write the
+// level's other buffer; the caller re-fills both buffers afterwards.
+int autotune(Mesh &m, int l, cudaStream_t s) {
+    Level &L = m.lv[l];
+    if (L.nslot == 0) return LBM_OK;
+    const int ncell = L.n * L.n * L.n;
+    const int cand[][2] = {{128, 1}, {128, 2}, {256, 1}, {256, 2}, {256, 4}, {512, 1}, {512, 2}};
+    cudaEvent_t e0, e1;
+    MLCK(cudaEventCreate(&e0), "cudaEventCreate");
+    MLCK(cudaEventCreate(&e1), "cudaEventCreate");
+    float best = 1e30f;
+    for (const auto &c : cand) {
+        if (c[0] * c[1] > 2 * ncell && !(c[0] == 128 && c[1] == 1)) continue;
+        for (int k = 0; k < 2; ++k) MLCK(launch_step(m, l, c[0], c[1], s, L.cur), "autotune");
+        MLCK(cudaEventRecord(e0, s), "cudaEventRecord");
+        for (int k = 0; k < 3; ++k) MLCK(launch_step(m, l, c[0], c[1], s, L.cur), "autotune");
+        MLCK(cudaEventRecord(e1, s), "cudaEventRecord");
+        MLCK(cudaEventSynchronize(e1), "cudaEventSynchronize");
+        float ms = 0.f;
+        MLCK(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+        if (ms < best) {
+            best = ms;
+            L.threads = c[0];
+            L.cpt = c[1];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return LBM_OK;
+}
+
+int capture(Mesh &m, cudaGraphExec_t *out) {
+    cudaStream_t cap;
+    MLCK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "cudaStreamCreate");
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    int st = LBM_OK;
+    if (e == cudaSuccess) {
+        st = advance(m, 0, 0.f, cap);
+        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        if (e2 != cudaSuccess && st == LBM_OK) st = report_cuda_error(e2, "graph capture");
+    } else {
+        st = report_cuda_error(e, "graph capture");
+    }
+    if (st == LBM_OK) {
+        e = cudaGraphInstantiate(out, g, 0);
+        if (e != cudaSuccess) st = report_cuda_error(e, "cudaGraphInstantiate");
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    return st;
+}
+
+}  // namespace
+
+void destroy(Mesh *m) {
+    if (!m) return;
+    for (int k = 0; k < 2; ++k)
+        if (m->graph[k]) cudaGraphExecDestroy(m->graph[k]);
+    for (int l = 0; l < MAXL; ++l) {
+        Level &L = m->lv[l];
+        cudaFree(L.buf[0]);
+        cudaFree(L.buf[1]);
+        cudaFree(L.origin);
+        cudaFree(L.copies);
+        cudaFree(L.interps);
+        cudaFree(L.restricts);
+        cudaFree(L.kmax);
+    }
+    delete m;
+}
+
+bool same_layout(const Mesh *m, const int nb[3], int edge, int lmax, const int8_t *leaf) {
+    if (!m || m->edge != edge || m->lmax != lmax) return false;
+    for (int a = 0; a < 3; ++a)
+        if (m->nb[a] != nb[a]) return false;
+    return memcmp(m->leaf.data(), leaf, m->leaf.size()) == 0;
+}
+
+int build(Mesh **out, const int nb[3], int edge, int lmax, const int8_t *leaf, double tau_fine,
+          const double lid[3], int periodic, cudaStream_t s) {
+    *out = nullptr;
+    if (lmax < 0 || lmax >= MAXL) return report_error(LBM_EINVAL, "lmax must be 0, 1 or 2");
+    if (edge < 1 || edge % (1 << lmax) != 0 || edge / (1 << lmax) < 2)
+        return report_error(LBM_EINVAL,
+                            "block edge must be a multiple of 2^lmax with >= 2 coarse cells");
+    for (int a = 0; a < 3; ++a)
+        if (nb[a] < 1) return report_error(LBM_EINVAL, "need at least one block per axis");
+    Mesh *m = new Mesh();
+    for (int a = 0; a < 3; ++a) m->nb[a] = nb[a];
+    m->edge = edge;
+    m->lmax = lmax;
+    m->nblk = nb[0] * nb[1] * nb[2];
+    m->leaf.assign(leaf, leaf + m->nblk);
+    for (int a = 0; a < 3; ++a) m->lid[a] = lid[a];
+    m->periodic = periodic;
+    for (int b = 0; b < m->nblk; ++b)
+        if (leaf[b] < 0 || leaf[b] > lmax) {
+            destroy(m);
+            return report_error(LBM_EINVAL, "leaf level outside 0..lmax");
+        }
+    if (!balanced(*m)) {
+        destroy(m);
+        return report_error(LBM_EINVAL, "touching blocks differ by more than one level");
+    }
+    const double nu_fine = (tau_fine - 0.5) / 3.0;
+    int st = LBM_OK;
+    for (int l = 0; l <= lmax && st == LBM_OK; ++l) {
+        Level &L = m->lv[l];
+        const int h = 1 << (lmax - l);
+        L.n = edge / h;
+        L.G = (L.n + 2) * (L.n + 2) * (L.n + 2);
+        for (int a = 0; a < 3; ++a) L.cells[a] = nb[a] * L.n;
+        L.tau = 3.0 * nu_fine / h + 0.5;
+        if (lmax > 0 && fabs(L.tau - 1.0) < 1e-3) {
+            st = report_error(LBM_EINVAL, "a level's tau is 1: the rescaling divides by tau - 1");
+            break;
+        }
+        L.slot.assign(m->nblk, -1);
+        std::vector<int> origin;
+        for (int b = 0; b < m->nblk; ++b)
+            if (leaf[b] >= l) {
+                L.slot[b] = L.nslot++;
+                const int bz = b / (nb[0] * nb[1]), by = (b / nb[0]) % nb[1], bx = b % nb[0];
+                origin.push_back(bx * L.n);
+                origin.push_back(by * L.n);
+                origin.push_back(bz * L.n);
+            }
+        if ((long long)L.nslot * Q * L.G >= (1LL << 31)) {
+            st = report_error(LBM_ENOTSUP, "a level exceeds 2^31 population values");
+            break;
+        }
+        const size_t bytes = (size_t)L.nslot * Q * L.G * sizeof(float);
+        cudaError_t e = cudaMalloc((void **)&L.buf[0], bytes);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&L.buf[1], bytes);
+        if (e == cudaSuccess)
+            e = cudaMalloc((void **)&L.kmax, sizeof(float) * std::max(L.nslot, 1));
+        if (e != cudaSuccess) {
+            st = report_cuda_error(e, "cudaMalloc(level)");
+            break;
+        }
+        st = upload(&L.origin, origin);
+    }
+    for (int l = 0; l <= lmax && st == LBM_OK; ++l) st = build_tasks(*m, l);
+    for (int l = 0; l <= lmax && st == LBM_OK; ++l) st = autotune(*m, l, s);
+    if (st == LBM_OK) {
+        // the state at build time is rest, f_i = w_i everywhere (the trial steps are overwritten)
+        for (int l = 0; l <= lmax; ++l) {
+            if (m->lv[l].nslot == 0) continue;
+            for (int k = 0; k < 2; ++k)
+                k_fill_rest<<<1024, 256, 0, s>>>(m->lv[l].buf[k], m->lv[l].nslot, m->lv[l].G);
+            cudaMemsetAsync(m->lv[l].kmax, 0, sizeof(float) * std::max(m->lv[l].nslot, 1), s);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = report_cuda_error(e, "mesh set-up");
+    }
+    if (st != LBM_OK) {
+        destroy(m);
+        return st;
+    }
+    *out = m;
+    return LBM_OK;
+}
+
+int run_cycles(Mesh *m, int cycles, cudaStream_t s, bool graphs) {
+    for (int c = 0; c < cycles; ++c) {
+        if (graphs) {
+            const int par = m->lv[0].cur;
+            if (!m->graph[par]) {
+                int saved[MAXL];
+                for (int l = 0; l <= m->lmax; ++l) saved[l] = m->lv[l].cur;
+                const int st = capture(*m, &m->graph[par]);
+                for (int l = 0; l <= m->lmax; ++l) m->lv[l].cur = saved[l];
+                if (st != LBM_OK) return st;
+            }
+            MLCK(cudaGraphLaunch(m->graph[par], s), "cudaGraphLaunch");
+            // a cycle flips level 0 once; finer levels step an even number of times
+            m->lv[0].cur ^= 1;
+        } else {
+            const int st = advance(*m, 0, 0.f, s);
+            if (st != LBM_OK) return st;
+        }
+        m->cycles += 1;
+    }
+    return LBM_OK;
+}
+
+int block_max(Mesh *m, double *out_host, cudaStream_t s) {
+    std::vector<int> ls(m->nblk), ll(m->nblk);
+    for (int b = 0; b < m->nblk; ++b) {
+        ll[b] = m->leaf[b];
+        ls[b] = m->lv[ll[b]].slot[b];
+    }
+    int *dls = nullptr, *dll = nullptr;
+    double *dout = nullptr;
+    int st = upload(&dls, ls);
+    if (st == LBM_OK) st = upload(&dll, ll);
+    if (st == LBM_OK && cudaMalloc((void **)&dout, sizeof(double) * m->nblk) != cudaSuccess)
+        st = report_error(LBM_ENOMEM, "cudaMalloc(block max)");
+    if (st == LBM_OK) {
+        const float *k1 = m->lmax >= 1 ? m->lv[1].kmax : m->lv[0].kmax;
+        const float *k2 = m->lmax >= 2 ? m->lv[2].kmax : k1;
+        k_leaf_max<<<blocks_for(m->nblk, 256), 256, 0, s>>>(dls, dll, m->nblk, m->lv[0].kmax, k1,
+                                                            k2, dout);
+        cudaError_t e = cudaMemcpyAsync(out_host, dout, sizeof(double) * m->nblk,
+                                        cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = report_cuda_error(e, "block max");
+    }
+    cudaFree(dls);
+    cudaFree(dll);
+    cudaFree(dout);
+    return st;
+}
+
+// interior populations of physical block b at level l, f[i][z][y][x] as doubles (host)
+int get_block(Mesh *m, int l, int b, double *out, cudaStream_t s) {
+    if (l < 0 || l > m->lmax || b < 0 || b >= m->nblk || m->lv[l].slot[b] < 0)
+        return report_error(LBM_EINVAL, "no such block at that level");
+    const Level &L = m->lv[l];
+    std::vector<float> tmp((size_t)Q * L.G);
+    MLCK(cudaMemcpyAsync(tmp.data(), L.buf[L.cur] + (size_t)L.slot[b] * Q * L.G,
+                         tmp.size() * sizeof(float), cudaMemcpyDeviceToHost, s),
+         "cudaMemcpyAsync");
+    MLCK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    const int n = L.n;
+    for (int i = 0; i < Q; ++i)
+        for (int z = 0; z < n; ++z)
+            for (int y = 0; y < n; ++y)
+                for (int x = 0; x < n; ++x)
+                    out[(((size_t)i * n + z) * n + y) * n + x] =
+                        tmp[(size_t)i * L.G + gidx(n, x, y, z)];
+    return LBM_OK;
+}
+
+int set_block(Mesh *m, int l, int b, const double *in, cudaStream_t s) {
+    if (l < 0 || l > m->lmax || b < 0 || b >= m->nblk || m->lv[l].slot[b] < 0)
+        return report_error(LBM_EINVAL, "no such block at that level");
+    Level &L = m->lv[l];
+    std::vector<float> tmp((size_t)Q * L.G);
+    float *dst = L.buf[L.cur] + (size_t)L.slot[b] * Q * L.G;
+    MLCK(cudaMemcpyAsync(tmp.data(), dst, tmp.size() * sizeof(float), cudaMemcpyDeviceToHost, s),
+         "cudaMemcpyAsync");
+    MLCK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    const int n = L.n;
+    for (int i = 0; i < Q; ++i)
+        for (int z = 0; z < n; ++z)
+            for (int y = 0; y < n; ++y)
+                for (int x = 0; x < n; ++x)
+                    tmp[(size_t)i * L.G + gidx(n, x, y, z)] =
+                        (float)in[(((size_t)i * n + z) * n + y) * n + x];
+    MLCK(cudaMemcpyAsync(dst, tmp.data(), tmp.size() * sizeof(float), cudaMemcpyHostToDevice, s),
+         "cudaMemcpyAsync");
+    MLCK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    return LBM_OK;
+}
+
+int info(const Mesh *m, int l, int *n, double *tau, int *nslot, int *threads, int *cpt) {
+    if (l < 0 || l > m->lmax) return report_error(LBM_EINVAL, "no such level");
+    const Level &L = m->lv[l];
+    if (n) *n = L.n;
+    if (tau) *tau = L.tau;
+    if (nslot) *nslot = L.nslot;
+    if (threads) *threads = L.threads;
+    if (cpt) *cpt = L.cpt;
+    return LBM_OK;
+}
+
+long long cells_per_cycle(const Mesh *m) {
+    long long c = 0;
+    for (int l = 0; l <= m->lmax; ++l)
+        c += (long long)m->lv[l].nslot * m->lv[l].n * m->lv[l].n * m->lv[l].n * (1LL << l);
+    return c;
+}
+
+}  // namespace ml
+}  // namespace lbm

@@ -104,12 +104,12 @@ extern "C" LBM_API int lbm_step_noalloc(int lattice, int dtype, int nx, int ny, 
     p.err = nullptr;
     p.tile_zero = nullptr;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // the one-cell kernel writes every tile maximum with a plain store, so the scratch needs no
-    // clearing between calls
+    // the automatic kernel choice (the same as lbm_step's default) only picks kernels that write
+    // every tile maximum with a plain store, so the scratch needs no clearing between calls
     e = (lattice == LBM_D2Q9)
-            ? lbm::step_d2q9(dtype, f_in_dev, f_out_dev, p, 1, tiles, nullptr, s, lbm::KERNEL_CELL)
+            ? lbm::step_d2q9(dtype, f_in_dev, f_out_dev, p, 1, tiles, nullptr, s, lbm::KERNEL_AUTO)
             : lbm::step_d3q19(dtype, f_in_dev, f_out_dev, p, 1, tiles, nullptr, s,
-                              lbm::KERNEL_CELL);
+                              lbm::KERNEL_AUTO);
     if (e != cudaSuccess) return lbm::report_cuda_error(e, "fused step launch");
     const int m = block / LBM_TILE, mz = (dim == 3) ? m : 1;
     const int nbx = (nx + block - 1) / block, nby = (ny + block - 1) / block;

@@ -100,9 +100,12 @@ cudaError_t launch_fused_step_tma(const void *fin, void *fout, const StepParams 
 
 cudaError_t step_d3q19(int dtype, const void *fin, void *fout, const StepParams &p, int mode,
                        void *tile_max, void *k_field, cudaStream_t s, int variant) {
-    const bool pair = dtype != 0 && (p.nx % 2 == 0) && variant == KERNEL_PAIR;
+    // automatic choice, from GB300 measurements at 256^3 / 512^3: the one-cell kernel for FP32
+    // and FP64, the two-cell packed kernel for 16-bit storage
+    const bool pair_ok = dtype != 0 && (p.nx % 2 == 0);
+    const bool pair = pair_ok && (variant == KERNEL_PAIR || (variant == KERNEL_AUTO && dtype >= 2));
     const bool tma = tma_applicable(dtype, p.nx) && variant == KERNEL_TMA;
-    if ((variant == KERNEL_PAIR && !pair) || (variant == KERNEL_TMA && !tma))
+    if ((variant == KERNEL_PAIR && !pair_ok) || (variant == KERNEL_TMA && !tma))
         return cudaErrorInvalidValue;
     switch (dtype) {
         case 0: return launch_fused_step<D3Q19, 0>(fin, fout, p, mode, tile_max, k_field, s);

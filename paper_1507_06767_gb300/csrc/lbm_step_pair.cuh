@@ -50,6 +50,68 @@ struct PairIO<3> {  // bfloat16 pair, shifted storage
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
+// Moments, equilibrium, Knudsen sensor and BGK collision of two cells at once in packed FP32
+// pairs (FFMA2 / FADD2 / FMUL2 of sm_100+), from their gathered deviations df_i = f_i - w_i.
+// Calls store(i, v) with the post-collision value of direction i in the storage convention of DT
+// (f* for plain storage, f* - w_i for shifted storage) and returns the two sensors (MODE != 0).
+template <class L, int DT, int MODE, class Store>
+__device__ __forceinline__ float2 relax_pair(const float2 *df, float omega_s, Store &&store) {
+    using S = Storage<DT>;
+    constexpr int Q = L::Q;
+    const float2 one = f2(1.f);
+    float2 drho = df[0], jx = f2(0.f), jy = f2(0.f), jz = f2(0.f);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) drho = __fadd2_rn(drho, df[i]);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        if (L::cx(i) == 1) jx = __fadd2_rn(jx, df[i]);
+        if (L::cx(i) == -1) jx = __fadd2_rn(jx, make_float2(-df[i].x, -df[i].y));
+        if (L::cy(i) == 1) jy = __fadd2_rn(jy, df[i]);
+        if (L::cy(i) == -1) jy = __fadd2_rn(jy, make_float2(-df[i].x, -df[i].y));
+        if (L::cz(i) == 1) jz = __fadd2_rn(jz, df[i]);
+        if (L::cz(i) == -1) jz = __fadd2_rn(jz, make_float2(-df[i].x, -df[i].y));
+    }
+    const float2 rho = __fadd2_rn(one, drho);
+    const float2 inv_rho = make_float2(__frcp_rn(rho.x), __frcp_rn(rho.y));
+    const float2 ux = __fmul2_rn(jx, inv_rho), uy = __fmul2_rn(jy, inv_rho),
+                 uz = __fmul2_rn(jz, inv_rho);
+    float2 usq = __fmul2_rn(ux, ux);
+    usq = __ffma2_rn(uy, uy, usq);
+    if (L::D == 3) usq = __ffma2_rn(uz, uz, usq);
+    const float2 neg_usq15 = __fmul2_rn(f2(-1.5f), usq);
+    const float2 neg_omega = f2(-omega_s);
+
+    float2 ksum = f2(0.f);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+        // c.u with the constant components folded
+        float2 cu = f2(0.f);
+        if (cx == 1) cu = ux;
+        if (cx == -1) cu = make_float2(-ux.x, -ux.y);
+        if (cy != 0) cu = (cx == 0) ? (cy == 1 ? uy : make_float2(-uy.x, -uy.y))
+                                    : __ffma2_rn(f2((float)cy), uy, cu);
+        if (cz != 0) cu = (cx == 0 && cy == 0) ? (cz == 1 ? uz : make_float2(-uz.x, -uz.y))
+                                               : __ffma2_rn(f2((float)cz), uz, cu);
+        // P = c.u/cs2 + ((c.u)^2 - cs2 u.u)/(2 cs2^2) = cu (3 + 4.5 cu) - 1.5 u.u
+        const float2 t = __ffma2_rn(f2(4.5f), cu, f2(3.f));
+        const float2 P = __ffma2_rn(cu, t, neg_usq15);
+        const float w = weight<L, float>(i);
+        const float2 A = __ffma2_rn(rho, P, drho);       // (f^eq_i - w_i) / w_i
+        const float2 fneq = __ffma2_rn(f2(-w), A, df[i]);  // f_i - f^eq_i
+        if (MODE != 0) {
+            const float2 feqw = __ffma2_rn(rho, P, rho);   // f^eq_i / w_i
+            const float2 r = make_float2(fabsf(fneq.x) * __frcp_rn(feqw.x),
+                                         fabsf(fneq.y) * __frcp_rn(feqw.y));
+            ksum = __ffma2_rn(r, f2(1.f / w), ksum);
+        }
+        float2 v = __ffma2_rn(neg_omega, fneq, df[i]);
+        if (!S::SHIFTED) v = __fadd2_rn(v, f2(w));
+        store(i, v);
+    }
+    return __fmul2_rn(ksum, f2(1.f / (float)Q));
+}
+
 template <class L, int DT, int MODE>
 __global__ void __launch_bounds__(CTA_X *CTA_Y, LBM_PAIR_MIN_BLOCKS)
     fused_step_pair_kernel(const typename Storage<DT>::T *__restrict__ fin,
@@ -69,8 +131,6 @@ __global__ void __launch_bounds__(CTA_X *CTA_Y, LBM_PAIR_MIN_BLOCKS)
     const size_t N = (size_t)nx * ny * nz;
     const size_t nxy = (size_t)nx * ny;
 
-    const float2 omega = f2((float)p.omega);
-    const float2 one = f2(1.f);
     int kmax = 0;
 
     if (MODE != 0 && p.tile_zero) {
@@ -119,63 +179,11 @@ __global__ void __launch_bounds__(CTA_X *CTA_Y, LBM_PAIR_MIN_BLOCKS)
             for (int i = 0; i < Q; ++i) df[i].y = a[i];
         }
 
-        // moments as deviations from rest, both cells at once
-        float2 drho = df[0], jx = f2(0.f), jy = f2(0.f), jz = f2(0.f);
-#pragma unroll
-        for (int i = 1; i < Q; ++i) drho = __fadd2_rn(drho, df[i]);
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            if (L::cx(i) == 1) jx = __fadd2_rn(jx, df[i]);
-            if (L::cx(i) == -1) jx = __fadd2_rn(jx, make_float2(-df[i].x, -df[i].y));
-            if (L::cy(i) == 1) jy = __fadd2_rn(jy, df[i]);
-            if (L::cy(i) == -1) jy = __fadd2_rn(jy, make_float2(-df[i].x, -df[i].y));
-            if (L::cz(i) == 1) jz = __fadd2_rn(jz, df[i]);
-            if (L::cz(i) == -1) jz = __fadd2_rn(jz, make_float2(-df[i].x, -df[i].y));
-        }
-        const float2 rho = __fadd2_rn(one, drho);
-        const float2 inv_rho = make_float2(__frcp_rn(rho.x), __frcp_rn(rho.y));
-        const float2 ux = __fmul2_rn(jx, inv_rho), uy = __fmul2_rn(jy, inv_rho),
-                     uz = __fmul2_rn(jz, inv_rho);
-        float2 usq = __fmul2_rn(ux, ux);
-        usq = __ffma2_rn(uy, uy, usq);
-        if (L::D == 3) usq = __ffma2_rn(uz, uz, usq);
-        const float2 usq15 = __fmul2_rn(f2(1.5f), usq);
-        const float2 neg_usq15 = make_float2(-usq15.x, -usq15.y);
-
-        float2 ksum = f2(0.f);
         T *out0 = fout + idx0;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-            // c.u with the constant components folded
-            float2 cu = f2(0.f);
-            if (cx == 1) cu = ux;
-            if (cx == -1) cu = make_float2(-ux.x, -ux.y);
-            if (cy != 0) cu = (cx == 0) ? (cy == 1 ? uy : make_float2(-uy.x, -uy.y))
-                                        : __ffma2_rn(f2((float)cy), uy, cu);
-            if (cz != 0) cu = (cx == 0 && cy == 0) ? (cz == 1 ? uz : make_float2(-uz.x, -uz.y))
-                                                   : __ffma2_rn(f2((float)cz), uz, cu);
-            // P = c.u/cs2 + ((c.u)^2 - cs2 u.u)/(2 cs2^2) = cu (3 + 4.5 cu) - 1.5 u.u
-            const float2 t = __ffma2_rn(f2(4.5f), cu, f2(3.f));
-            const float2 P = __ffma2_rn(cu, t, neg_usq15);
-            const float w = weight<L, float>(i);
-            const float2 A = __ffma2_rn(rho, P, drho);           // (f^eq_i - w_i) / w_i
-            const float2 fneq = __ffma2_rn(f2(-w), A, df[i]);      // f_i - f^eq_i
-            if (MODE != 0) {
-                const float2 feqw = __ffma2_rn(rho, P, rho);       // f^eq_i / w_i
-                const float2 r = make_float2(fabsf(fneq.x) * __frcp_rn(feqw.x),
-                                             fabsf(fneq.y) * __frcp_rn(feqw.y));
-                ksum = __ffma2_rn(r, f2(1.f / w), ksum);
-            }
-            float2 dnew = __ffma2_rn(make_float2(-omega.x, -omega.y), fneq, df[i]);
-            if (!S::SHIFTED) dnew = __fadd2_rn(dnew, f2(w));
-            PairIO<DT>::store2(out0 + (size_t)i * N, dnew);
-            (void)cx;
-            (void)cy;
-            (void)cz;
-        }
+        const float2 K = relax_pair<L, DT, MODE>(df, (float)p.omega, [&](int i, float2 v) {
+            PairIO<DT>::store2(out0 + (size_t)i * N, v);
+        });
         if (MODE != 0) {
-            const float2 K = __fmul2_rn(ksum, f2(1.f / (float)Q));
             const int kb = max(__float_as_int(K.x), __float_as_int(K.y));
             kmax = kb > kmax ? kb : kmax;
             if (MODE == 2) {

@@ -83,6 +83,10 @@ _SIGS = {
     "lbm_conservation": (_i, [_h, _dp, _dp]),
     "lbm_kernel_time": (_i, [_h, _dp, ctypes.POINTER(_ll)]),
     "lbm_blocks_step": (_i, [_h, _vp]),
+    "lbm_blocks_get": (_i, [_h, _i, _i, _vp]),
+    "lbm_blocks_set": (_i, [_h, _i, _i, _vp]),
+    "lbm_blocks_info": (_i, [_h, _i, ctypes.POINTER(_i), _dp, ctypes.POINTER(_i),
+                             ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_ll)]),
     "lbm_set_sensor_average": (_i, [_h, _i]),
     "lbm_sensor_average": (_i, [_h, _i, _vp, ctypes.POINTER(_ll)]),
     "lbm_levels": (_i, [_h, _i, _d, _d, _i, _i, _i, _vp]),
@@ -283,8 +287,101 @@ def lbm_kernel_time(h):
     return ms.value, n.value
 
 
+class LevelBatch(ctypes.Structure):
+    """struct lbm_level_batch of include/lbm.h."""
+    _fields_ = [("nbx", _i), ("nby", _i), ("nbz", _i), ("edge", _i), ("lmax", _i),
+                ("leaf", ctypes.c_void_p), ("cycles", _i), ("block_max", ctypes.c_void_p)]
+
+
 def lbm_blocks_step(h, batch=None) -> int:
-    return _ck(_lib.lbm_blocks_step(h, _ptr(batch)), "lbm_blocks_step")
+    p = ctypes.byref(batch) if isinstance(batch, LevelBatch) else _ptr(batch)
+    return _ck(_lib.lbm_blocks_step(h, p), "lbm_blocks_step")
+
+
+def lbm_blocks_get(h, level: int, block: int, out) -> int:
+    return _ck(_lib.lbm_blocks_get(h, level, block, _ptr(out)), "lbm_blocks_get")
+
+
+def lbm_blocks_set(h, level: int, block: int, arr) -> int:
+    return _ck(_lib.lbm_blocks_set(h, level, block, _ptr(arr)), "lbm_blocks_set")
+
+
+def lbm_blocks_info(h, level: int):
+    """(cells per block edge, tau, blocks at the level, threads, cells per thread, cell updates
+    per cycle)."""
+    n, nb, th, cpt = _i(), _i(), _i(), _i()
+    tau = ctypes.c_double()
+    cu = ctypes.c_longlong()
+    _ck(_lib.lbm_blocks_info(h, level, ctypes.byref(n), ctypes.byref(tau), ctypes.byref(nb),
+                             ctypes.byref(th), ctypes.byref(cpt), ctypes.byref(cu)),
+        "lbm_blocks_info")
+    return n.value, tau.value, nb.value, th.value, cpt.value, cu.value
+
+
+class BlockMesh:
+    """Multi-level block mesh on a handle: leaf[nbz, nby, nbx] leaf levels, block edge `edge`."""
+
+    def __init__(self, leaf, edge, lmax, tau_fine, lid=(0.0, 0.0), periodic=0, graphs=True):
+        import torch  # noqa: F401  (the caller's CUDA context)
+
+        self.leaf = np.ascontiguousarray(leaf, dtype=np.int8)
+        nbz, nby, nbx = self.leaf.shape
+        self.nb = (nbx, nby, nbz)
+        self.edge, self.lmax = int(edge), int(lmax)
+        self.h = lbm_create(LBM_D3Q19, nbx * edge, nby * edge, nbz * edge, float(tau_fine))
+        lbm_set_lid(self.h, float(lid[0]), float(lid[1]))
+        lbm_set_periodic(self.h, int(periodic))
+        lbm_set_graphs(self.h, 1 if graphs else 0)
+        self.step(0)
+
+    def _batch(self, cycles, out):
+        return LevelBatch(self.nb[0], self.nb[1], self.nb[2], self.edge, self.lmax,
+                          self.leaf.ctypes.data, int(cycles),
+                          out.ctypes.data if out is not None else None)
+
+    def step(self, cycles, block_max=False):
+        out = np.empty(self.leaf.size) if block_max else None
+        lbm_blocks_step(self.h, self._batch(cycles, out))
+        return out
+
+    def info(self, level):
+        return lbm_blocks_info(self.h, level)
+
+    def block_index(self, bx, by, bz):
+        return (bz * self.nb[1] + by) * self.nb[0] + bx
+
+    def get_block(self, level, b):
+        n = self.info(level)[0]
+        out = np.empty((19, n, n, n))
+        lbm_blocks_get(self.h, level, int(b), out)
+        return out
+
+    def set_block(self, level, b, f):
+        lbm_blocks_set(self.h, level, int(b), np.ascontiguousarray(f, dtype=np.float64))
+
+    def leaf_field(self, level):
+        n = self.info(level)[0]
+        nbx, nby, nbz = self.nb
+        out = np.full((19, nbz * n, nby * n, nbx * n), np.nan)
+        for bz in range(nbz):
+            for by in range(nby):
+                for bx in range(nbx):
+                    if self.leaf[bz, by, bx] >= level:
+                        out[:, bz * n:(bz + 1) * n, by * n:(by + 1) * n, bx * n:(bx + 1) * n] = \
+                            self.get_block(level, self.block_index(bx, by, bz))
+        return out
+
+    def close(self):
+        if self.h:
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            if self.h and _lib is not None:
+                self.close()
+        except Exception:
+            pass
 
 
 def lbm_step_noalloc(lattice, dtype, nx, ny, nz, tau, lid_x, lid_z, periodic, f_in_dev, f_out_dev,

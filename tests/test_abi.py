@@ -73,7 +73,12 @@ def test_host_side_setters_and_queries(L):
                 call(h, *args)
             assert ei.value.status == L.LBM_EINVAL, call
         with pytest.raises(L.LbmError) as ei:
-            L.lbm_blocks_step(h)
+            L.lbm_blocks_step(h)  # NULL batch
+        assert ei.value.status == L.LBM_EINVAL
+        leaf = np.zeros(1, dtype=np.int8)
+        batch = L.LevelBatch(1, 1, 1, 40, 0, leaf.ctypes.data, 0, None)
+        with pytest.raises(L.LbmError) as ei:  # BF16 storage (set above) is not supported
+            L.lbm_blocks_step(h, batch)
         assert ei.value.status == L.LBM_ENOTSUP
         L.lbm_set_block(h, 32)
         L.lbm_set_lid(h, 0.05, 0.01)

@@ -1,0 +1,123 @@
+"""GPU parity of the multi-level block mesh (lbm_blocks_step, FP32) with the FP64 oracle
+(oracle/lbm_multilevel.c), through the C ABI.
+
+Tolerances: populations max|f_gpu - f_ref| / max|f_ref| <= 2e-6 after 12 cycles of a 3-level
+lid-driven mesh (FP32 rounding of f, interpolation and restriction add a few roundings per cycle);
+block sensor maxima 1e-4 relative (K is a mean of |f^neq| / f^eq with f^neq ~ 1e-4 f).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1507_06767_gb300 as pkg
+
+    return pkg
+
+
+def three_level_leaf():
+    leaf = np.ones((4, 3, 3), np.int8)
+    leaf[0, :, :] = 0
+    leaf[2, 2, 1] = 2  # next to the lid plane (y = top)
+    leaf[2, 1, 1] = 2
+    return leaf
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    m = ~np.isnan(b)
+    return float(np.abs(a[m] - b[m]).max() / np.abs(b[m]).max())
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_three_level_cavity_matches_oracle(L, graphs):
+    leaf = three_level_leaf()
+    edge, lmax, tau, cycles = 8, 2, 0.6, 12
+    g = L.BlockMesh(leaf, edge, lmax, tau, lid=(0.1, 0.02), graphs=graphs)
+    o = O.MultiLevel(leaf, edge, lmax, tau, lid=(0.1, 0.0, 0.02))
+    for level in range(lmax + 1):
+        n, tau_l, nblocks, threads, cpt, _ = g.info(level)
+        assert (n, nblocks) == (o.level_info(level)[0], int((leaf >= level).sum()))
+        assert abs(tau_l - o.level_info(level)[1]) < 1e-15
+        assert threads in (128, 256, 512) and cpt in (1, 2, 4)
+    bm = g.step(cycles, block_max=True)
+    o.cycles(cycles)
+    for level in range(lmax + 1):
+        assert rel(g.leaf_field(level), o.leaf_field(level)) < 2e-6, level
+    ref = o.block_max()
+    assert rel(bm, ref) < 1e-4
+    g.close()
+
+
+def test_graph_replay_is_bitwise_direct_launches(L):
+    leaf = three_level_leaf()
+    out = []
+    for graphs in (True, False):
+        g = L.BlockMesh(leaf, 8, 2, 0.6, lid=(0.1, 0.0), graphs=graphs)
+        g.step(5)
+        out.append([g.leaf_field(level) for level in range(3)])
+        g.close()
+    for a, b in zip(*out):
+        assert np.array_equal(a, b, equal_nan=True)
+
+
+def test_couette_across_interface_on_gpu(L):
+    """The Couette pin of the oracle, on the GPU: linear profile across a level interface."""
+    U, D = 0.01, 16.0
+    leaf = np.zeros((1, 4, 1), np.int8)
+    leaf[:, 2:, :] = 1
+    g = L.BlockMesh(leaf, 4, 1, 0.8, lid=(U, 0.0), periodic=L.LBM_PERIODIC_X | L.LBM_PERIODIC_Z)
+    g.step(6000)
+    for level, lo, hi in ((0, 0.0, 8.0), (1, 8.0, 16.0)):
+        f = g.leaf_field(level)
+        with np.errstate(invalid="ignore"):
+            ux = (f[[1, 7, 9, 11, 13]].sum(0) - f[[2, 8, 10, 12, 14]].sum(0)) / f.sum(0)
+        h = 2 ** (1 - level)
+        y = (np.arange(ux.shape[1]) + 0.5) * h
+        sel = (y > lo) & (y < hi)
+        prof = np.array([np.nanmean(ux[:, j, :]) for j in np.where(sel)[0]])
+        assert np.abs(prof - U * y[sel] / D).max() < 2e-4 * U
+    g.close()
+
+
+def test_single_level_mesh_matches_uniform_path(L):
+    """With one level the block mesh is the uniform lattice: it follows the uniform fused step to
+    FP32 rounding (different kernels, same arithmetic)."""
+    leaf = np.zeros((2, 2, 3), np.int8)
+    g = L.BlockMesh(leaf, 8, 0, 0.7, lid=(0.1, 0.0))
+    g.step(20)
+    u = L.Lattice(L.LBM_D3Q19, 24, 16, 16, 0.7, dtype=L.LBM_F32, lid=(0.1, 0.0))
+    u.step(20)
+    assert rel(g.leaf_field(0), u.populations()) < 1e-6
+    g.close()
+    u.close()
+
+
+def test_block_mesh_argument_errors(L):
+    h = L.lbm_create(L.LBM_D3Q19, 24, 8, 8, 0.6)
+    try:
+        bad = np.array([2, 0, 0], np.int8)  # a level-2 block touching level 0
+        with pytest.raises(L.LbmError) as ei:
+            L.lbm_blocks_step(h, L.LevelBatch(3, 1, 1, 8, 2, bad.ctypes.data, 1, None))
+        assert ei.value.status == L.LBM_EINVAL
+        ok = np.zeros(3, np.int8)
+        with pytest.raises(L.LbmError) as ei:  # 3 x 4 != 24
+            L.lbm_blocks_step(h, L.LevelBatch(3, 1, 1, 4, 0, ok.ctypes.data, 1, None))
+        assert ei.value.status == L.LBM_EINVAL
+        with pytest.raises(L.LbmError) as ei:
+            L.lbm_blocks_get(h, 0, 0, np.empty(1))
+        assert ei.value.status == L.LBM_ESTATE
+    finally:
+        L.lbm_destroy(h)
