@@ -83,24 +83,35 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+def step_kernel_of(w):
+    """Name of the fused step kernel the library picks for the workload (LBM_KERNEL_AUTO: the
+    two-cell packed kernel for 16-bit storage with an even nx, else the one-cell kernel) and the
+    headers that define it."""
+    if w["dtype"] in ("F16S", "BF16S") and w["n"] % 2 == 0:
+        return "fused_step_pair_kernel", ("lbm_step_pair.cuh", "lbm_step.cuh", "lbm_traits.cuh")
+    return "fused_step_kernel", ("lbm_step.cuh", "lbm_traits.cuh")
+
+
+def kernel_source_hash(w):
     h = hashlib.sha256()
-    for fn in ("lbm_step.cuh", "lbm_traits.cuh"):
+    for fn in step_kernel_of(w)[1]:
         with open(os.path.join(ROOT, "paper_1507_06767_gb300", "csrc", fn), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload):
+def recorded_traffic(workload, w):
     """DRAM bytes per launch of the fused step from the committed ncu summary, if it was taken on
-    the current kernel source; else None."""
+    the current kernel source at the lattice size run now; else None."""
+    if w["n"] != WORKLOADS[workload]["n"]:
+        return None
     path = os.path.join(ROOT, "profiles", f"fused_step_{workload}.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     m_src = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
     m_tr = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    if not m_src or not m_tr or m_src.group(1) != kernel_source_hash():
+    if not m_src or not m_tr or m_src.group(1) != kernel_source_hash(w):
         return None
     return float(m_tr.group(1))
 
@@ -388,8 +399,8 @@ def run_ours(args, w, ws, rank, local):
     avg_kernel_ms = k_ms / max(k_n, 1)
     achieved = per_launch_bytes / (avg_kernel_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": recorded_traffic(args.workload),
-                "peak_kind": peak_kind, "kernel": "fused_step_kernel",
+                "frac": round(achieved / peak, 4), "traffic": recorded_traffic(args.workload, w),
+                "peak_kind": peak_kind, "kernel": step_kernel_of(w)[0],
                 "kernel_ms": round(avg_kernel_ms, 5),
                 "algorithmic_bytes_per_launch": per_launch_bytes}
     # launches of our kernels in the timed region: fused step every step, plus tile->block and
@@ -411,7 +422,7 @@ def run_ours(args, w, ws, rank, local):
         "dtype": DTYPE_NAME[w["dtype"]],
         "data": "synthetic (lid-driven cavity from rest)",
         "config": {"workload": args.workload, "lattice": f"D{3 if q == 19 else 2}Q{q}",
-                   "cells": cells, "re": w["re"], "tau": round(tau, 6), "lid_u": w["u"],
+                   "edge": n, "cells": cells, "re": w["re"], "tau": round(tau, 6), "lid_u": w["u"],
                    "sensor_every": w["sensor_every"], "block": w["block"], "blocks": nb,
                    "flag_rule": w["rule"], "flag_param": param,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
@@ -499,10 +510,17 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--edge", type=int, default=None,
+                    help="run the workload on a lattice of this edge instead (small profiling "
+                         "captures); the JSON line then names the edge in its config")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.edge is not None:
+        if w["rule"] == "blocks" or args.edge < 8:
+            ap.error("--edge applies to the uniform-lattice workloads, edge >= 8")
+        w["n"] = args.edge
     ws, rank, local = dist_env()
 
     if args.impl == "reference":

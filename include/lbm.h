@@ -350,6 +350,59 @@ LBM_API int lbm_blocks_set(lbm_t *h, int level, int block, const double *in_host
 LBM_API int lbm_blocks_info(lbm_t *h, int level, int *n, double *tau, int *nblocks, int *threads,
                             int *cells_per_thread, long long *cell_updates_per_cycle);
 
+/*
+ * Regridding of one refinement level from the sensor (Sec. 5.2: cells flagged by the sensor, one
+ * layer of buffer cells, refinement boxes holding at least 80 % flagged cells and subdivided
+ * otherwise, proper nesting inside the next coarser level with a row of coarse buffer cells).
+ * The clustering is the point-clustering method of Berger and Rigoutsos (1991), which the paper's
+ * solver uses; the steps, in tag cells of coarsen^d lattice cells (coarsen^2 x 1 for D2Q9):
+ *
+ *   1. tag a tag cell if the field exceeds `threshold` (strict >) in one of its cells or one of
+ *      them is NaN;
+ *   2. tag every tag cell within Chebyshev distance `buffer` of a tagged one (periodic axes of the
+ *      handle wrap, the domain edge stops the buffer elsewhere);
+ *   3. if `allowed` is not NULL (tx * ty * tz bytes, x fastest, nonzero = covered by the coarser
+ *      level), keep a tag only where every tag cell within Chebyshev distance `nest` is covered,
+ *      positions beyond a non-periodic domain edge counting as covered;
+ *   4. cluster, starting from the whole tag grid: shrink a box to the bounding box of its tags
+ *      (drop it if empty); accept it if tags >= efficiency * volume; else cut it at the empty
+ *      slab (hole) nearest the centre of its axis (least |2p - L|; ties: longer axis, lower axis,
+ *      lower p; the hole starts the upper piece); else at the strongest strict sign change of the
+ *      signature's second difference D[i] = s[i-1] - 2 s[i] + s[i+1], between slabs i and i + 1,
+ *      strength |D[i+1] - D[i]| (ties: nearer the centre, longer axis, lower axis, lower p); else
+ *      at floor(L / 2) of the longest axis (ties: lower axis).  A cut is admissible only if both
+ *      pieces are >= min_width slabs long; without one the box is accepted as it is.  Signatures
+ *      are the tag counts of the slabs normal to each axis.
+ *
+ * field_dev is a device array of nx * ny * nz doubles (x fastest), or NULL for the handle's
+ * per-cell sensor of its most recent sensor step (lbm_set_sensor_field(h, 1) before stepping;
+ * LBM_ESTATE otherwise).  Boxes come back in lattice cells, half-open ([lo, hi) per axis, the
+ * high end cut at the lattice edge), sorted by (lo_z, lo_y, lo_x); tag cells in `boxes` keep their
+ * order.  *nboxes receives the number of boxes; if it exceeds max_boxes, nothing is written to
+ * `boxes` and the call returns LBM_EINVAL.  ntagged (may be NULL) receives the number of tag cells
+ * tagged after steps 1-3, tags_out (host, tx * ty * tz bytes, may be NULL) the tags themselves
+ * (0/1).  Tag, buffer, nesting and the slab counts of each round of boxes run on the GPU; the cut
+ * decisions are made on the host between rounds.  Synchronises.  Arguments out of range
+ * (coarsen < 1, buffer < 0, nest < 0, min_width < 1, efficiency outside [0, 1] or NaN) give
+ * LBM_EINVAL.
+ */
+typedef struct lbm_box {
+    int lo[3];  /* x, y, z */
+    int hi[3];
+} lbm_box;
+typedef struct lbm_regrid_params {
+    int coarsen;             /* tag cell edge in lattice cells (>= 1) */
+    double threshold;        /* T of step 1 */
+    int buffer;              /* step 2 (the paper uses 1) */
+    const uint8_t *allowed;  /* step 3 mask (host) or NULL */
+    int nest;                /* step 3 buffer (the paper uses 1) */
+    double efficiency;       /* step 4 (the paper uses 0.8) */
+    int min_width;           /* step 4, in tag cells (>= 1) */
+} lbm_regrid_params;
+LBM_API int lbm_regrid(lbm_t *h, const double *field_dev, const lbm_regrid_params *p,
+                       lbm_box *boxes, int max_boxes, int *nboxes, long long *ntagged,
+                       uint8_t *tags_out);
+
 #ifdef __cplusplus
 }
 #endif

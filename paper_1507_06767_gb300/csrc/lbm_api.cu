@@ -1001,4 +1001,50 @@ LBM_API int lbm_blocks_info(lbm_t *h, int level, int *n, double *tau, int *nbloc
     return lbm::ml::info(h->mesh, level, n, tau, nblocks, threads, cells_per_thread);
 }
 
+LBM_API int lbm_regrid(lbm_t *h, const double *field_dev, const lbm_regrid_params *p,
+                       lbm_box *boxes, int max_boxes, int *nboxes, long long *ntagged,
+                       uint8_t *tags_out) {
+    CHECK_H(h);
+    if (!p || !nboxes) return fail(LBM_EINVAL, "lbm_regrid: NULL params or nboxes");
+    if (max_boxes < 0 || (max_boxes > 0 && !boxes))
+        return fail(LBM_EINVAL, "lbm_regrid: boxes is NULL or max_boxes < 0");
+    if (p->coarsen < 1 || p->buffer < 0 || p->nest < 0 || p->min_width < 1 ||
+        !(p->efficiency >= 0.0 && p->efficiency <= 1.0))
+        return fail(LBM_EINVAL,
+                    "lbm_regrid: need coarsen >= 1, buffer >= 0, nest >= 0, min_width >= 1 and "
+                    "efficiency in [0, 1]");
+    const void *field = field_dev;
+    int ftype = LBM_F64;
+    if (!field) {
+        if (!h->have_kfield || !h->kfield)
+            return fail(LBM_ESTATE,
+                        "no per-cell sensor recorded (lbm_set_sensor_field before stepping)");
+        field = h->kfield;
+        ftype = h->rtype();
+    }
+    lbm::rg::Params rp;
+    rp.coarsen = p->coarsen;
+    rp.threshold = p->threshold;
+    rp.buffer = p->buffer;
+    rp.nest = p->nest;
+    rp.efficiency = p->efficiency;
+    rp.min_width = p->min_width;
+    std::vector<int> out;
+    long long nt = 0;
+    int st = lbm::rg::regrid(field, ftype, h->nx, h->ny, h->nz, h->periodic, rp, p->allowed, &out,
+                             &nt, tags_out, h->stream);
+    if (st != LBM_OK) return st;
+    const int n = (int)(out.size() / 6);
+    *nboxes = n;
+    if (ntagged) *ntagged = nt;
+    if (n > max_boxes)
+        return fail(LBM_EINVAL, "lbm_regrid: %d boxes, more than max_boxes = %d", n, max_boxes);
+    for (int k = 0; k < n; ++k)
+        for (int a = 0; a < 3; ++a) {
+            boxes[k].lo[a] = out[6 * k + a];
+            boxes[k].hi[a] = out[6 * k + 3 + a];
+        }
+    return LBM_OK;
+}
+
 }  // extern "C"

@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "lbm_traits.cuh"
 
 namespace lbm {
@@ -71,6 +73,22 @@ int set_block(Mesh *m, int l, int b, const double *in, cudaStream_t s);
 int info(const Mesh *m, int l, int *n, double *tau, int *nslot, int *threads, int *cpt);
 long long cells_per_cycle(const Mesh *m);
 }  // namespace ml
+
+// Regridding of one level (lbm_regrid.cu).  field: nx * ny * nz values of field_type (LBM_F64:
+// double, LBM_F32: float) on the device; boxes_out receives 6 ints per box (lo x y z, hi x y z).
+namespace rg {
+struct Params {
+    int coarsen;
+    double threshold;
+    int buffer;
+    int nest;
+    double efficiency;
+    int min_width;
+};
+int regrid(const void *field, int field_type, int nx, int ny, int nz, int periodic,
+           const Params &p, const uint8_t *allowed_host, std::vector<int> *boxes_out,
+           long long *ntagged, uint8_t *tags_out, cudaStream_t s);
+}  // namespace rg
 
 // Error state shared by the C-ABI translation units (lbm_api.cu).
 int report_error(int code, const char *msg);

@@ -92,6 +92,7 @@ _SIGS = {
     "lbm_levels": (_i, [_h, _i, _d, _d, _i, _i, _i, _vp]),
     "lbm_levels_fit": (_i, [_h, _i, _i, _i, _i, _vp]),
     "lbm_step_noalloc": (_i, [_i, _i, _i, _i, _i, _d, _d, _d, _i, _vp, _vp, _i, _vp, _vp]),
+    "lbm_regrid": (_i, [_h, _vp, _vp, _vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_ll), _vp]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -318,6 +319,29 @@ def lbm_blocks_info(h, level: int):
     return n.value, tau.value, nb.value, th.value, cpt.value, cu.value
 
 
+class RegridParams(ctypes.Structure):
+    """struct lbm_regrid_params of include/lbm.h."""
+    _fields_ = [("coarsen", _i), ("threshold", _d), ("buffer", _i), ("allowed", ctypes.c_void_p),
+                ("nest", _i), ("efficiency", _d), ("min_width", _i)]
+
+
+class Box(ctypes.Structure):
+    """struct lbm_box of include/lbm.h."""
+    _fields_ = [("lo", _i * 3), ("hi", _i * 3)]
+
+
+def lbm_regrid(h, field_dev, params, boxes, max_boxes: int, tags_out=None):
+    """Returns (number of boxes, tagged tag cells).  `boxes` is a ctypes array of Box (or an
+    address), `field_dev` a device array of doubles or None for the handle's sensor field."""
+    nb = _i()
+    nt = ctypes.c_longlong()
+    bp = boxes if isinstance(boxes, ctypes.Array) else _ptr(boxes)
+    st = _lib.lbm_regrid(h, _ptr(field_dev), ctypes.byref(params), bp, int(max_boxes),
+                         ctypes.byref(nb), ctypes.byref(nt), _ptr(tags_out))
+    _ck(st, "lbm_regrid")
+    return nb.value, nt.value
+
+
 class BlockMesh:
     """Multi-level block mesh on a handle: leaf[nbz, nby, nbx] leaf levels, block edge `edge`."""
 
@@ -536,6 +560,26 @@ class Lattice:
         out = np.empty((self.nz, self.ny, self.nx))
         lbm_get_sensor_field(self.h, out)
         return out
+
+    def regrid(self, threshold, coarsen=1, buffer=1, efficiency=0.8, min_width=1, allowed=None,
+               nest=1, field=None, max_boxes=1 << 16):
+        """Boxes [n, 6] (lo x y z, hi x y z, lattice cells) and the tag grid [tz, ty, tx] of one
+        regrid of this lattice from its sensor field (``field``: a CUDA tensor of nz*ny*nx doubles
+        to use instead)."""
+        r = int(coarsen)
+        tz = -(-self.nz // r) if self.nz > 1 else 1
+        tshape = (tz, -(-self.ny // r), -(-self.nx // r))
+        mask = None
+        if allowed is not None:
+            mask = np.ascontiguousarray(allowed, dtype=np.uint8).reshape(tshape)
+        p = RegridParams(r, float(threshold), int(buffer), _ptr(mask), int(nest),
+                         float(efficiency), int(min_width))
+        tags = np.empty(tshape, dtype=np.uint8)
+        boxes = (Box * max(int(max_boxes), 1))()
+        n, _ = lbm_regrid(self.h, field, p, boxes, int(max_boxes), tags)
+        out = np.array([list(boxes[k].lo) + list(boxes[k].hi) for k in range(n)],
+                       dtype=np.int64).reshape(-1, 6)
+        return out, tags.astype(bool)
 
     def conservation(self):
         return lbm_conservation(self.h)

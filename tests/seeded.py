@@ -58,3 +58,26 @@ def block_maxima(seed: int, n: int, ties: int = 0, nans: int = 0, near=None) -> 
             if j % 3 == 0:
                 v[k] = base
     return v
+
+
+def rng_for(*key) -> np.random.Generator:
+    """Generator seeded by a tuple of names and integers (stable across runs and machines)."""
+    import zlib
+
+    return rng(zlib.crc32(repr(key).encode()))
+
+
+def blob_field(seed: int, shape, blobs: int = 6, background=(1e-5, 1e-3), peak=(1e-2, 1e-1)):
+    """A positive per-cell field [nz, ny, nx] shaped like a refinement sensor: log-uniform
+    background noise plus a few Gaussian bumps of log-uniform height and radius 1..shape/6."""
+    g = rng(seed)
+    nz, ny, nx = shape
+    f = np.exp(g.uniform(np.log(background[0]), np.log(background[1]), size=shape))
+    zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    for _ in range(blobs):
+        c = [g.uniform(0, n) for n in shape]
+        r = g.uniform(1.0, max(1.5, max(shape) / 6.0))
+        h = np.exp(g.uniform(np.log(peak[0]), np.log(peak[1])))
+        d2 = (zz - c[0]) ** 2 + (yy - c[1]) ** 2 + (xx - c[2]) ** 2
+        f += h * np.exp(-d2 / (2.0 * r * r))
+    return f
