@@ -403,6 +403,58 @@ LBM_API int lbm_regrid(lbm_t *h, const double *field_dev, const lbm_regrid_param
                        lbm_box *boxes, int max_boxes, int *nboxes, long long *ntagged,
                        uint8_t *tags_out);
 
+/*
+ * Learned predictor of the block sensor maxima (not in the paper; it serves the dynamic
+ * regridding of Sec. 5.2, which re-evaluates the sensor at every level-0 step, by estimating
+ * where the sensor will be large some steps ahead, so that a regrid can refine before the flow
+ * gets there; the exact sensor stays the fallback and the judge of the predicted flags).
+ *
+ * lbm_block_features writes, per block of edge `block` (along z too for D3Q19; partial blocks at
+ * the high ends), the mean over its cells of rho, u_x, u_y (and u_z for D3Q19) of the current
+ * populations: out_dev[c * nblocks + b] (FP32, device, caller-owned; blocks x fastest), queued on
+ * the handle's stream.
+ *
+ * The network: X -> normalise ((x - shift[c]) * scale[c] per input channel) -> 3x3 conv (cin ->
+ * hidden) + ReLU -> 3x3 conv (hidden -> hidden) + ReLU -> 3x3 conv (hidden -> 1), zero padding,
+ * inputs X[batch][cin][h][w] and outputs Y[batch][1][h][w] in FP32 on the device.  Parameters
+ * are one flat FP32 vector: W1[hidden][cin][3][3], b1[hidden], W2[hidden][hidden][3][3],
+ * b2[hidden], W3[1][hidden][3][3], b3[1] (lbm_net_param_count values); weights and activations
+ * are used in BF16 with FP32 accumulation; the master parameters, gradients and Adam moments are
+ * FP32.  Training minimises the mean over all outputs of (Y - T)^2 with Adam (Kingma and Ba 2015:
+ * m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2, theta -= lr (m / (1 - b1^t)) /
+ * (sqrt(v / (1 - b2^t)) + eps)).  cin is 3 or 4 and hidden 8 or 16 (LBM_EINVAL otherwise).
+ *
+ * lbm_net_backward runs the forward pass and writes the gradients of the loss (lbm_net_get_grads);
+ * lbm_net_adam applies one Adam step with the current gradients (lbm_net_set_grads replaces them,
+ * e.g. with gradients averaged over several processes); lbm_net_train_step is backward + Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8).  A non-NULL loss_host receives the loss and synchronises;
+ * otherwise the calls queue their kernels on the network's stream (lbm_net_set_stream) and return.
+ * lbm_net_set_params sets the parameters and clears the Adam state.  Targets and predictions are
+ * in log10 units: lbm_net_log_targets writes t = log10(max(K, floor_k)) - offset for n block
+ * maxima (NaN for a NaN maximum), lbm_net_to_maxima K = 10^(y + offset); the latter feeds lbm_flags_from_maxima.
+ */
+typedef struct lbm_net_s lbm_net;
+LBM_API int lbm_block_features(lbm_t *h, int block, float *out_dev);
+LBM_API lbm_net *lbm_net_create(int cin, int hidden);
+LBM_API void lbm_net_destroy(lbm_net *n);
+LBM_API int lbm_net_set_stream(lbm_net *n, void *stream);
+LBM_API int lbm_net_param_count(lbm_net *n);
+LBM_API int lbm_net_set_normalisation(lbm_net *n, const float *shift, const float *scale);
+LBM_API int lbm_net_set_params(lbm_net *n, const float *host);
+LBM_API int lbm_net_get_params(lbm_net *n, float *host);
+LBM_API int lbm_net_get_grads(lbm_net *n, float *host);
+LBM_API int lbm_net_set_grads(lbm_net *n, const float *host);
+LBM_API int lbm_net_forward(lbm_net *n, const float *x_dev, int batch, int h, int w, float *y_dev);
+LBM_API int lbm_net_backward(lbm_net *n, const float *x_dev, const float *target_dev, int batch,
+                             int h, int w, double *loss_host);
+LBM_API int lbm_net_adam(lbm_net *n, float lr, float beta1, float beta2, float eps);
+LBM_API int lbm_net_train_step(lbm_net *n, const float *x_dev, const float *target_dev, int batch,
+                               int h, int w, float lr, double *loss_host);
+LBM_API int lbm_net_log_targets(const double *kmax_dev, long long n, float offset, float floor_k,
+                                float *t_dev, void *stream);
+LBM_API int lbm_net_to_maxima(const float *y_dev, long long n, float offset, double *kmax_dev,
+                              void *stream);
+
 #ifdef __cplusplus
 }
 #endif

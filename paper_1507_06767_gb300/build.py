@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbm.so")
 
 SOURCES = ["lbm_api.cu", "lbm_aux.cu", "lbm_step_d2q9.cu", "lbm_step_d3q19.cu", "lbm_noalloc.cu",
-           "lbm_multilevel.cu", "lbm_regrid.cu"]
+           "lbm_multilevel.cu", "lbm_regrid.cu", "lbm_net.cu"]
 HEADERS = ["lbm_traits.cuh", "lbm_step.cuh", "lbm_step_pair.cuh", "lbm_step_tma.cuh",
            "lbm_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -1001,6 +1001,17 @@ LBM_API int lbm_blocks_info(lbm_t *h, int level, int *n, double *tau, int *nbloc
     return lbm::ml::info(h->mesh, level, n, tau, nblocks, threads, cells_per_thread);
 }
 
+LBM_API int lbm_block_features(lbm_t *h, int block, float *out_dev) {
+    CHECK_H(h);
+    if (block < 1 || !out_dev) return fail(LBM_EINVAL, "lbm_block_features: block >= 1, out_dev");
+    int st = ensure_buffers(h);
+    if (st != LBM_OK) return st;
+    CK(lbm::block_features(h->q, h->dtype, h->buf[h->cur], h->nx, h->ny, h->nz, block, out_dev,
+                           h->stream),
+       "block features");
+    return LBM_OK;
+}
+
 LBM_API int lbm_regrid(lbm_t *h, const double *field_dev, const lbm_regrid_params *p,
                        lbm_box *boxes, int max_boxes, int *nboxes, long long *ntagged,
                        uint8_t *tags_out) {

@@ -104,6 +104,54 @@ __global__ void k_moments(const typename Storage<DT>::T *f, size_t N, size_t c0,
     }
 }
 
+// Block means of the cell moments: one CTA per block of edge b (partial blocks at the high ends),
+// out[c][block] for c = rho, u_x, u_y (, u_z) with blocks in x-fastest order.  Sums in double.
+constexpr int FEAT_THREADS = 256;
+
+template <class L, int DT>
+__global__ void __launch_bounds__(FEAT_THREADS)
+    k_block_features(const typename Storage<DT>::T *f, int nx, int ny, int nz, int b, int bz,
+                     int nbx, int nby, int nblocks, float *out) {
+    const int blk = blockIdx.x;
+    const int bx = blk % nbx, by = (blk / nbx) % nby, bzi = blk / (nbx * nby);
+    const int x0 = bx * b, y0 = by * b, z0 = bzi * bz;
+    const int ex = min(b, nx - x0), ey = min(b, ny - y0), ez = min(bz, nz - z0);
+    const int ncell = ex * ey * ez;
+    const size_t N = (size_t)nx * ny * nz;
+    double acc[4] = {0, 0, 0, 0};
+    for (int k = threadIdx.x; k < ncell; k += blockDim.x) {
+        const int x = x0 + k % ex, y = y0 + (k / ex) % ey, z = z0 + k / (ex * ey);
+        const size_t c = ((size_t)z * ny + y) * nx + x;
+        double r = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            const double v = stored_to_f64<L, DT>(f[(size_t)i * N + c], i);
+            r += v;
+            jx += L::cx(i) * v;
+            jy += L::cy(i) * v;
+            jz += L::cz(i) * v;
+        }
+        acc[0] += r;
+        acc[1] += jx / r;
+        acc[2] += jy / r;
+        acc[3] += jz / r;
+    }
+    __shared__ double sh[4][FEAT_THREADS];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int st = FEAT_THREADS / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const int nch = L::D == 3 ? 4 : 3;
+        for (int k = 0; k < nch; ++k) out[(size_t)k * nblocks + blk] = (float)(sh[k][0] / ncell);
+    }
+}
+
 constexpr int CONS_THREADS = 256;
 
 template <class L, int DT>
@@ -405,6 +453,17 @@ cudaError_t moments_f64(int q, int dtype, const void *f, size_t N, size_t c0, si
                         double *rho, double *u, cudaStream_t s) {
     LBM_DISPATCH(q, dtype, (k_moments<L, DT><<<ew_grid(nc, 1), EW_THREADS, 0, s>>>(
                                static_cast<const typename Storage<DT>::T *>(f), N, c0, nc, rho, u)));
+    return cudaGetLastError();
+}
+
+cudaError_t block_features(int q, int dtype, const void *f, int nx, int ny, int nz, int b,
+                          float *out, cudaStream_t s) {
+    const int bz = nz > 1 ? b : 1;
+    const int nbx = (nx + b - 1) / b, nby = (ny + b - 1) / b, nbz = (nz + bz - 1) / bz;
+    const int nblocks = nbx * nby * nbz;
+    LBM_DISPATCH(q, dtype, (k_block_features<L, DT><<<nblocks, FEAT_THREADS, 0, s>>>(
+                               static_cast<const typename Storage<DT>::T *>(f), nx, ny, nz, b, bz,
+                               nbx, nby, nblocks, out)));
     return cudaGetLastError();
 }
 

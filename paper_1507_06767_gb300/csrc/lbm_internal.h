@@ -36,6 +36,10 @@ cudaError_t storage_to_f64(int q, int dtype, int i0, int nq, const void *in, dou
 // rho[nc] and u[3][nc] of cells [c0, c0 + nc).
 cudaError_t moments_f64(int q, int dtype, const void *f, size_t N, size_t c0, size_t nc,
                         double *rho, double *u, cudaStream_t s);
+// Block means of rho, u_x, u_y (, u_z for D3Q19) over blocks of edge b (b along z only for 3-D
+// lattices): out[c * nblocks + block], blocks x fastest.
+cudaError_t block_features(int q, int dtype, const void *f, int nx, int ny, int nz, int b,
+                           float *out, cudaStream_t s);
 // Deterministic FP64 sums: result[0] = mass, [1..3] = momentum, [4] = number of non-finite
 // populations.  partial must hold CONS_PARTS * 5 doubles.
 constexpr int CONS_PARTS = 608;

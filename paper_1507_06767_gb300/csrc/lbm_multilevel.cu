@@ -13,17 +13,18 @@
 //   * a level step is the fused pull step of every block of the level (moving-wall bounce-back at
 //     the domain walls, moments, equilibrium, Knudsen sensor, BGK collision) reading a one-cell
 //     ghost layer;
-//   * ghost cells inside another block of the same level are copies; the others are trilinear
-//     (3/4, 1/4 per axis; 5/4, -1/4 extrapolation at a wall) interpolations of the coarser level,
-//     linear in time between its states before and after its step, with f^neq rescaled by
-//     (tau_f - 1) / (2 (tau_c - 1));
+//   * a population pulled from another block of the same level is read from that block directly
+//     (a 27-entry neighbour table per block); one pulled from where the level does not exist is
+//     read from the block's own ghost layer, filled by trilinear (3/4, 1/4 per axis; 5/4, -1/4
+//     extrapolation at a wall) interpolation of the coarser level, linear in time between its
+//     states before and after its step, with f^neq rescaled by (tau_f - 1) / (2 (tau_c - 1));
 //   * after the two sub-steps of level l + 1, the level-l cells under it become the average of
 //     their 8 fine cells with f^neq rescaled by 2 (tau_c - 1) / (tau_f - 1).
 //
 // Device layout of a level: one buffer of nslot blocks x 19 populations x (n + 2)^3 ghosted cells
-// (block-major, then population, then z, y, x), two buffers (ping-pong).  The ghost and
-// restriction work is precomputed on the host as task lists (flat element offsets and weights), so
-// the kernels are plain gathers.  A cycle is captured once per level-0 buffer parity as a CUDA graph
+// (block-major, then population, then z, y, x), two buffers (ping-pong); only the ghost cells that
+// face a coarser neighbour are used.  The interpolation and restriction work is precomputed on the
+// host as task lists (flat element offsets and weights), so those kernels are plain gathers.  A cycle is captured once per level-0 buffer parity as a CUDA graph
 // and replayed.  The launch shape of each level's step kernel (threads per CTA and cells per
 // thread) is chosen by timing the candidates once when the mesh is built.
 #include <cuda_runtime.h>
@@ -44,9 +45,14 @@ namespace ml {
 constexpr int Q = 19;
 constexpr int MAXL = 3;
 
-struct CopyTask {
-    int dst, src;  // flat offsets of population 0 (population i adds i * G)
-};
+// neighbour table entries besides a slot number
+constexpr int NB_GHOST = -1;  // the neighbouring block exists only on a coarser level
+constexpr int NB_WALL = -2;   // the neighbouring block lies outside the (non-periodic) domain
+constexpr int NB_TOP = 16;    // index of the (0, +1, 0) neighbour: (dx+1) + 3 (dy+1) + 9 (dz+1)
+// interior x = 0 sits XOFF floats into its row (one 32-byte sector, so whole interior rows start
+// on a sector boundary); rows are padded to a multiple of 8 floats
+constexpr int XOFF = 8;
+
 struct InterpTask {
     int dst;
     int src[8];
@@ -58,22 +64,24 @@ struct RestrictTask {
 };
 
 struct Level {
-    int n = 0, G = 0;      // cells per block edge, ghosted cells per block
+    int n = 0, G = 0;      // cells per block edge, values per population per block (ghosted)
+    int P = 0, plane = 0;  // row pitch (XOFF + n + 1 rounded up to 8) and plane size P (n + 2)
     double tau = 1.0;
     int nslot = 0;
     std::vector<int> slot;  // physical block -> slot or -1
     int cells[3] = {0, 0, 0};
     float *buf[2] = {nullptr, nullptr};
     int cur = 0;
-    int *origin = nullptr;  // device: 3 ints per slot (level-cell origin of the block)
-    CopyTask *copies = nullptr;
-    int ncopy = 0;
+    int *nbr = nullptr;  // device: 27 entries per slot (slot, NB_GHOST or NB_WALL)
     InterpTask *interps = nullptr;  // from level - 1
     int ninterp = 0;
     RestrictTask *restricts = nullptr;  // level cells under level + 1
     int nrestrict = 0;
     float *kmax = nullptr;  // device: per-slot sensor max of the level's last step (int bits)
-    int threads = 256, cpt = 1;  // step launch shape (autotuned)
+    // step launch shape (autotuned): flat kernel with `threads` per CTA and `cpt` cells per
+    // thread, or (tiled) the brick kernel walking `zc` planes
+    bool tiled = false;
+    int threads = 256, cpt = 1, zc = 1;
 };
 
 struct Mesh {
@@ -87,14 +95,6 @@ struct Mesh {
 };
 
 // ---------------------------------------------------------------------------------- kernels
-__global__ void k_copy(const CopyTask *t, int n, float *buf, int G) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const CopyTask c = t[k];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) buf[c.dst + i * G] = buf[c.src + i * G];
-}
-
 __device__ __forceinline__ void moments19(const float *f, float &rho, float &ux, float &uy,
                                           float &uz) {
     float r = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
@@ -118,7 +118,10 @@ __device__ __forceinline__ float feq19(int i, float rho, float ux, float uy, flo
     return weight<D3Q19, float>(i) * rho * (1.f + 3.f * cu + 4.5f * cu * cu - 1.5f * uu);
 }
 
-// coarse -> fine ghost: interpolate in space and time, rescale the non-equilibrium part
+// coarse -> fine ghost: interpolate in space and time, rescale the non-equilibrium part.  BLEND:
+// theta > 0 (the coarse states before and after its step are mixed); without it only the state
+// before the coarse step is read.
+template <bool BLEND>
 __global__ void k_interp(const InterpTask *t, int n, float *fine, int Gf, const float *cprev,
                          const float *ccur, int Gc, float theta, float scale) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -131,7 +134,10 @@ __global__ void k_interp(const InterpTask *t, int n, float *fine, int Gf, const 
 #pragma unroll
         for (int s = 0; s < 8; ++s) {
             const int o = it.src[s] + i * Gc;
-            a += it.w[s] * ((1.f - theta) * cprev[o] + theta * ccur[o]);
+            if (BLEND)
+                a += it.w[s] * ((1.f - theta) * cprev[o] + theta * ccur[o]);
+            else
+                a += it.w[s] * cprev[o];
         }
         acc[i] = a;
     }
@@ -146,11 +152,11 @@ __global__ void k_interp(const InterpTask *t, int n, float *fine, int Gf, const 
 
 // level cells under the finer level: average of 8 fine cells, non-equilibrium part rescaled
 __global__ void k_restrict(const RestrictTask *t, int n, float *coarse, int Gc, const float *fine,
-                           int nf, int Gf, float scale) {
+                           int pf, int planef, int Gf, float scale) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const RestrictTask r = t[k];
-    const int row = nf + 2, plane = (nf + 2) * (nf + 2);
+    const int row = pf, plane = planef;
     float avg[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -168,53 +174,117 @@ __global__ void k_restrict(const RestrictTask *t, int n, float *coarse, int Gc, 
 }
 
 struct StepArgs {
-    int n, G;
-    int cells[3];
-    int periodic;
+    int n, G, P, plane;  // cells per edge, values per population, row pitch, plane size
     float omega;
     float lid_x, lid_z;
 };
 
-// one pull step of every block of a level; grid (slot, chunk), each thread `cpt` cells
-__global__ void k_step(const float *__restrict__ in, float *__restrict__ out, const int *origin,
-                       const StepArgs a, int cpt, float *kmax) {
+// One cell of a level step (pull, bounce-back at walls, moments, equilibrium, sensor, collision);
+// returns its sensor value.  src / dst: the block's slot in the two buffers.
+template <int NT>
+__device__ __forceinline__ float step_cell(const float *__restrict__ in, const float *src,
+                                           float *dst, const int *snb, bool top,
+                                           const StepArgs &a, int x, int y, int z) {
     using L = D3Q19;
+    const int n = NT ? NT : a.n;
+    const int G = a.G, row = a.P, plane = a.plane;
+    const int g = (z + 1) * plane + (y + 1) * row + XOFF + x;
+    // a pull along +c leaves the block at the low face, along -c at the high face
+    const bool xl = x == 0, xh = x == n - 1, yl = y == 0, yh = y == n - 1;
+    const bool zl = z == 0, zh = z == n - 1;
+    float df[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+        const int dx = (cx == 1 && xl) ? -1 : ((cx == -1 && xh) ? 1 : 0);
+        const int dy = (cy == 1 && yl) ? -1 : ((cy == -1 && yh) ? 1 : 0);
+        const int dz = (cz == 1 && zl) ? -1 : ((cz == -1 && zh) ? 1 : 0);
+        float v;
+        if ((dx | dy | dz) == 0) {
+            v = src[i * G + g - (cz * plane + cy * row + cx)];
+        } else {
+            const int nb = snb[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)];
+            if (nb >= 0) {
+                v = in[(size_t)nb * Q * G + i * G + (z - cz - dz * n + 1) * plane +
+                       (y - cy - dy * n + 1) * row + XOFF + (x - cx - dx * n)];
+            } else if (nb == NB_GHOST) {
+                v = src[i * G + g - (cz * plane + cy * row + cx)];
+            } else {
+                v = src[L::opp(i) * G + g];
+                if (dy == 1 && top)
+                    v += 6.f * weight<L, float>(i) * ((float)cx * a.lid_x + (float)cz * a.lid_z);
+            }
+        }
+        df[i] = v - weight<L, float>(i);
+    }
+    return relax_store_cell<L, 1, 1>(df, a.omega, dst, (size_t)G, g);
+}
+
+// warp max of the sensor bits, one atomic per warp (every lane of the warp must call this)
+__device__ __forceinline__ void block_max_flush(int km, float *kmax, int slot, int lane) {
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) km = max(km, __shfl_xor_sync(~0u, km, off));
+    if (lane == 0) atomicMax(reinterpret_cast<int *>(kmax) + slot, km);
+}
+
+// Flat mapping: grid (slot, chunk), cells of a block in x-fastest order, each thread `cpt` cells.
+// NT is the block edge when it is one of the compiled sizes (shifts instead of divisions), 0
+// otherwise.
+template <int NT>
+__global__ void k_step(const float *__restrict__ in, float *__restrict__ out,
+                       const int *__restrict__ nbr, const StepArgs a, int cpt, float *kmax) {
+    __shared__ int snb[27];
     const int slot = blockIdx.x;
-    const int n = a.n, G = a.G, row = n + 2, plane = (n + 2) * (n + 2);
+    if (threadIdx.x < 27) snb[threadIdx.x] = nbr[27 * slot + threadIdx.x];
+    __syncthreads();
+    const int n = NT ? NT : a.n;
     const int ncell = n * n * n;
-    const float *src = in + (size_t)slot * Q * G;
-    float *dst = out + (size_t)slot * Q * G;
-    const int ox = origin[3 * slot], oy = origin[3 * slot + 1], oz = origin[3 * slot + 2];
+    const bool top = snb[NB_TOP] == NB_WALL;  // the block touches the lid wall
+    const float *src = in + (size_t)slot * Q * a.G;
+    float *dst = out + (size_t)slot * Q * a.G;
     int km = 0;
     for (int r = 0; r < cpt; ++r) {
         const int c = (blockIdx.y * cpt + r) * blockDim.x + threadIdx.x;
         if (c >= ncell) break;
-        const int x = c % n, y = (c / n) % n, z = c / (n * n);
-        const int g = (z + 1) * plane + (y + 1) * row + (x + 1);
-        float df[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-            const int gx = ox + x - cx, gy = oy + y - cy, gz = oz + z - cz;
-            const bool wx = (gx < 0 || gx >= a.cells[0]) && !(a.periodic & 1);
-            const bool wy = (gy < 0 || gy >= a.cells[1]) && !(a.periodic & 2);
-            const bool wz = (gz < 0 || gz >= a.cells[2]) && !(a.periodic & 4);
-            float v;
-            if (wx || wy || wz) {
-                v = src[L::opp(i) * G + g];
-                if (gy == a.cells[1] && !(a.periodic & 2))
-                    v += 6.f * weight<L, float>(i) * ((float)cx * a.lid_x + (float)cz * a.lid_z);
-            } else {
-                v = src[i * G + g - (cz * plane + cy * row + cx)];
-            }
-            df[i] = v - weight<L, float>(i);
-        }
-        const float K = relax_store_cell<L, 1, 1>(df, a.omega, dst, (size_t)G, g);
+        const float K = step_cell<NT>(in, src, dst, snb, top, a, c % n, (c / n) % n, c / (n * n));
         km = max(km, __float_as_int(K));
     }
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) km = max(km, __shfl_xor_sync(~0u, km, off));
-    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int *>(kmax) + slot, km);
+    block_max_flush(km, kmax, slot, threadIdx.x & 31);
+}
+
+// Tiled mapping for NT = 8, 16, 32, 64: a CTA of 256 threads is a TX x TY x TZ brick of cells
+// (whole rows in x) that walks through `zc` planes of the block, so the planes pulled from along z
+// were read by the same CTA just before (L1 reuse, as in the uniform step).
+template <int NT>
+struct Tile {
+    static constexpr int TX = NT;
+    static constexpr int TY = NT >= 16 ? 256 / NT : NT;
+    static constexpr int TZ = 256 / (TX * TY);
+};
+
+template <int NT>
+__global__ void __launch_bounds__(256, 4) k_step_tiled(const float *__restrict__ in,
+                                                    float *__restrict__ out,
+                                                    const int *__restrict__ nbr, const StepArgs a,
+                                                    int zc, float *kmax) {
+    using T = Tile<NT>;
+    __shared__ int snb[27];
+    const int slot = blockIdx.x;
+    const int tid = (threadIdx.z * T::TY + threadIdx.y) * T::TX + threadIdx.x;
+    if (tid < 27) snb[tid] = nbr[27 * slot + tid];
+    __syncthreads();
+    const bool top = snb[NB_TOP] == NB_WALL;
+    const float *src = in + (size_t)slot * Q * a.G;
+    float *dst = out + (size_t)slot * Q * a.G;
+    constexpr int ytiles = NT / T::TY;
+    const int y = (blockIdx.y % ytiles) * T::TY + threadIdx.y;
+    const int z0 = (blockIdx.y / ytiles) * zc;
+    int km = 0;
+    for (int zz = threadIdx.z; zz < zc; zz += T::TZ) {
+        const float K = step_cell<NT>(in, src, dst, snb, top, a, threadIdx.x, y, z0 + zz);
+        km = max(km, __float_as_int(K));
+    }
+    block_max_flush(km, kmax, slot, tid & 31);
 }
 
 __global__ void k_fill_rest(float *buf, int nslot, int G) {
@@ -256,7 +326,9 @@ namespace {
         if (e_ != cudaSuccess) return report_cuda_error(e_, what); \
     } while (0)
 
-int gidx(int n, int x, int y, int z) { return ((z + 1) * (n + 2) + (y + 1)) * (n + 2) + (x + 1); }
+int gidx(const Level &L, int x, int y, int z) {
+    return (z + 1) * L.plane + (y + 1) * L.P + XOFF + x;
+}
 
 bool balanced(const Mesh &m) {
     for (int z = 0; z < m.nb[2]; ++z)
@@ -302,12 +374,12 @@ int cell_offset(const Mesh &m, int l, const int g[3], int *slot_out) {
     const int s = L.slot[blk];
     *slot_out = s;
     if (s < 0) return -1;
-    return s * Q * L.G + gidx(L.n, loc[0], loc[1], loc[2]);
+    return s * Q * L.G + gidx(L, loc[0], loc[1], loc[2]);
 }
 
 int build_tasks(Mesh &m, int l) {
     Level &L = m.lv[l];
-    std::vector<CopyTask> copies;
+    std::vector<int> nbr;
     std::vector<InterpTask> interps;
     const int n = L.n;
     for (int b = 0; b < m.nblk; ++b) {
@@ -327,13 +399,10 @@ int build_tasks(Mesh &m, int l) {
                         g[a] = w;
                     }
                     if (!inside) continue;  // a wall: the step bounces back
-                    const int dst = s * Q * L.G + gidx(n, x, y, z);
+                    const int dst = s * Q * L.G + gidx(L, x, y, z);
                     int ns;
-                    const int src = cell_offset(m, l, g, &ns);
-                    if (ns >= 0) {
-                        copies.push_back({dst, src});
-                        continue;
-                    }
+                    cell_offset(m, l, g, &ns);
+                    if (ns >= 0) continue;  // the step reads the neighbouring block directly
                     if (l == 0) return report_error(LBM_EINVAL, "level-0 ghost without a source");
                     // ghost centre (g + 1/2) h_l lies at g/2 + 1/4 coarse cells: coarse cell
                     // g >> 1, offset -1/4 (g even) or +1/4 (g odd)
@@ -377,9 +446,28 @@ int build_tasks(Mesh &m, int l) {
                     interps.push_back(it);
                 }
     }
-    int st = upload(&L.copies, copies);
+    // neighbour table: for each slot and each of the 27 offsets, the slot of the neighbouring
+    // block at this level, NB_GHOST if that block exists only coarser, NB_WALL outside the domain
+    nbr.assign((size_t)27 * std::max(L.nslot, 1), NB_WALL);
+    for (int b = 0; b < m.nblk; ++b) {
+        const int s = L.slot[b];
+        if (s < 0) continue;
+        const int bc[3] = {b % m.nb[0], (b / m.nb[0]) % m.nb[1], b / (m.nb[0] * m.nb[1])};
+        for (int k = 0; k < 27; ++k) {
+            const int d[3] = {k % 3 - 1, (k / 3) % 3 - 1, k / 9 - 1};
+            int c[3];
+            bool inside = true;
+            for (int a = 0; a < 3; ++a) {
+                c[a] = wrap(bc[a] + d[a], m.nb[a], m.periodic & (1 << a));
+                if (c[a] < 0) inside = false;
+            }
+            if (!inside) continue;
+            const int o = L.slot[(c[2] * m.nb[1] + c[1]) * m.nb[0] + c[0]];
+            nbr[(size_t)27 * s + k] = o >= 0 ? o : NB_GHOST;
+        }
+    }
+    int st = upload(&L.nbr, nbr);
     if (st != LBM_OK) return st;
-    L.ncopy = (int)copies.size();
     st = upload(&L.interps, interps);
     if (st != LBM_OK) return st;
     L.ninterp = (int)interps.size();
@@ -393,8 +481,8 @@ int build_tasks(Mesh &m, int l) {
             for (int z = 0; z < n; ++z)
                 for (int y = 0; y < n; ++y)
                     for (int x = 0; x < n; ++x)
-                        rs.push_back({sc * Q * L.G + gidx(n, x, y, z),
-                                      sf * Q * F.G + gidx(F.n, 2 * x, 2 * y, 2 * z)});
+                        rs.push_back({sc * Q * L.G + gidx(L, x, y, z),
+                                      sf * Q * F.G + gidx(F, 2 * x, 2 * y, 2 * z)});
         }
         st = upload(&L.restricts, rs);
         if (st != LBM_OK) return st;
@@ -408,22 +496,64 @@ StepArgs step_args(const Mesh &m, int l) {
     StepArgs a;
     a.n = L.n;
     a.G = L.G;
-    for (int k = 0; k < 3; ++k) a.cells[k] = L.cells[k];
-    a.periodic = m.periodic;
+    a.P = L.P;
+    a.plane = L.plane;
     a.omega = (float)(1.0 / L.tau);
     a.lid_x = (float)m.lid[0];
     a.lid_z = (float)m.lid[2];
     return a;
 }
 
-cudaError_t launch_step(const Mesh &m, int l, int threads, int cpt, cudaStream_t s, int src) {
+bool has_tiled(int n) { return n == 8 || n == 16 || n == 32 || n == 64; }
+
+template <int NT>
+cudaError_t launch_tiled(const Level &L, const StepArgs &a, int zc, cudaStream_t s, int src) {
+    using T = Tile<NT>;
+    const dim3 block(T::TX, T::TY, T::TZ);
+    const dim3 grid(L.nslot, (NT / T::TY) * (NT / zc));
+    k_step_tiled<NT><<<grid, block, 0, s>>>(L.buf[src], L.buf[src ^ 1], L.nbr, a, zc, L.kmax);
+    return cudaGetLastError();
+}
+
+// tiled: zc planes per CTA (a multiple of the brick depth dividing n); else flat with
+// threads x cpt cells per CTA
+cudaError_t launch_step(const Mesh &m, int l, bool tiled, int threads, int cpt, int zc,
+                        cudaStream_t s, int src) {
     const Level &L = m.lv[l];
+    const StepArgs a = step_args(m, l);
+    if (tiled) {
+        switch (L.n) {
+            case 8: return launch_tiled<8>(L, a, zc, s, src);
+            case 16: return launch_tiled<16>(L, a, zc, s, src);
+            case 32: return launch_tiled<32>(L, a, zc, s, src);
+            case 64: return launch_tiled<64>(L, a, zc, s, src);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     const int ncell = L.n * L.n * L.n;
     const int chunks = (ncell + threads * cpt - 1) / (threads * cpt);
     dim3 grid(L.nslot, chunks);
-    k_step<<<grid, threads, 0, s>>>(L.buf[src], L.buf[src ^ 1], L.origin, step_args(m, l), cpt,
-                                    L.kmax);
+    const float *fin = L.buf[src];
+    float *fout = L.buf[src ^ 1];
+    switch (L.n) {
+        case 4: k_step<4><<<grid, threads, 0, s>>>(fin, fout, L.nbr, a, cpt, L.kmax); break;
+        case 8: k_step<8><<<grid, threads, 0, s>>>(fin, fout, L.nbr, a, cpt, L.kmax); break;
+        case 16: k_step<16><<<grid, threads, 0, s>>>(fin, fout, L.nbr, a, cpt, L.kmax); break;
+        case 32: k_step<32><<<grid, threads, 0, s>>>(fin, fout, L.nbr, a, cpt, L.kmax); break;
+        case 64: k_step<64><<<grid, threads, 0, s>>>(fin, fout, L.nbr, a, cpt, L.kmax); break;
+        default: k_step<0><<<grid, threads, 0, s>>>(fin, fout, L.nbr, a, cpt, L.kmax); break;
+    }
     return cudaGetLastError();
+}
+
+int brick_depth(int n) {
+    switch (n) {
+        case 8: return Tile<8>::TZ;
+        case 16: return Tile<16>::TZ;
+        case 32: return Tile<32>::TZ;
+        case 64: return Tile<64>::TZ;
+        default: return 0;
+    }
 }
 
 inline unsigned blocks_for(int n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -433,18 +563,21 @@ inline unsigned blocks_for(int n, int t) { return (unsigned)((n + t - 1) / t); }
 int advance(Mesh &m, int l, float theta, cudaStream_t s) {
     Level &L = m.lv[l];
     if (L.nslot == 0) return LBM_OK;  // no block reaches this level (nor a finer one)
-    if (L.ncopy)
-        k_copy<<<blocks_for(L.ncopy, 256), 256, 0, s>>>(L.copies, L.ncopy, L.buf[L.cur], L.G);
     if (l > 0 && L.ninterp) {
         const Level &C = m.lv[l - 1];
         const float scale = (float)((L.tau - 1.0) / (2.0 * (C.tau - 1.0)));
-        k_interp<<<blocks_for(L.ninterp, 128), 128, 0, s>>>(L.interps, L.ninterp, L.buf[L.cur],
-                                                              L.G, C.buf[C.cur ^ 1], C.buf[C.cur],
-                                                              C.G, theta, scale);
+        if (theta > 0.f)
+            k_interp<true><<<blocks_for(L.ninterp, 128), 128, 0, s>>>(
+                L.interps, L.ninterp, L.buf[L.cur], L.G, C.buf[C.cur ^ 1], C.buf[C.cur], C.G,
+                theta, scale);
+        else
+            k_interp<false><<<blocks_for(L.ninterp, 128), 128, 0, s>>>(
+                L.interps, L.ninterp, L.buf[L.cur], L.G, C.buf[C.cur ^ 1], C.buf[C.cur], C.G,
+                theta, scale);
     }
     MLCK(cudaGetLastError(), "ghost fill");
     MLCK(cudaMemsetAsync(L.kmax, 0, sizeof(float) * L.nslot, s), "memset(kmax)");
-    MLCK(launch_step(m, l, L.threads, L.cpt, s, L.cur), "level step");
+    MLCK(launch_step(m, l, L.tiled, L.threads, L.cpt, L.zc, s, L.cur), "level step");
     L.cur ^= 1;
     if (l < m.lmax) {
         int st = advance(m, l + 1, 0.f, s);
@@ -454,37 +587,54 @@ int advance(Mesh &m, int l, float theta, cudaStream_t s) {
         if (L.nrestrict) {
             const float scale = (float)(2.0 * (L.tau - 1.0) / (F.tau - 1.0));
             k_restrict<<<blocks_for(L.nrestrict, 128), 128, 0, s>>>(
-                L.restricts, L.nrestrict, L.buf[L.cur], L.G, F.buf[F.cur], F.n, F.G, scale);
+                L.restricts, L.nrestrict, L.buf[L.cur], L.G, F.buf[F.cur], F.P, F.plane, F.G,
+                scale);
             MLCK(cudaGetLastError(), "restriction");
         }
     }
     return LBM_OK;
 }
 
-// Time each launch shape of the level step once and keep the fastest.  The trial steps write the
-// level's other buffer; the caller re-fills both buffers afterwards.
+// Time each launch shape of the level step once and keep the fastest: the flat kernel with
+// (threads, cells per thread) in {128, 256, 512} x {1, 2, 4}, and the tiled kernel with every depth
+// of planes it can walk.  The trial steps write the level's other buffer; the caller re-fills both
+// buffers afterwards.
 int autotune(Mesh &m, int l, cudaStream_t s) {
     Level &L = m.lv[l];
     if (L.nslot == 0) return LBM_OK;
     const int ncell = L.n * L.n * L.n;
-    const int cand[][2] = {{128, 1}, {128, 2}, {256, 1}, {256, 2}, {256, 4}, {512, 1}, {512, 2}};
+    struct Cand {
+        bool tiled;
+        int threads, cpt, zc;
+    };
+    std::vector<Cand> cand;
+    const int flat[][2] = {{128, 1}, {128, 2}, {256, 1}, {256, 2}, {256, 4}, {512, 1}, {512, 2}};
+    for (const auto &c : flat)
+        if (c[0] * c[1] <= 2 * ncell || (c[0] == 128 && c[1] == 1))
+            cand.push_back({false, c[0], c[1], 1});
+    if (has_tiled(L.n))
+        for (int zc = brick_depth(L.n); zc <= L.n; zc *= 2)
+            cand.push_back({true, 256, zc / brick_depth(L.n), zc});
     cudaEvent_t e0, e1;
     MLCK(cudaEventCreate(&e0), "cudaEventCreate");
     MLCK(cudaEventCreate(&e1), "cudaEventCreate");
     float best = 1e30f;
-    for (const auto &c : cand) {
-        if (c[0] * c[1] > 2 * ncell && !(c[0] == 128 && c[1] == 1)) continue;
-        for (int k = 0; k < 2; ++k) MLCK(launch_step(m, l, c[0], c[1], s, L.cur), "autotune");
+    for (const Cand &c : cand) {
+        for (int k = 0; k < 2; ++k)
+            MLCK(launch_step(m, l, c.tiled, c.threads, c.cpt, c.zc, s, L.cur), "autotune");
         MLCK(cudaEventRecord(e0, s), "cudaEventRecord");
-        for (int k = 0; k < 3; ++k) MLCK(launch_step(m, l, c[0], c[1], s, L.cur), "autotune");
+        for (int k = 0; k < 3; ++k)
+            MLCK(launch_step(m, l, c.tiled, c.threads, c.cpt, c.zc, s, L.cur), "autotune");
         MLCK(cudaEventRecord(e1, s), "cudaEventRecord");
         MLCK(cudaEventSynchronize(e1), "cudaEventSynchronize");
         float ms = 0.f;
         MLCK(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
         if (ms < best) {
             best = ms;
-            L.threads = c[0];
-            L.cpt = c[1];
+            L.tiled = c.tiled;
+            L.threads = c.threads;
+            L.cpt = c.cpt;
+            L.zc = c.zc;
         }
     }
     cudaEventDestroy(e0);
@@ -524,8 +674,7 @@ void destroy(Mesh *m) {
         Level &L = m->lv[l];
         cudaFree(L.buf[0]);
         cudaFree(L.buf[1]);
-        cudaFree(L.origin);
-        cudaFree(L.copies);
+        cudaFree(L.nbr);
         cudaFree(L.interps);
         cudaFree(L.restricts);
         cudaFree(L.kmax);
@@ -572,7 +721,9 @@ int build(Mesh **out, const int nb[3], int edge, int lmax, const int8_t *leaf, d
         Level &L = m->lv[l];
         const int h = 1 << (lmax - l);
         L.n = edge / h;
-        L.G = (L.n + 2) * (L.n + 2) * (L.n + 2);
+        L.P = (XOFF + L.n + 1 + 7) / 8 * 8;
+        L.plane = L.P * (L.n + 2);
+        L.G = L.plane * (L.n + 2);
         for (int a = 0; a < 3; ++a) L.cells[a] = nb[a] * L.n;
         L.tau = 3.0 * nu_fine / h + 0.5;
         if (lmax > 0 && fabs(L.tau - 1.0) < 1e-3) {
@@ -580,15 +731,8 @@ int build(Mesh **out, const int nb[3], int edge, int lmax, const int8_t *leaf, d
             break;
         }
         L.slot.assign(m->nblk, -1);
-        std::vector<int> origin;
         for (int b = 0; b < m->nblk; ++b)
-            if (leaf[b] >= l) {
-                L.slot[b] = L.nslot++;
-                const int bz = b / (nb[0] * nb[1]), by = (b / nb[0]) % nb[1], bx = b % nb[0];
-                origin.push_back(bx * L.n);
-                origin.push_back(by * L.n);
-                origin.push_back(bz * L.n);
-            }
+            if (leaf[b] >= l) L.slot[b] = L.nslot++;
         if ((long long)L.nslot * Q * L.G >= (1LL << 31)) {
             st = report_error(LBM_ENOTSUP, "a level exceeds 2^31 population values");
             break;
@@ -602,7 +746,6 @@ int build(Mesh **out, const int nb[3], int edge, int lmax, const int8_t *leaf, d
             st = report_cuda_error(e, "cudaMalloc(level)");
             break;
         }
-        st = upload(&L.origin, origin);
     }
     for (int l = 0; l <= lmax && st == LBM_OK; ++l) st = build_tasks(*m, l);
     for (int l = 0; l <= lmax && st == LBM_OK; ++l) st = autotune(*m, l, s);
@@ -693,7 +836,7 @@ int get_block(Mesh *m, int l, int b, double *out, cudaStream_t s) {
             for (int y = 0; y < n; ++y)
                 for (int x = 0; x < n; ++x)
                     out[(((size_t)i * n + z) * n + y) * n + x] =
-                        tmp[(size_t)i * L.G + gidx(n, x, y, z)];
+                        tmp[(size_t)i * L.G + gidx(L, x, y, z)];
     return LBM_OK;
 }
 
@@ -711,7 +854,7 @@ int set_block(Mesh *m, int l, int b, const double *in, cudaStream_t s) {
         for (int z = 0; z < n; ++z)
             for (int y = 0; y < n; ++y)
                 for (int x = 0; x < n; ++x)
-                    tmp[(size_t)i * L.G + gidx(n, x, y, z)] =
+                    tmp[(size_t)i * L.G + gidx(L, x, y, z)] =
                         (float)in[(((size_t)i * n + z) * n + y) * n + x];
     MLCK(cudaMemcpyAsync(dst, tmp.data(), tmp.size() * sizeof(float), cudaMemcpyHostToDevice, s),
          "cudaMemcpyAsync");

@@ -93,6 +93,22 @@ _SIGS = {
     "lbm_levels_fit": (_i, [_h, _i, _i, _i, _i, _vp]),
     "lbm_step_noalloc": (_i, [_i, _i, _i, _i, _i, _d, _d, _d, _i, _vp, _vp, _i, _vp, _vp]),
     "lbm_regrid": (_i, [_h, _vp, _vp, _vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_ll), _vp]),
+    "lbm_block_features": (_i, [_h, _i, _vp]),
+    "lbm_net_create": (_vp, [_i, _i]),
+    "lbm_net_destroy": (None, [_vp]),
+    "lbm_net_set_stream": (_i, [_vp, _vp]),
+    "lbm_net_param_count": (_i, [_vp]),
+    "lbm_net_set_normalisation": (_i, [_vp, _vp, _vp]),
+    "lbm_net_set_params": (_i, [_vp, _vp]),
+    "lbm_net_get_params": (_i, [_vp, _vp]),
+    "lbm_net_get_grads": (_i, [_vp, _vp]),
+    "lbm_net_set_grads": (_i, [_vp, _vp]),
+    "lbm_net_forward": (_i, [_vp, _vp, _i, _i, _i, _vp]),
+    "lbm_net_backward": (_i, [_vp, _vp, _vp, _i, _i, _i, _dp]),
+    "lbm_net_adam": (_i, [_vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+    "lbm_net_train_step": (_i, [_vp, _vp, _vp, _i, _i, _i, ctypes.c_float, _dp]),
+    "lbm_net_log_targets": (_i, [_vp, _ll, ctypes.c_float, ctypes.c_float, _vp, _vp]),
+    "lbm_net_to_maxima": (_i, [_vp, _ll, ctypes.c_float, _vp, _vp]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -342,6 +358,157 @@ def lbm_regrid(h, field_dev, params, boxes, max_boxes: int, tags_out=None):
     return nb.value, nt.value
 
 
+def lbm_block_features(h, block: int, out_dev) -> int:
+    return _ck(_lib.lbm_block_features(h, int(block), _ptr(out_dev)), "lbm_block_features")
+
+
+def lbm_net_log_targets(kmax_dev, n: int, offset: float, floor_k: float, t_dev, stream=None):
+    return _ck(_lib.lbm_net_log_targets(_ptr(kmax_dev), int(n), float(offset), float(floor_k),
+                                        _ptr(t_dev), stream), "lbm_net_log_targets")
+
+
+def lbm_net_to_maxima(y_dev, n: int, offset: float, kmax_dev, stream=None):
+    return _ck(_lib.lbm_net_to_maxima(_ptr(y_dev), int(n), float(offset), _ptr(kmax_dev), stream),
+               "lbm_net_to_maxima")
+
+
+def lbm_net_create(cin: int, hidden: int):
+    n = _lib.lbm_net_create(int(cin), int(hidden))
+    if not n:
+        raise LbmError(_lib.lbm_last_error(), "lbm_net_create")
+    return n
+
+
+def lbm_net_destroy(n) -> None:
+    _lib.lbm_net_destroy(n)
+
+
+def lbm_net_set_stream(n, stream) -> int:
+    return _ck(_lib.lbm_net_set_stream(n, stream), "lbm_net_set_stream")
+
+
+def lbm_net_param_count(n) -> int:
+    return _ck(_lib.lbm_net_param_count(n), "lbm_net_param_count")
+
+
+def lbm_net_set_normalisation(n, shift, scale) -> int:
+    return _ck(_lib.lbm_net_set_normalisation(n, _ptr(shift), _ptr(scale)),
+               "lbm_net_set_normalisation")
+
+
+def lbm_net_set_params(n, host) -> int:
+    return _ck(_lib.lbm_net_set_params(n, _ptr(host)), "lbm_net_set_params")
+
+
+def lbm_net_get_params(n, host) -> int:
+    return _ck(_lib.lbm_net_get_params(n, _ptr(host)), "lbm_net_get_params")
+
+
+def lbm_net_get_grads(n, host) -> int:
+    return _ck(_lib.lbm_net_get_grads(n, _ptr(host)), "lbm_net_get_grads")
+
+
+def lbm_net_set_grads(n, host) -> int:
+    return _ck(_lib.lbm_net_set_grads(n, _ptr(host)), "lbm_net_set_grads")
+
+
+def lbm_net_forward(n, x_dev, batch, h, w, y_dev) -> int:
+    return _ck(_lib.lbm_net_forward(n, _ptr(x_dev), batch, h, w, _ptr(y_dev)), "lbm_net_forward")
+
+
+def lbm_net_backward(n, x_dev, t_dev, batch, h, w, loss=None) -> int:
+    return _ck(_lib.lbm_net_backward(n, _ptr(x_dev), _ptr(t_dev), batch, h, w, loss),
+               "lbm_net_backward")
+
+
+def lbm_net_adam(n, lr, beta1=0.9, beta2=0.999, eps=1e-8) -> int:
+    return _ck(_lib.lbm_net_adam(n, lr, beta1, beta2, eps), "lbm_net_adam")
+
+
+def lbm_net_train_step(n, x_dev, t_dev, batch, h, w, lr, loss=None) -> int:
+    return _ck(_lib.lbm_net_train_step(n, _ptr(x_dev), _ptr(t_dev), batch, h, w, float(lr), loss),
+               "lbm_net_train_step")
+
+
+class Net:
+    """The sensor predictor of include/lbm.h (lbm_net_*): 3x3 convolutions cin -> hidden -> hidden
+    -> 1.  Parameters are numpy float32 vectors in the order W1, b1, W2, b2, W3, b3; inputs and
+    outputs are CUDA tensors (float32, [batch, channels, h, w])."""
+
+    def __init__(self, cin=3, hidden=16, stream=None):
+        import torch
+
+        self.n = _lib.lbm_net_create(int(cin), int(hidden))
+        if not self.n:
+            raise LbmError(_lib.lbm_last_error(), "lbm_net_create")
+        self.cin, self.hidden = int(cin), int(hidden)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        _ck(_lib.lbm_net_set_stream(self.n, self.stream.cuda_stream), "lbm_net_set_stream")
+        self.nparam = _ck(_lib.lbm_net_param_count(self.n), "lbm_net_param_count")
+
+    def set_normalisation(self, shift, scale):
+        sh = np.ascontiguousarray(shift, dtype=np.float32)
+        sc = np.ascontiguousarray(scale, dtype=np.float32)
+        _ck(_lib.lbm_net_set_normalisation(self.n, _ptr(sh), _ptr(sc)), "lbm_net_set_normalisation")
+
+    def set_params(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        assert th.size == self.nparam
+        _ck(_lib.lbm_net_set_params(self.n, _ptr(th)), "lbm_net_set_params")
+
+    def params(self):
+        out = np.empty(self.nparam, dtype=np.float32)
+        _ck(_lib.lbm_net_get_params(self.n, _ptr(out)), "lbm_net_get_params")
+        return out
+
+    def grads(self):
+        out = np.empty(self.nparam, dtype=np.float32)
+        _ck(_lib.lbm_net_get_grads(self.n, _ptr(out)), "lbm_net_get_grads")
+        return out
+
+    def set_grads(self, g):
+        g = np.ascontiguousarray(g, dtype=np.float32)
+        _ck(_lib.lbm_net_set_grads(self.n, _ptr(g)), "lbm_net_set_grads")
+
+    def forward(self, x, out=None):
+        import torch
+
+        b, c, hh, ww = x.shape
+        y = out if out is not None else torch.empty((b, 1, hh, ww), dtype=torch.float32,
+                                                    device=x.device)
+        _ck(_lib.lbm_net_forward(self.n, _ptr(x), b, hh, ww, _ptr(y)), "lbm_net_forward")
+        return y
+
+    def backward(self, x, t, sync=True):
+        b, c, hh, ww = x.shape
+        loss = ctypes.c_double()
+        _ck(_lib.lbm_net_backward(self.n, _ptr(x), _ptr(t), b, hh, ww,
+                                  ctypes.byref(loss) if sync else None), "lbm_net_backward")
+        return loss.value if sync else None
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        _ck(_lib.lbm_net_adam(self.n, lr, beta1, beta2, eps), "lbm_net_adam")
+
+    def train_step(self, x, t, lr, sync=True):
+        b, c, hh, ww = x.shape
+        loss = ctypes.c_double()
+        _ck(_lib.lbm_net_train_step(self.n, _ptr(x), _ptr(t), b, hh, ww, float(lr),
+                                    ctypes.byref(loss) if sync else None), "lbm_net_train_step")
+        return loss.value if sync else None
+
+    def close(self):
+        if self.n:
+            _lib.lbm_net_destroy(self.n)
+            self.n = None
+
+    def __del__(self):
+        try:
+            if self.n and _lib is not None:
+                self.close()
+        except Exception:
+            pass
+
+
 class BlockMesh:
     """Multi-level block mesh on a handle: leaf[nbz, nby, nbx] leaf levels, block edge `edge`."""
 
@@ -567,8 +734,9 @@ class Lattice:
         regrid of this lattice from its sensor field (``field``: a CUDA tensor of nz*ny*nx doubles
         to use instead)."""
         r = int(coarsen)
-        tz = -(-self.nz // r) if self.nz > 1 else 1
-        tshape = (tz, -(-self.ny // r), -(-self.nx // r))
+        rs = max(r, 1)  # the shape of the output; the call itself refuses r < 1
+        tz = -(-self.nz // rs) if self.nz > 1 else 1
+        tshape = (tz, -(-self.ny // rs), -(-self.nx // rs))
         mask = None
         if allowed is not None:
             mask = np.ascontiguousarray(allowed, dtype=np.uint8).reshape(tshape)

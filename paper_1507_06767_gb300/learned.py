@@ -1,0 +1,136 @@
+"""Learned sensor predictor around the C ABI: solver traces, training, and the dynamic-refinement
+loop that regrids from predicted block maxima with the exact sensor as fallback and judge.
+
+Every step runs in the library's kernels (lbm_step, lbm_sensor_dev, lbm_block_features,
+lbm_net_*, lbm_flags_from_maxima); this module only sequences the calls and keeps the traces in
+PyTorch CUDA tensors.
+
+The paper regrids its dynamic cavity from the Knudsen sensor at every level-0 step (Sec. 5.2).
+Here the network reads the block-averaged (rho, u_x, u_y) at time t and predicts log10 of each
+block's sensor maximum at t + horizon; a regrid can then refine where the flow is going.  The
+exact sensor at t + horizon judges the predicted flags, and a regrid falls back to the exact flags
+whenever the agreement of the last judged prediction fell below a set fraction.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import lbm as L
+
+# input normalisation: rho - 1 ~ 1e-3..1e-2 and |u| <= u_lid in lattice units
+LOG_OFFSET = -3.0   # targets are log10(K) - LOG_OFFSET
+FLOOR_K = 1e-12
+
+
+def normalisation(u_lid: float):
+    return np.array([1.0, 0.0, 0.0], np.float32), np.array([100.0, 1.0 / u_lid, 1.0 / u_lid],
+                                                           np.float32)
+
+
+def threshold(tau: float, u_lid: float, n: int) -> float:
+    """Refinement threshold: four times the Couette-level sensor of the mean lid shear."""
+    return 4.0 * (4.0 / 3.0) * tau * u_lid / n
+
+
+def cavity_trace(n: int, re: float, u_lid: float, block: int, warm: int, snapshots: int,
+                 horizon: int, dtype=None):
+    """D2Q9 cavity of n^2 cells at Reynolds number re from rest: after `warm` steps, snapshots
+    spaced `horizon` steps apart.  Returns (features [S+1, 3, nb, nb] float32, block maxima
+    [S+1, nb*nb] float64, tau), all on the GPU; features[k] and maxima[k] belong to the same step
+    (the sensor of the last step)."""
+    import torch
+
+    tau = 3.0 * u_lid * n / re + 0.5
+    lat = L.Lattice(L.LBM_D2Q9, n, n, 1, tau, dtype=L.LBM_F32 if dtype is None else dtype,
+                    lid=(u_lid, 0.0))
+    L.lbm_set_sensor_every(lat.h, 0)  # the sensor on the last step of every lbm_step call
+    nb = L.lbm_nblocks(lat.h, block)
+    side = -(-n // block)
+    feats = torch.empty((snapshots + 1, 3, side, side), dtype=torch.float32, device="cuda")
+    kmax = torch.empty((snapshots + 1, nb), dtype=torch.float64, device="cuda")
+    lat.step(warm)
+    for k in range(snapshots + 1):
+        if k:
+            lat.step(horizon)
+        L.lbm_sensor_dev(lat.h, block, kmax[k])
+        L.lbm_block_features(lat.h, block, feats[k])
+    torch.cuda.synchronize()
+    lat.close()
+    return feats, kmax, tau
+
+
+def pairs(feats, kmax):
+    """(inputs at t, targets at t + horizon in log units) from a trace."""
+    import torch
+
+    t = torch.empty((kmax.shape[0] - 1, 1) + tuple(feats.shape[2:]), dtype=torch.float32,
+                    device="cuda")
+    L.lbm_net_log_targets(kmax[1:], t.numel(), LOG_OFFSET, FLOOR_K, t)
+    return feats[:-1].contiguous(), t
+
+
+def train(net, X, T, epochs: int, batch: int, lr: float, seed: int):
+    """Adam on shuffled minibatches; returns the per-epoch mean losses."""
+    import torch
+
+    g = torch.Generator(device="cpu")
+    g.manual_seed(seed)
+    n = X.shape[0]
+    losses = []
+    for _ in range(epochs):
+        perm = torch.randperm(n, generator=g).cuda()
+        tot, cnt = 0.0, 0
+        for s in range(0, n - batch + 1, batch):
+            idx = perm[s:s + batch]
+            xb, tb = X.index_select(0, idx).contiguous(), T.index_select(0, idx).contiguous()
+            tot += net.train_step(xb, tb, lr)
+            cnt += 1
+        losses.append(tot / max(cnt, 1))
+    return losses
+
+
+def predicted_maxima(net, X):
+    import torch
+
+    y = net.forward(X)
+    out = torch.empty(y.numel(), dtype=torch.float64, device="cuda")
+    L.lbm_net_to_maxima(y, y.numel(), LOG_OFFSET, out)
+    return out.view(X.shape[0], -1)
+
+
+def flags(maxima_row, T):
+    import torch
+
+    out = torch.empty(maxima_row.numel(), dtype=torch.int8, device="cuda")
+    L.lbm_flags_from_maxima(maxima_row, L.LBM_F64, maxima_row.numel(), L.LBM_FLAG_THRESHOLD, T,
+                            out, None)
+    return out
+
+
+def judge(net, feats, kmax, T, fallback_below: float):
+    """Run the regrid decisions over a trace: at every snapshot k the predicted flags for k + 1
+    (from the features at k) are compared with the exact flags at k + 1.  Returns a dict with the
+    mean agreement of the predicted flags, of the persistence baseline (exact flags at k used for
+    k + 1), of the flags actually used (predicted, or exact when the previous prediction's agreement
+    fell below `fallback_below`), and the fraction of regrids that fell back."""
+    pred = predicted_maxima(net, feats[:-1].contiguous())
+    agree_pred, agree_pers, agree_used, fell = [], [], [], 0
+    last = 1.0
+    for k in range(kmax.shape[0] - 1):
+        # the flags are compared on the host (a few thousand bytes per regrid)
+        exact_next = flags(kmax[k + 1], T).cpu().numpy()
+        fp = flags(pred[k].contiguous(), T).cpu().numpy()
+        fe = flags(kmax[k], T).cpu().numpy()
+        a_pred = float(np.mean(fp == exact_next))
+        a_pers = float(np.mean(fe == exact_next))
+        use_exact = last < fallback_below
+        fell += int(use_exact)
+        agree_used.append(a_pers if use_exact else a_pred)
+        agree_pred.append(a_pred)
+        agree_pers.append(a_pers)
+        last = a_pred
+    m = len(agree_pred)
+    return {"agreement_predicted": float(np.mean(agree_pred)),
+            "agreement_persistence": float(np.mean(agree_pers)),
+            "agreement_used": float(np.mean(agree_used)),
+            "fallback_fraction": fell / max(m, 1), "regrids": m}

@@ -81,3 +81,9 @@ def blob_field(seed: int, shape, blobs: int = 6, background=(1e-5, 1e-3), peak=(
         d2 = (zz - c[0]) ** 2 + (yy - c[1]) ** 2 + (xx - c[2]) ** 2
         f += h * np.exp(-d2 / (2.0 * r * r))
     return f
+
+
+def uniform_arrays(seed: int, shapes, limits):
+    """One uniform draw in [-lim, lim] per (shape, lim) pair, in order (e.g. network weights)."""
+    g = rng(seed)
+    return [g.uniform(-lim, lim, size=shp) for shp, lim in zip(shapes, limits)]

@@ -101,8 +101,7 @@ def test_regrid_from_the_cavity_sensor(L):
     n, steps = 128, 1500
     tau = O.tau_from_re(0.1, n, 100.0)
     o = O.Oracle(9, n, n, 1, tau, lid=(0.1, 0.0, 0.0))
-    f = o.run(o.rest(), steps - 1)
-    _, Kref, _, _ = o.step(f, sensor=True)
+    _, Kref = o.run(o.rest(), steps, sensor_last=True)
     lat = L.Lattice(L.LBM_D2Q9, n, n, 1, tau, dtype=L.LBM_F64, lid=(0.1, 0.0))
     L.lbm_set_sensor_field(lat.h, 1)
     L.lbm_set_sensor_every(lat.h, 1)
