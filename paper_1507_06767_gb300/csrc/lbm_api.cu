@@ -144,6 +144,7 @@ StepParams params_of(const lbm_t *h) {
     p.omega = 1.0 / h->tau;
     p.lid_x = h->lid_x;
     p.lid_z = h->lid_z;
+    lbm::finish_params(p);
     p.err = h->err_dev;
     p.tile_zero = nullptr;
     return p;

@@ -101,6 +101,7 @@ extern "C" LBM_API int lbm_step_noalloc(int lattice, int dtype, int nx, int ny, 
     p.omega = 1.0 / tau;
     p.lid_x = lid_x;
     p.lid_z = lid_z;
+    lbm::finish_params(p);
     p.err = nullptr;
     p.tile_zero = nullptr;
     cudaStream_t s = static_cast<cudaStream_t>(stream);

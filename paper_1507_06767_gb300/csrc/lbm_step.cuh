@@ -41,6 +41,16 @@ constexpr int TILE = 8;
 #ifndef LBM_STORE_HINT
 #define LBM_STORE_HINT 0
 #endif
+// 1: CTAs whose cells and all their pull sources lie inside the lattice take a gather without
+// wall or wrap logic (one address offset per direction)
+#ifndef LBM_INTERIOR_FAST
+#define LBM_INTERIOR_FAST 1
+#endif
+// 1: rows whose y and z neighbours lie inside the lattice but that touch an x face take a gather
+// with only the x wall / wrap logic
+#ifndef LBM_XEDGE_PATH
+#define LBM_XEDGE_PATH 1
+#endif
 
 template <class T>
 __device__ __forceinline__ T load_pop(const T *p) {
@@ -64,7 +74,9 @@ __device__ __forceinline__ void store_pop(T *p, T v) {
 
 // Pull-gather of cell (x, y, z) in the general case (walls with moving-lid bounce-back, periodic
 // wrap): writes the deviations from rest df_i = f_i - w_i of the populations arriving at the cell.
-template <class L, int DT>
+// YZ_IN: the caller guarantees 1 <= y <= ny - 2 and (3-D) 1 <= z <= nz - 2, so only x can leave
+// the lattice.
+template <class L, int DT, bool YZ_IN = false>
 __device__ __forceinline__ void gather_cell(const typename Storage<DT>::T *__restrict__ fin,
                                             const StepParams &p, size_t N, int x, int y, int z,
                                             typename Storage<DT>::R *df) {
@@ -77,20 +89,20 @@ __device__ __forceinline__ void gather_cell(const typename Storage<DT>::T *__res
     const int xp = (x == nx - 1) ? 0 : x + 1;
     const bool vxm = (x > 0) || perx;
     const bool vxp = (x < nx - 1) || perx;
-    const int ym = (y == 0) ? ny - 1 : y - 1;
-    const int yp = (y == ny - 1) ? 0 : y + 1;
-    const bool vym = (y > 0) || pery;
-    const bool vyp = (y < ny - 1) || pery;  // false <=> the y+1 ghost is the lid
+    const int ym = (!YZ_IN && y == 0) ? ny - 1 : y - 1;
+    const int yp = (!YZ_IN && y == ny - 1) ? 0 : y + 1;
+    const bool vym = YZ_IN || (y > 0) || pery;
+    const bool vyp = YZ_IN || (y < ny - 1) || pery;  // false <=> the y+1 ghost is the lid
     int zm = z, zp = z;
     bool vzm = true, vzp = true;
     if (L::D == 3) {
-        zm = (z == 0) ? nz - 1 : z - 1;
-        zp = (z == nz - 1) ? 0 : z + 1;
-        vzm = (z > 0) || perz;
-        vzp = (z < nz - 1) || perz;
+        zm = (!YZ_IN && z == 0) ? nz - 1 : z - 1;
+        zp = (!YZ_IN && z == nz - 1) ? 0 : z + 1;
+        vzm = YZ_IN || (z > 0) || perz;
+        vzp = YZ_IN || (z < nz - 1) || perz;
     }
     const int idx = (z * ny + y) * nx + x;
-    const R lidx = (R)p.lid_x, lidz = (R)p.lid_z;
+    const R lidx = param_lid_x<R>(p), lidz = param_lid_z<R>(p);
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
         const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
@@ -108,6 +120,25 @@ __device__ __forceinline__ void gather_cell(const typename Storage<DT>::T *__res
             // moving lid: + 2 w_i (c_i . u_lid) / c_s^2, wall density 1
             v += R(6) * weight<L, R>(i) * (R(cx) * lidx + R(cz) * lidz);
         }
+        df[i] = v;
+    }
+}
+
+// Pull-gather of a cell whose q sources all lie inside the lattice (no wall, no wrap): population i
+// comes from idx - (c_z plane + c_y nx + c_x) of population i's array.
+template <class L, int DT>
+__device__ __forceinline__ void gather_interior(const typename Storage<DT>::T *__restrict__ fin,
+                                                size_t N, int nx, int plane, size_t idx,
+                                                typename Storage<DT>::R *df) {
+    using S = Storage<DT>;
+    using R = typename S::R;
+    const typename S::T *base = fin + idx;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        const long long off =
+            (long long)i * (long long)N - (long long)(L::cz(i) * plane + L::cy(i) * nx + L::cx(i));
+        R v = S::to_r(load_pop(base + off));
+        if (!S::SHIFTED) v -= weight<L, R>(i);
         df[i] = v;
     }
 }
@@ -178,7 +209,7 @@ __global__ void __launch_bounds__(CTA_X *CTA_Y, LBM_STEP_MIN_BLOCKS)
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const bool active = (x < nx) && (y < ny);
     const size_t N = (size_t)nx * ny * nz;
-    const R omega = (R)p.omega;
+    const R omega = param_omega<R>(p);
 
     // clear the other tile buffer for the next sensor step (kernels that combine tiles across
     // CTAs with atomics need it zeroed)
@@ -192,6 +223,10 @@ __global__ void __launch_bounds__(CTA_X *CTA_Y, LBM_STEP_MIN_BLOCKS)
     }
 
     B kmax = 0;
+    // a warp is one row of 32 cells: when the row and all its pull sources lie inside the lattice
+    // (a warp-uniform test) the gather needs no wall or wrap logic
+    const bool inner_x = blockIdx.x * CTA_X >= 1 && (blockIdx.x + 1) * CTA_X <= nx - 1;
+    const bool inner_y = y >= 1 && y <= ny - 2;
 
     for (int dz = 0; dz < ZT; ++dz) {
         const int z = z0 + dz;
@@ -199,7 +234,13 @@ __global__ void __launch_bounds__(CTA_X *CTA_Y, LBM_STEP_MIN_BLOCKS)
         if (active) {
             const int idx = (z * ny + y) * nx + x;
             R df[Q];
-            gather_cell<L, DT>(fin, p, N, x, y, z, df);
+            const bool inner_yz = inner_y && (L::D == 2 || (z >= 1 && z <= nz - 2));
+            if (LBM_INTERIOR_FAST && inner_yz && inner_x)
+                gather_interior<L, DT>(fin, N, nx, nx * ny, (size_t)idx, df);
+            else if (LBM_XEDGE_PATH && inner_yz)
+                gather_cell<L, DT, true>(fin, p, N, x, y, z, df);
+            else
+                gather_cell<L, DT>(fin, p, N, x, y, z, df);
             const R K = relax_store_cell<L, DT, MODE>(df, omega, fout, N, idx);
             if (MODE != 0) {
                 const B kb = max_bits(K);

@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(CTA_X *CTA_Y, LBM_PAIR_MIN_BLOCKS)
         }
 
         T *out0 = fout + idx0;
-        const float2 K = relax_pair<L, DT, MODE>(df, (float)p.omega, [&](int i, float2 v) {
+        const float2 K = relax_pair<L, DT, MODE>(df, p.omega_f, [&](int i, float2 v) {
             PairIO<DT>::store2(out0 + (size_t)i * N, v);
         });
         if (MODE != 0) {

@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(TMA_THREADS, TMA_CTAS_PER_SM)
     }
 
     // -------------------------------------------------------------------- consumer warps
-    const float omega = (float)p.omega;
+    const float omega = p.omega_f;
     int g = 0;
     for (int u = blockIdx.x; u < U; u += gridDim.x) {
         const TmaUnit w = tma_unit(u, uxc, ny, nz);

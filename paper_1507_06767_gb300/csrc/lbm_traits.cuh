@@ -128,8 +128,36 @@ struct StepParams {
     int ntx, nty, ntz; // base tiles per axis
     double omega;      // 1 / tau
     double lid_x, lid_z;
+    float omega_f, lid_x_f, lid_z_f;  // the same in float (no FP64 conversion in FP32 kernels)
     int *err;          // device-visible error word for bounded waits (may be null)
     void *tile_zero;   // tile-maxima buffer a sensor step clears for the next one (may be null)
 };
+
+// The relaxation rate and lid velocity in the kernel's arithmetic type.
+template <class R>
+__device__ __forceinline__ R param_omega(const StepParams &p);
+template <>
+__device__ __forceinline__ double param_omega<double>(const StepParams &p) { return p.omega; }
+template <>
+__device__ __forceinline__ float param_omega<float>(const StepParams &p) { return p.omega_f; }
+template <class R>
+__device__ __forceinline__ R param_lid_x(const StepParams &p);
+template <>
+__device__ __forceinline__ double param_lid_x<double>(const StepParams &p) { return p.lid_x; }
+template <>
+__device__ __forceinline__ float param_lid_x<float>(const StepParams &p) { return p.lid_x_f; }
+template <class R>
+__device__ __forceinline__ R param_lid_z(const StepParams &p);
+template <>
+__device__ __forceinline__ double param_lid_z<double>(const StepParams &p) { return p.lid_z; }
+template <>
+__device__ __forceinline__ float param_lid_z<float>(const StepParams &p) { return p.lid_z_f; }
+
+// Fill the float copies of the double parameters (host side, after omega and the lid are set).
+inline void finish_params(StepParams &p) {
+    p.omega_f = (float)p.omega;
+    p.lid_x_f = (float)p.lid_x;
+    p.lid_z_f = (float)p.lid_z;
+}
 
 }  // namespace lbm
