@@ -453,7 +453,10 @@ def run_learned(args, w, ws, rank, local):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
                      "kernel": "fused_step_kernel (D2Q9 FP32, 72 B per cell)",
-                     "kernel_ms": round(avg_kernel_ms, 5)},
+                     "kernel_ms": round(avg_kernel_ms, 5),
+                     "note": "kernel_ms from a pass with per-launch events, which lengthen a "
+                             "~12 us launch; the loop's own time per step bounds it from above",
+                     "loop_gbs": round(per_launch / (ms / steps / 1e3) / 1e9, 1)},
         "e2e": {"value": round(n * n * steps * ws / e2e_s / 1e6, 1), "unit": "MLUPS",
                 "h2d_bytes_per_step": 0, "d2h_bytes_per_step": round(side * side / hz, 2)},
         "gpu_launches": steps + nreg * 6,

@@ -46,11 +46,6 @@ constexpr int TILE = 8;
 #ifndef LBM_INTERIOR_FAST
 #define LBM_INTERIOR_FAST 1
 #endif
-// 1: rows whose y and z neighbours lie inside the lattice but that touch an x face take a gather
-// with only the x wall / wrap logic
-#ifndef LBM_XEDGE_PATH
-#define LBM_XEDGE_PATH 1
-#endif
 
 template <class T>
 __device__ __forceinline__ T load_pop(const T *p) {
@@ -73,10 +68,9 @@ __device__ __forceinline__ void store_pop(T *p, T v) {
 }
 
 // Pull-gather of cell (x, y, z) in the general case (walls with moving-lid bounce-back, periodic
-// wrap): writes the deviations from rest df_i = f_i - w_i of the populations arriving at the cell.
-// YZ_IN: the caller guarantees 1 <= y <= ny - 2 and (3-D) 1 <= z <= nz - 2, so only x can leave
-// the lattice.
-template <class L, int DT, bool YZ_IN = false>
+// wrap): writes the deviations from rest df_i = f_i - w_i of the populations arriving at the cell
+// to df[i * STRIDE] (STRIDE 2 fills one lane of an array of pairs).
+template <class L, int DT, int STRIDE = 1>
 __device__ __forceinline__ void gather_cell(const typename Storage<DT>::T *__restrict__ fin,
                                             const StepParams &p, size_t N, int x, int y, int z,
                                             typename Storage<DT>::R *df) {
@@ -89,17 +83,17 @@ __device__ __forceinline__ void gather_cell(const typename Storage<DT>::T *__res
     const int xp = (x == nx - 1) ? 0 : x + 1;
     const bool vxm = (x > 0) || perx;
     const bool vxp = (x < nx - 1) || perx;
-    const int ym = (!YZ_IN && y == 0) ? ny - 1 : y - 1;
-    const int yp = (!YZ_IN && y == ny - 1) ? 0 : y + 1;
-    const bool vym = YZ_IN || (y > 0) || pery;
-    const bool vyp = YZ_IN || (y < ny - 1) || pery;  // false <=> the y+1 ghost is the lid
+    const int ym = (y == 0) ? ny - 1 : y - 1;
+    const int yp = (y == ny - 1) ? 0 : y + 1;
+    const bool vym = (y > 0) || pery;
+    const bool vyp = (y < ny - 1) || pery;  // false <=> the y+1 ghost is the lid
     int zm = z, zp = z;
     bool vzm = true, vzp = true;
     if (L::D == 3) {
-        zm = (!YZ_IN && z == 0) ? nz - 1 : z - 1;
-        zp = (!YZ_IN && z == nz - 1) ? 0 : z + 1;
-        vzm = YZ_IN || (z > 0) || perz;
-        vzp = YZ_IN || (z < nz - 1) || perz;
+        zm = (z == 0) ? nz - 1 : z - 1;
+        zp = (z == nz - 1) ? 0 : z + 1;
+        vzm = (z > 0) || perz;
+        vzp = (z < nz - 1) || perz;
     }
     const int idx = (z * ny + y) * nx + x;
     const R lidx = param_lid_x<R>(p), lidz = param_lid_z<R>(p);
@@ -120,7 +114,7 @@ __device__ __forceinline__ void gather_cell(const typename Storage<DT>::T *__res
             // moving lid: + 2 w_i (c_i . u_lid) / c_s^2, wall density 1
             v += R(6) * weight<L, R>(i) * (R(cx) * lidx + R(cz) * lidz);
         }
-        df[i] = v;
+        df[i * STRIDE] = v;
     }
 }
 
@@ -234,11 +228,9 @@ __global__ void __launch_bounds__(CTA_X *CTA_Y, LBM_STEP_MIN_BLOCKS)
         if (active) {
             const int idx = (z * ny + y) * nx + x;
             R df[Q];
-            const bool inner_yz = inner_y && (L::D == 2 || (z >= 1 && z <= nz - 2));
-            if (LBM_INTERIOR_FAST && inner_yz && inner_x)
+            // (a third path for rows that touch only an x face measured slower: spills)
+            if (LBM_INTERIOR_FAST && inner_x && inner_y && (L::D == 2 || (z >= 1 && z <= nz - 2)))
                 gather_interior<L, DT>(fin, N, nx, nx * ny, (size_t)idx, df);
-            else if (LBM_XEDGE_PATH && inner_yz)
-                gather_cell<L, DT, true>(fin, p, N, x, y, z, df);
             else
                 gather_cell<L, DT>(fin, p, N, x, y, z, df);
             const R K = relax_store_cell<L, DT, MODE>(df, omega, fout, N, idx);

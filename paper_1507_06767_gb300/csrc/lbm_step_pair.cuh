@@ -170,13 +170,9 @@ __global__ void __launch_bounds__(CTA_X *CTA_Y, LBM_PAIR_MIN_BLOCKS)
                 df[i] = v;
             }
         } else {
-            float a[Q];
-            gather_cell<L, DT>(fin, p, N, x0, y, z, a);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) df[i].x = a[i];
-            gather_cell<L, DT>(fin, p, N, x0 + 1, y, z, a);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) df[i].y = a[i];
+            // each cell of the pair straight into its lane of df (no staging array)
+            gather_cell<L, DT, 2>(fin, p, N, x0, y, z, reinterpret_cast<float *>(df));
+            gather_cell<L, DT, 2>(fin, p, N, x0 + 1, y, z, reinterpret_cast<float *>(df) + 1);
         }
 
         T *out0 = fout + idx0;

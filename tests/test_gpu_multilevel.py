@@ -121,3 +121,39 @@ def test_block_mesh_argument_errors(L):
         assert ei.value.status == L.LBM_ESTATE
     finally:
         L.lbm_destroy(h)
+
+
+def test_bench_mesh_full_size_one_cycle(L):
+    """The multi-level benchmark mesh at full size (16^3 blocks of 32 finest cells, 512^3 finest,
+    3 levels; 4096 / 1408 / 336 blocks at levels 0 / 1 / 2), in its benchmark launch configuration
+    (autotuned shapes, graph replay): every block of every level set to a seeded perturbed state,
+    one cycle on the GPU and in the FP64 oracle, every block of every level compared (2e-6, as
+    above; FP32 storage of the seeded state is a 6e-8 relative difference of the inputs)."""
+    import bench
+    from tests import seeded
+
+    w = bench.WORKLOADS["d3q19_blocks_512_3level"]
+    leaf = bench.block_placement(w, L)
+    tau = bench.tau_of(w)
+    g = L.BlockMesh(leaf, w["block"], w["lmax"], tau, lid=(w["u"], 0.0))
+    g.step(0)  # builds the mesh (and autotunes) at rest
+    o = O.MultiLevel(leaf, w["block"], w["lmax"], tau, lid=(w["u"], 0.0, 0.0))
+    _, wts, _ = O.lattice(19)
+    rng = seeded.rng(4096)
+    flat = leaf.reshape(-1)
+    for level in range(w["lmax"] + 1):
+        n = g.info(level)[0]
+        for b in np.where(flat >= level)[0]:
+            f = wts[:, None, None, None] * (1.0 + rng.uniform(-0.01, 0.01, size=(19, n, n, n)))
+            g.set_block(level, int(b), f)
+            o.set_block(level, int(b), f)
+    g.step(1)
+    o.cycles(1)
+    worst = 0.0
+    for level in range(w["lmax"] + 1):
+        for b in np.where(flat >= level)[0]:
+            ref = o.get_block(level, int(b))
+            worst = max(worst, float(np.abs(g.get_block(level, int(b)) - ref).max() /
+                                     np.abs(ref).max()))
+    assert worst < 2e-6, worst
+    g.close()

@@ -425,3 +425,85 @@ def test_levels_and_time_average(L, q, dims, dtype, kband):
         assert np.array_equal(fit[~near], O.levels_fit(ref, 1, 3)[~near]), src
         assert fit.min() == 1 and fit.max() == 3
     lat.close()
+
+
+# ------------------------------------------------------- 512^3 16-bit storage, full size, sampled
+def decode16(raw16, dtype_name):
+    """Stored 16-bit deviations f - w_i as float64."""
+    if dtype_name == "F16S":
+        return raw16.view(np.float16).astype(np.float64)
+    return (raw16.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("dtype_name,rel_store", [("F16S", 2.0 ** -10), ("BF16S", 2.0 ** -7)])
+def test_cavity_d3q19_512_16bit_full_size_sampled(L, dtype_name, rel_store):
+    """The 512^3 D3Q19 mixed-precision workloads in the benchmark's launch configuration (the
+    two-cell kernel, sensor every step): one step from a seeded perturbed 16-bit state.  The oracle
+    evaluates sampled sub-boxes of 20^3 cells taken from the decoded state (corners under the lid,
+    edges, faces, the middle): every cell whose pull sources lie in the sub-box, or beyond a face
+    that is a wall of the full lattice, has the same inputs as in the full lattice.  Outputs are
+    compared in deviation form within the 16-bit storage rounding (2^-11 / 2^-8 of the value, with
+    a factor 2 margin, plus 1e-7 absolute for values in the half subnormal range), and the block
+    maxima of 16^3 blocks against the oracle's within 1e-5 (FP32 arithmetic on identical stored
+    inputs)."""
+    n, q = 512, 19
+    tau = O.tau_from_re(0.1, n, 1000.0)
+    lat = L.Lattice(q, n, n, n, tau, dtype=getattr(L, "LBM_" + dtype_name), lid=(0.1, 0.0))
+    L.lbm_set_sensor_every(lat.h, 1)
+    c, w, _ = O.lattice(q)
+    N = n ** 3
+    g = seeded.rng(512)
+    raw = np.empty((q, N), dtype=np.uint16)
+    for i in range(q):  # stored deviations w_i * U(-0.03, 0.03), drawn population by population
+        d = (w[i] * g.uniform(-0.03, 0.03, size=N)).astype(np.float32)
+        if dtype_name == "F16S":
+            raw[i] = d.astype(np.float16).view(np.uint16)
+        else:  # round to nearest even on the upper 16 bits
+            b = d.view(np.uint32)
+            raw[i] = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16).astype(np.uint16)
+        del d
+    lat.set_raw(raw.view(np.uint8).reshape(-1))
+    lat.step(1)
+    out = lat.raw().view(np.uint16).reshape(q, n, n, n)
+    gmax = lat.sensor(16)
+    lat.close()
+    raw = raw.reshape(q, n, n, n)
+    S = 20
+    origins = [(0, 0, 0), (n - S, n - S, n - S), (0, n - S, 0), (n - S, n - S, 0), (n - S, 0, n - S),
+               (n // 2, n // 2, n // 2), (0, n // 3, n - S), (n // 4, n - S, n // 2)]
+    checked = 0
+    for (x0, y0, z0) in origins:
+        sub = decode16(raw[:, z0:z0 + S, y0:y0 + S, x0:x0 + S].copy(), dtype_name)
+        f_sub = sub + w[:, None, None, None]
+        o = O.Oracle(q, S, S, S, tau, lid=(0.1, 0.0, 0.0) if y0 + S == n else (0.0, 0.0, 0.0))
+        ok = []
+        for a, a0 in ((0, x0), (1, y0), (2, z0)):
+            loc = np.arange(S)
+            good = (loc >= 1) & (loc <= S - 2)
+            good |= (loc == 0) & (a0 == 0)
+            good |= (loc == S - 1) & (a0 + S == n)
+            ok.append(good)
+        zz, yy, xx = np.meshgrid(np.where(ok[2])[0], np.where(ok[1])[0], np.where(ok[0])[0],
+                                 indexing="ij")
+        cells = ((zz * S + yy) * S + xx).reshape(-1)
+        ref, K = o.step_cells(f_sub, cells)
+        got = decode16(out[:, z0:z0 + S, y0:y0 + S, x0:x0 + S].copy(), dtype_name).reshape(q, -1)
+        got = got[:, cells].T
+        dref = ref - w[None, :]
+        err = np.abs(got - dref)
+        # 1e-7 absolute: the half spacing below 2^-14 is 2^-24, plus FP32 arithmetic
+        assert (err <= rel_store * np.abs(dref) + 1e-7).all(), (x0, y0, z0, err.max())
+        checked += len(cells)
+    assert checked > 30000
+    # sampled 16^3 blocks with their one-cell margin (or a real wall) inside an 18^3 sub-box
+    nb = n // 16
+    for (bx, by, bz) in ((0, 0, 0), (nb - 1, nb - 1, nb - 1), (0, nb - 1, nb - 1), (nb // 2, nb - 1, 3),
+                         (7, 11, 13)):
+        x0, y0, z0 = [max(0, min(n - 18, 16 * b - 1)) for b in (bx, by, bz)]
+        sub = decode16(raw[:, z0:z0 + 18, y0:y0 + 18, x0:x0 + 18].copy(), dtype_name)
+        o = O.Oracle(q, 18, 18, 18, tau, lid=(0.1, 0.0, 0.0) if y0 + 18 == n else (0.0, 0.0, 0.0))
+        zz, yy, xx = np.meshgrid(np.arange(16) + 16 * bz - z0, np.arange(16) + 16 * by - y0,
+                                 np.arange(16) + 16 * bx - x0, indexing="ij")
+        _, K = o.step_cells(sub + w[:, None, None, None], ((zz * 18 + yy) * 18 + xx).reshape(-1))
+        bidx = (bz * nb + by) * nb + bx
+        assert abs(gmax[bidx] - K.max()) / K.max() < 1e-5, (bx, by, bz)
