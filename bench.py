@@ -90,27 +90,35 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def step_kernel_of(w):
+def step_kernel_of(w, variant="auto"):
     """Name of the fused step kernel the library picks for the workload (LBM_KERNEL_AUTO: the
-    two-cell packed kernel for 16-bit storage with an even nx, else the one-cell kernel) and the
-    headers that define it."""
-    if w["dtype"] in ("F16S", "BF16S") and w["n"] % 2 == 0:
-        return "fused_step_pair_kernel", ("lbm_step_pair.cuh", "lbm_step.cuh", "lbm_traits.cuh")
+    two-cell packed kernel for 16-bit storage with an even nx on D2Q9 and on D3Q19 lattices of at
+    least 2^26 cells, else the one-cell kernel) and the headers that define it."""
+    cells = w["n"] ** (3 if w["q"] == 19 else 2)
+    pair = ("fused_step_pair_kernel", ("lbm_step_pair.cuh", "lbm_step.cuh", "lbm_traits.cuh"))
+    if variant == "pair":
+        return pair
+    if variant == "tma":
+        return "fused_step_tma_kernel", ("lbm_step_tma.cuh", "lbm_step.cuh", "lbm_traits.cuh")
+    if variant == "auto" and w["dtype"] in ("F16S", "BF16S") and w["n"] % 2 == 0 and (
+            w["q"] == 9 or cells >= 1 << 26):
+        return pair
     return "fused_step_kernel", ("lbm_step.cuh", "lbm_traits.cuh")
 
 
-def kernel_source_hash(w):
+def kernel_source_hash(w, variant="auto"):
     h = hashlib.sha256()
-    for fn in step_kernel_of(w)[1]:
+    for fn in step_kernel_of(w, variant)[1]:
         with open(os.path.join(ROOT, "paper_1507_06767_gb300", "csrc", fn), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload, w):
+def recorded_traffic(workload, w, variant="auto"):
     """DRAM bytes per launch of the fused step from the committed ncu summary, if it was taken on
-    the current kernel source at the lattice size run now; else None."""
-    if w["n"] != WORKLOADS[workload]["n"]:
+    the current kernel source at the lattice size run now, with the default kernel choice; else
+    None."""
+    if w["n"] != WORKLOADS[workload]["n"] or variant != "auto":
         return None
     path = os.path.join(ROOT, "profiles", f"fused_step_{workload}.md")
     if not os.path.exists(path):
@@ -118,7 +126,7 @@ def recorded_traffic(workload, w):
     txt = open(path).read()
     m_src = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
     m_tr = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    if not m_src or not m_tr or m_src.group(1) != kernel_source_hash(w):
+    if not m_src or not m_tr or m_src.group(1) != kernel_source_hash(w, variant):
         return None
     return float(m_tr.group(1))
 
@@ -481,6 +489,7 @@ def run_ours(args, w, ws, rank, local):
     dtype = getattr(L, "LBM_" + w["dtype"])
     lat = L.Lattice(q, n, n, nz, tau, dtype=dtype, lid=(w["u"], 0.0))
     h = lat.h
+    L.lbm_set_kernel_variant(h, getattr(L, "LBM_KERNEL_" + args.kernel.upper()))
     L.lbm_set_sensor_every(h, w["sensor_every"])
     lat.block = w["block"]
     nb = L.lbm_nblocks(h, w["block"])
@@ -553,8 +562,9 @@ def run_ours(args, w, ws, rank, local):
     avg_kernel_ms = k_ms / max(k_n, 1)
     achieved = per_launch_bytes / (avg_kernel_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": recorded_traffic(args.workload, w),
-                "peak_kind": peak_kind, "kernel": step_kernel_of(w)[0],
+                "frac": round(achieved / peak, 4),
+                "traffic": recorded_traffic(args.workload, w, args.kernel),
+                "peak_kind": peak_kind, "kernel": step_kernel_of(w, args.kernel)[0],
                 "kernel_ms": round(avg_kernel_ms, 5),
                 "algorithmic_bytes_per_launch": per_launch_bytes}
     # launches of our kernels in the timed region: fused step every step, plus tile->block and
@@ -664,6 +674,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "cell", "pair", "tma"],
+                    help="fused step kernel (default: the library's automatic choice)")
     ap.add_argument("--edge", type=int, default=None,
                     help="run the workload on a lattice of this edge instead (small profiling "
                          "captures); the JSON line then names the edge in its config")
