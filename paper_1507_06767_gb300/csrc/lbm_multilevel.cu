@@ -193,30 +193,6 @@ __device__ __forceinline__ float step_cell(const float *__restrict__ in, const f
     const bool xl = x == 0, xh = x == n - 1, yl = y == 0, yh = y == n - 1;
     const bool zl = z == 0, zh = z == n - 1;
     float df[Q];
-    if (!(yl | yh | zl | zh)) {
-        // y and z neighbours inside the block: only pulls along x can leave it, to the x
-        // neighbour block (or its interpolated ghosts, or a wall)
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-            const int off = cz * plane + cy * row + cx;
-            float v;
-            if (cx == 0 || !(cx == 1 ? xl : xh)) {
-                v = src[i * G + g - off];
-            } else {
-                const int dx = -cx;
-                const int nb = snb[(dx + 1) + 3 + 9];
-                if (nb >= 0)
-                    v = in[(size_t)nb * Q * G + i * G + g - off - dx * n];
-                else if (nb == NB_GHOST)
-                    v = src[i * G + g - off];
-                else
-                    v = src[L::opp(i) * G + g];
-            }
-            df[i] = v - weight<L, float>(i);
-        }
-        return relax_store_cell<L, 1, 1>(df, a.omega, dst, (size_t)G, g);
-    }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
