@@ -626,17 +626,43 @@ def oracle_sample(w, n_edge, steps, rng_note=""):
     return cells * steps / dt / 1e6, dt, O.threads()
 
 
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+
+    return platform.machine()
+
+
 def cpu_baseline_block(w):
-    """The oracle on the host cores on a bounded sample of the full workload."""
+    """The oracle on the host cores on a bounded sample of the full workload (all cores), plus a
+    single-thread sample on a smaller cube of the same cavity."""
+    import oracle as O
+
     n = w["n"]
     cells = cells_of(w)
     # calibrate on a couple of steps, then size the sample to ~15 s
     rate, _, _ = oracle_sample(w, min(n, 64 if w["q"] == 19 else 128), 2)
     steps = max(2, min(200, int(15.0 * rate * 1e6 / cells)))
     mlups, dt, threads = oracle_sample(w, n, steps)
+    prev = O.set_threads(1)
+    try:
+        edge = min(n, 64 if w["q"] == 19 else 256)
+        one, dt1, _ = oracle_sample(w, edge, 4)
+    finally:
+        O.set_threads(prev)
+    dim = 3 if w["q"] == 19 else 2
     return {"value": round(mlups, 3), "unit": "MLUPS", "cores": threads, "kind": "oracle",
-            "sample": f"{steps} steps of the full {n}^{3 if w['q'] == 19 else 2} lattice from rest, "
-                      f"FP64, sensor+block max+flags every sensor step ({dt:.1f} s)"}
+            "sample": f"{steps} steps of the full {n}^{dim} lattice from rest, "
+                      f"FP64, sensor+block max+flags every sensor step ({dt:.1f} s)",
+            "single_thread": {"value": round(one, 3), "unit": "MLUPS",
+                              "sample": f"4 steps of a {edge}^{dim} cube ({dt1:.1f} s)"},
+            "cpu": cpu_model()}
 
 
 def run_reference(args, w):

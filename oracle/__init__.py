@@ -88,6 +88,7 @@ def _load():
             lib.orc_step_cells.argtypes = [pp, dp, ctypes.c_longlong,
                                            ctypes.POINTER(ctypes.c_longlong), dp, dp]
             lib.orc_threads.argtypes = []
+            lib.orc_set_threads.argtypes = [ctypes.c_int]
             lib.ml_create.argtypes = [ctypes.POINTER(_MLDesc), ctypes.POINTER(ctypes.c_int8),
                                       ctypes.POINTER(ctypes.c_int)]
             lib.ml_create.restype = ctypes.c_void_p
@@ -102,7 +103,7 @@ def _load():
             for name in ("ml_cycles", "ml_block_max", "ml_get_block", "ml_set_block",
                          "ml_level_info"):
                 getattr(lib, name).restype = ctypes.c_int
-            for name in ("orc_threads", "orc_step_cells", "orc_lattice", "orc_step", "orc_run", "orc_collide", "orc_stream_push",
+            for name in ("orc_threads", "orc_set_threads", "orc_step_cells", "orc_lattice", "orc_step", "orc_run", "orc_collide", "orc_stream_push",
                          "orc_sensor", "orc_equilibrium", "orc_block_max", "orc_conservation"):
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
@@ -126,6 +127,11 @@ def _check(status: int, what: str):
 def threads() -> int:
     """Threads the oracle's parallel loops use (OpenMP; OMP_NUM_THREADS caps it)."""
     return int(_load().orc_threads())
+
+
+def set_threads(n: int) -> int:
+    """Use n threads in the oracle's parallel loops from now on; returns the previous count."""
+    return int(_load().orc_set_threads(int(n)))
 
 
 def lattice(q: int):

@@ -316,6 +316,18 @@ int orc_threads(void) {
 #endif
 }
 
+/* Set the number of threads of the oracle's parallel loops (n >= 1); returns the previous count. */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    const int old = omp_get_max_threads();
+    if (n >= 1) omp_set_num_threads(n);
+    return old;
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 /* Run n pull steps in place on fs (scratch holds the other buffer).  K (if given) receives the
  * sensor of the last step. */
 int orc_run(const orc_params *p, double *fs, double *scratch, int n, double *K) {

@@ -112,9 +112,10 @@ struct lbm_s {
     // multi-level block mesh of lbm_blocks_step (built on first use)
     lbm::ml::Mesh *mesh = nullptr;
 
-    // graph cache: runs of two plain steps, by starting buffer
-    cudaGraphExec_t pair_exec[2] = {nullptr, nullptr};
-    cudaStream_t pair_stream[2] = {nullptr, nullptr};
+    // graph cache: runs of RUN_LEN[k] plain steps (k = 0: 2 steps, 1: 16 steps), by starting
+    // buffer
+    cudaGraphExec_t pair_exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    cudaStream_t pair_stream[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     bool pair_valid = false;
 
     int rtype() const { return dtype == LBM_F64 ? LBM_F64 : LBM_F32; }
@@ -124,11 +125,14 @@ struct lbm_s {
 
 namespace {
 
+constexpr int RUN_LEN[2] = {2, 16};  // plain steps per cached graph (even: parity is kept)
+
 void drop_graphs(lbm_t *h) {
-    for (int k = 0; k < 2; ++k) {
-        if (h->pair_exec[k]) cudaGraphExecDestroy(h->pair_exec[k]);
-        h->pair_exec[k] = nullptr;
-    }
+    for (int j = 0; j < 2; ++j)
+        for (int k = 0; k < 2; ++k) {
+            if (h->pair_exec[j][k]) cudaGraphExecDestroy(h->pair_exec[j][k]);
+            h->pair_exec[j][k] = nullptr;
+        }
     h->pair_valid = false;
 }
 
@@ -257,14 +261,16 @@ int timed_step(lbm_t *h, int mode) {
 }
 
 // Capture (once per stream and starting buffer) a graph of two plain steps: src -> other -> src.
-int pair_graph(lbm_t *h, int src, cudaGraphExec_t *out) {
-    if (h->pair_valid && h->pair_exec[src] && h->pair_stream[src] == h->stream) {
-        *out = h->pair_exec[src];
+// The cached graph of RUN_LEN[len] plain steps starting from buffer src (captured on first use).
+int pair_graph(lbm_t *h, int src, int len, cudaGraphExec_t *out) {
+    cudaGraphExec_t &slot = h->pair_exec[len][src];
+    if (h->pair_valid && slot && h->pair_stream[len][src] == h->stream) {
+        *out = slot;
         return LBM_OK;
     }
-    if (h->pair_exec[src]) {
-        cudaGraphExecDestroy(h->pair_exec[src]);
-        h->pair_exec[src] = nullptr;
+    if (slot) {
+        cudaGraphExecDestroy(slot);
+        slot = nullptr;
     }
     cudaStream_t cap;
     CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "cudaStreamCreate");
@@ -272,8 +278,8 @@ int pair_graph(lbm_t *h, int src, cudaGraphExec_t *out) {
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         const StepParams p = params_of(h);
-        for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-            const int s = src ^ k;
+        for (int k = 0; k < RUN_LEN[len] && e == cudaSuccess; ++k) {
+            const int s = src ^ (k & 1);
             if (h->q == LBM_D2Q9)
                 e = lbm::step_d2q9(h->dtype, h->buf[s], h->buf[s ^ 1], p, 0, nullptr, nullptr, cap,
                                    h->variant);
@@ -284,16 +290,16 @@ int pair_graph(lbm_t *h, int src, cudaGraphExec_t *out) {
         cudaError_t e2 = cudaStreamEndCapture(cap, &g);
         if (e == cudaSuccess) e = e2;
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->pair_exec[src], g, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&slot, g, 0);
     if (g) cudaGraphDestroy(g);
     cudaStreamDestroy(cap);
     if (e != cudaSuccess) {
-        h->pair_exec[src] = nullptr;
+        slot = nullptr;
         return cuda_fail(e, "graph capture");
     }
-    h->pair_stream[src] = h->stream;
+    h->pair_stream[len][src] = h->stream;
     h->pair_valid = true;
-    *out = h->pair_exec[src];
+    *out = slot;
     return LBM_OK;
 }
 
@@ -619,13 +625,19 @@ LBM_API int lbm_step(lbm_t *h, int n) {
                 ++run;
             }
             if (run >= 4) {
-                cudaGraphExec_t ge;
-                st = pair_graph(h, h->cur, &ge);
-                if (st != LBM_OK) return st;
-                const int pairs = run / 2;
-                for (int k = 0; k < pairs; ++k) CK(cudaGraphLaunch(ge, h->stream), "cudaGraphLaunch");
-                h->t += 2LL * pairs;
-                s += 2 * pairs;
+                // whole runs of 16 steps, then pairs; every graph keeps the buffer parity
+                for (int len = 1; len >= 0; --len) {
+                    const int count = run / RUN_LEN[len];
+                    if (count == 0) continue;
+                    cudaGraphExec_t ge;
+                    st = pair_graph(h, h->cur, len, &ge);
+                    if (st != LBM_OK) return st;
+                    for (int k = 0; k < count; ++k)
+                        CK(cudaGraphLaunch(ge, h->stream), "cudaGraphLaunch");
+                    h->t += (long long)count * RUN_LEN[len];
+                    s += count * RUN_LEN[len];
+                    run -= count * RUN_LEN[len];
+                }
                 continue;
             }
         }

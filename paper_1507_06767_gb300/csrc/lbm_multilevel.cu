@@ -49,9 +49,21 @@ constexpr int MAXL = 3;
 constexpr int NB_GHOST = -1;  // the neighbouring block exists only on a coarser level
 constexpr int NB_WALL = -2;   // the neighbouring block lies outside the (non-periodic) domain
 constexpr int NB_TOP = 16;    // index of the (0, +1, 0) neighbour: (dx+1) + 3 (dy+1) + 9 (dz+1)
-// interior x = 0 sits XOFF floats into its row (one 32-byte sector, so whole interior rows start
-// on a sector boundary); rows are padded to a multiple of 8 floats
-constexpr int XOFF = 8;
+// Block layout of one population: (n + 2) planes z = -1..n of (n + 2) rows y = -1..n of n cells
+// x = 0..n-1 (interior rows contiguous, no padding), then the two x-ghost columns x = -1 and x = n
+// as (n + 2) x (n + 2) arrays over (z, y); G = that size rounded up to 32 floats, so every block and
+// population starts on a 128-byte line.  Whole planes are contiguous, so a level of 8^3 or 16^3
+// blocks streams without the partly used lines a padded row pitch leaves (ncu: 3x and 2x DRAM
+// over-fetch on those levels with padded 128-byte-aligned rows).
+__host__ __device__ __forceinline__ int side_base(int n, int side) {  // side 0: x = -1, 1: x = n
+    return (n + 2) * (n + 2) * (n + side);
+}
+// offset of cell (x, y, z), -1 <= x, y, z <= n, within one population of a block
+__host__ __device__ __forceinline__ int cell_index(int n, int x, int y, int z) {
+    if (x < 0) return side_base(n, 0) + (z + 1) * (n + 2) + (y + 1);
+    if (x >= n) return side_base(n, 1) + (z + 1) * (n + 2) + (y + 1);
+    return ((z + 1) * (n + 2) + (y + 1)) * n + x;
+}
 
 struct InterpTask {
     int dst;
@@ -65,7 +77,7 @@ struct RestrictTask {
 
 struct Level {
     int n = 0, G = 0;      // cells per block edge, values per population per block (ghosted)
-    int P = 0, plane = 0;  // row pitch (XOFF + n + 1 rounded up to 8) and plane size P (n + 2)
+    int P = 0, plane = 0;  // row pitch (n) and plane size n (n + 2) of the interior rows
     double tau = 1.0;
     int nslot = 0;
     std::vector<int> slot;  // physical block -> slot or -1
@@ -187,8 +199,8 @@ __device__ __forceinline__ float step_cell(const float *__restrict__ in, const f
                                            const StepArgs &a, int x, int y, int z) {
     using L = D3Q19;
     const int n = NT ? NT : a.n;
-    const int G = a.G, row = a.P, plane = a.plane;
-    const int g = (z + 1) * plane + (y + 1) * row + XOFF + x;
+    const int G = a.G, row = n, plane = n * (n + 2);
+    const int g = (z + 1) * plane + (y + 1) * row + x;
     // a pull along +c leaves the block at the low face, along -c at the high face
     const bool xl = x == 0, xh = x == n - 1, yl = y == 0, yh = y == n - 1;
     const bool zl = z == 0, zh = z == n - 1;
@@ -206,9 +218,11 @@ __device__ __forceinline__ float step_cell(const float *__restrict__ in, const f
             const int nb = snb[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)];
             if (nb >= 0) {
                 v = in[(size_t)nb * Q * G + i * G + (z - cz - dz * n + 1) * plane +
-                       (y - cy - dy * n + 1) * row + XOFF + (x - cx - dx * n)];
+                       (y - cy - dy * n + 1) * row + (x - cx - dx * n)];
             } else if (nb == NB_GHOST) {
-                v = src[i * G + g - (cz * plane + cy * row + cx)];
+                // interpolated ghost: an x-ghost column, or a ghost row / plane of the block
+                v = src[i * G + (dx != 0 ? side_base(n, dx > 0) + (z - cz + 1) * (n + 2) + (y - cy + 1)
+                                         : g - (cz * plane + cy * row + cx))];
             } else {
                 v = src[L::opp(i) * G + g];
                 if (dy == 1 && top)
@@ -326,9 +340,7 @@ namespace {
         if (e_ != cudaSuccess) return report_cuda_error(e_, what); \
     } while (0)
 
-int gidx(const Level &L, int x, int y, int z) {
-    return (z + 1) * L.plane + (y + 1) * L.P + XOFF + x;
-}
+int gidx(const Level &L, int x, int y, int z) { return cell_index(L.n, x, y, z); }
 
 bool balanced(const Mesh &m) {
     for (int z = 0; z < m.nb[2]; ++z)
@@ -721,9 +733,9 @@ int build(Mesh **out, const int nb[3], int edge, int lmax, const int8_t *leaf, d
         Level &L = m->lv[l];
         const int h = 1 << (lmax - l);
         L.n = edge / h;
-        L.P = (XOFF + L.n + 1 + 7) / 8 * 8;
-        L.plane = L.P * (L.n + 2);
-        L.G = L.plane * (L.n + 2);
+        L.P = L.n;
+        L.plane = L.n * (L.n + 2);
+        L.G = ((L.n + 2) * (L.n + 2) * (L.n + 2) + 31) / 32 * 32;
         for (int a = 0; a < 3; ++a) L.cells[a] = nb[a] * L.n;
         L.tau = 3.0 * nu_fine / h + 0.5;
         if (lmax > 0 && fabs(L.tau - 1.0) < 1e-3) {
