@@ -94,6 +94,11 @@ struct Level {
     // thread, or (tiled) the brick kernel walking `zc` planes
     bool tiled = false;
     int threads = 256, cpt = 1, zc = 1;
+    // finest level only: its second sub-step also restricts onto the next coarser level (tiled
+    // brick kernel walking fuse_zc planes); the coarser level then skips k_restrict
+    bool fuse = false;
+    int fuse_zc = 2;
+    int *cslot = nullptr;  // device: per slot, the slot of the same block one level coarser
 };
 
 struct Mesh {
@@ -102,6 +107,7 @@ struct Mesh {
     double lid[3] = {0, 0, 0};
     int periodic = 0;
     Level lv[MAXL];
+    int fusion = 0;  // 0: timed choice, 1: separate restriction, 2: fused where possible
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // by level-0 buffer parity
     long long cycles = 0;
 };
@@ -192,11 +198,16 @@ struct StepArgs {
 };
 
 // One cell of a level step (pull, bounce-back at walls, moments, equilibrium, sensor, collision);
-// returns its sensor value.  src / dst: the block's slot in the two buffers.
-template <int NT>
+// returns its sensor value.  src / dst: the block's slot in the two buffers; also(i, v) sees every
+// stored post-collision population.
+struct NoVisit {
+    __device__ __forceinline__ void operator()(int, float) const {}
+};
+template <int NT, class Also = NoVisit>
 __device__ __forceinline__ float step_cell(const float *__restrict__ in, const float *src,
                                            float *dst, const int *snb, bool top,
-                                           const StepArgs &a, int x, int y, int z) {
+                                           const StepArgs &a, int x, int y, int z,
+                                           Also &&also = NoVisit()) {
     using L = D3Q19;
     const int n = NT ? NT : a.n;
     const int G = a.G, row = n, plane = n * (n + 2);
@@ -231,7 +242,11 @@ __device__ __forceinline__ float step_cell(const float *__restrict__ in, const f
         }
         df[i] = v - weight<L, float>(i);
     }
-    return relax_store_cell<L, 1, 1>(df, a.omega, dst, (size_t)G, g);
+    return relax_cell<L, 1, 1>(df, a.omega, [&](int i, float d) {
+        const float v = d + weight<L, float>(i);
+        dst[(size_t)i * G + g] = v;
+        also(i, v);
+    });
 }
 
 // warp max of the sensor bits, one atomic per warp (every lane of the warp must call this)
@@ -297,6 +312,79 @@ __global__ void __launch_bounds__(256, 4) k_step_tiled(const float *__restrict__
     for (int zz = threadIdx.z; zz < zc; zz += T::TZ) {
         const float K = step_cell<NT>(in, src, dst, snb, top, a, threadIdx.x, y, z0 + zz);
         km = max(km, __float_as_int(K));
+    }
+    block_max_flush(km, kmax, slot, tid & 31);
+}
+
+// Where the fused restriction writes: the coarser level's current buffer, the coarse slot of every
+// fine block, and the rescaling of the non-equilibrium part 2 (tau_c - 1) / (tau_f - 1).
+struct RestrictArgs {
+    float *coarse;
+    const int *cslot;
+    int Gc;
+    float scale;
+};
+
+// The tiled step of the finest level's second sub-step fused with the restriction onto the next
+// coarser level (NT = 16, 32, 64: bricks one plane deep; zc even).  Each 2 x 2 x 2 group of fine
+// cells is summed in a fixed order: x pairs by a lane shuffle, then the z pair in the owning
+// thread, then the y pair from shared memory; the coarse cell is the average with its f^neq
+// rescaled, as in k_restrict, so the restriction kernel and its re-read of the fine level are
+// skipped.
+template <int NT>
+__global__ void __launch_bounds__(256, 4)
+    k_step_tiled_restrict(const float *__restrict__ in, float *__restrict__ out,
+                          const int *__restrict__ nbr, const StepArgs a, int zc, float *kmax,
+                          const RestrictArgs r) {
+    using T = Tile<NT>;
+    static_assert(T::TZ == 1 && T::TY % 2 == 0, "one-plane bricks with row pairs");
+    constexpr int NC = NT / 2, CX = NT / 2, CY = T::TY / 2;
+    __shared__ int snb[27];
+    __shared__ float part[2][Q][CY][CX];  // [y parity][population][coarse row][coarse x]
+    const int slot = blockIdx.x;
+    const int tid = threadIdx.y * T::TX + threadIdx.x;
+    if (tid < 27) snb[tid] = nbr[27 * slot + tid];
+    __syncthreads();
+    const bool top = snb[NB_TOP] == NB_WALL;
+    const float *src = in + (size_t)slot * Q * a.G;
+    float *dst = out + (size_t)slot * Q * a.G;
+    constexpr int ytiles = NT / T::TY;
+    const int y = (blockIdx.y % ytiles) * T::TY + threadIdx.y;
+    const int z0 = (blockIdx.y / ytiles) * zc;
+    const int x = threadIdx.x;
+    const int ypar = threadIdx.y & 1, yc = threadIdx.y >> 1, xc = x >> 1;
+    const bool owner = (x & 1) == 0;
+    float *coarse = r.coarse + (size_t)r.cslot[slot] * Q * r.Gc;
+    int km = 0;
+    for (int zz = 0; zz < zc; ++zz) {
+        const bool second = zz & 1;
+        const float K = step_cell<NT>(in, src, dst, snb, top, a, x, y, z0 + zz, [&](int i, float v) {
+            const float pair = v + __shfl_xor_sync(0xffffffffu, v, 1);
+            if (owner) {
+                float &acc = part[ypar][i][yc][xc];
+                acc = second ? acc + pair : pair;
+            }
+        });
+        km = max(km, __float_as_int(K));
+        if (second) {
+            __syncthreads();
+            if (tid < CY * CX) {
+                const int cy = tid / CX, cx = tid % CX;
+                float avg[Q];
+#pragma unroll
+                for (int i = 0; i < Q; ++i) avg[i] = 0.125f * (part[0][i][cy][cx] + part[1][i][cy][cx]);
+                float rho, ux, uy, uz;
+                moments19(avg, rho, ux, uy, uz);
+                const int gx = cx, gy = (y - threadIdx.y) / 2 + cy, gz = (z0 + zz) / 2;
+                const int gc = ((gz + 1) * (NC + 2) + (gy + 1)) * NC + gx;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const float fe = feq19(i, rho, ux, uy, uz);
+                    coarse[i * r.Gc + gc] = fe + r.scale * (avg[i] - fe);
+                }
+            }
+            __syncthreads();
+        }
     }
     block_max_flush(km, kmax, slot, tid & 31);
 }
@@ -480,6 +568,13 @@ int build_tasks(Mesh &m, int l) {
     }
     int st = upload(&L.nbr, nbr);
     if (st != LBM_OK) return st;
+    if (l > 0) {  // the same physical block one level coarser (levels nest per block)
+        std::vector<int> cs(std::max(L.nslot, 1), 0);
+        for (int b = 0; b < m.nblk; ++b)
+            if (L.slot[b] >= 0) cs[L.slot[b]] = m.lv[l - 1].slot[b];
+        st = upload(&L.cslot, cs);
+        if (st != LBM_OK) return st;
+    }
     st = upload(&L.interps, interps);
     if (st != LBM_OK) return st;
     L.ninterp = (int)interps.size();
@@ -558,6 +653,37 @@ cudaError_t launch_step(const Mesh &m, int l, bool tiled, int threads, int cpt, 
     return cudaGetLastError();
 }
 
+template <int NT>
+cudaError_t launch_fused(const Mesh &m, int l, int zc, cudaStream_t s, int src) {
+    const Level &L = m.lv[l], &C = m.lv[l - 1];
+    using T = Tile<NT>;
+    RestrictArgs r;
+    r.coarse = C.buf[C.cur];
+    r.cslot = L.cslot;
+    r.Gc = C.G;
+    r.scale = (float)(2.0 * (C.tau - 1.0) / (L.tau - 1.0));
+    const dim3 block(T::TX, T::TY, T::TZ);
+    const dim3 grid(L.nslot, (NT / T::TY) * (NT / zc));
+    k_step_tiled_restrict<NT><<<grid, block, 0, s>>>(L.buf[src], L.buf[src ^ 1], L.nbr,
+                                                     step_args(m, l), zc, L.kmax, r);
+    return cudaGetLastError();
+}
+
+// The fused step + restriction of level l onto l - 1 (n = 16, 32 or 64; zc even, dividing n).
+cudaError_t launch_step_restrict(const Mesh &m, int l, int zc, cudaStream_t s, int src) {
+    switch (m.lv[l].n) {
+        case 16: return launch_fused<16>(m, l, zc, s, src);
+        case 32: return launch_fused<32>(m, l, zc, s, src);
+        case 64: return launch_fused<64>(m, l, zc, s, src);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+bool can_fuse(const Mesh &m, int l) {
+    const int n = m.lv[l].n;
+    return l == m.lmax && l > 0 && (n == 16 || n == 32 || n == 64) && m.lv[l - 1].nrestrict > 0;
+}
+
 int brick_depth(int n) {
     switch (n) {
         case 8: return Tile<8>::TZ;
@@ -589,14 +715,17 @@ int advance(Mesh &m, int l, float theta, cudaStream_t s) {
     }
     MLCK(cudaGetLastError(), "ghost fill");
     MLCK(cudaMemsetAsync(L.kmax, 0, sizeof(float) * L.nslot, s), "memset(kmax)");
-    MLCK(launch_step(m, l, L.tiled, L.threads, L.cpt, L.zc, s, L.cur), "level step");
+    if (L.fuse && theta > 0.f)  // the second sub-step of the finest level restricts as it steps
+        MLCK(launch_step_restrict(m, l, L.fuse_zc, s, L.cur), "level step + restriction");
+    else
+        MLCK(launch_step(m, l, L.tiled, L.threads, L.cpt, L.zc, s, L.cur), "level step");
     L.cur ^= 1;
     if (l < m.lmax) {
         int st = advance(m, l + 1, 0.f, s);
         if (st == LBM_OK) st = advance(m, l + 1, 0.5f, s);
         if (st != LBM_OK) return st;
         const Level &F = m.lv[l + 1];
-        if (L.nrestrict) {
+        if (L.nrestrict && !F.fuse) {
             const float scale = (float)(2.0 * (L.tau - 1.0) / (F.tau - 1.0));
             k_restrict<<<blocks_for(L.nrestrict, 128), 128, 0, s>>>(
                 L.restricts, L.nrestrict, L.buf[L.cur], L.G, F.buf[F.cur], F.P, F.plane, F.G,
@@ -649,6 +778,45 @@ int autotune(Mesh &m, int l, cudaStream_t s) {
             L.zc = c.zc;
         }
     }
+    // finest level: the fused step + restriction against the best step plus k_restrict (or as
+    // the mesh's fusion setting forces)
+    L.fuse = false;
+    if (can_fuse(m, l) && m.fusion == 2) {
+        L.fuse = true;
+        L.fuse_zc = 4;
+    } else if (can_fuse(m, l) && m.fusion == 0) {
+        Level &C = m.lv[l - 1];
+        const float scale = (float)(2.0 * (C.tau - 1.0) / (L.tau - 1.0));
+        for (int k = 0; k < 2; ++k)
+            MLCK(launch_step(m, l, L.tiled, L.threads, L.cpt, L.zc, s, L.cur), "autotune");
+        MLCK(cudaEventRecord(e0, s), "cudaEventRecord");
+        for (int k = 0; k < 3; ++k) {
+            MLCK(launch_step(m, l, L.tiled, L.threads, L.cpt, L.zc, s, L.cur), "autotune");
+            k_restrict<<<blocks_for(C.nrestrict, 128), 128, 0, s>>>(
+                C.restricts, C.nrestrict, C.buf[C.cur], C.G, L.buf[L.cur ^ 1], L.P, L.plane, L.G,
+                scale);
+        }
+        MLCK(cudaEventRecord(e1, s), "cudaEventRecord");
+        MLCK(cudaEventSynchronize(e1), "cudaEventSynchronize");
+        float separate = 0.f;
+        MLCK(cudaEventElapsedTime(&separate, e0, e1), "cudaEventElapsedTime");
+        for (int zc = 2; zc <= L.n; zc *= 2) {
+            for (int k = 0; k < 2; ++k)
+                MLCK(launch_step_restrict(m, l, zc, s, L.cur), "autotune");
+            MLCK(cudaEventRecord(e0, s), "cudaEventRecord");
+            for (int k = 0; k < 3; ++k)
+                MLCK(launch_step_restrict(m, l, zc, s, L.cur), "autotune");
+            MLCK(cudaEventRecord(e1, s), "cudaEventRecord");
+            MLCK(cudaEventSynchronize(e1), "cudaEventSynchronize");
+            float ms = 0.f;
+            MLCK(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+            if (ms < separate) {
+                separate = ms;
+                L.fuse = true;
+                L.fuse_zc = zc;
+            }
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return LBM_OK;
@@ -687,6 +855,7 @@ void destroy(Mesh *m) {
         cudaFree(L.buf[0]);
         cudaFree(L.buf[1]);
         cudaFree(L.nbr);
+        cudaFree(L.cslot);
         cudaFree(L.interps);
         cudaFree(L.restricts);
         cudaFree(L.kmax);
@@ -702,7 +871,7 @@ bool same_layout(const Mesh *m, const int nb[3], int edge, int lmax, const int8_
 }
 
 int build(Mesh **out, const int nb[3], int edge, int lmax, const int8_t *leaf, double tau_fine,
-          const double lid[3], int periodic, cudaStream_t s) {
+          const double lid[3], int periodic, int fusion, cudaStream_t s) {
     *out = nullptr;
     if (lmax < 0 || lmax >= MAXL) return report_error(LBM_EINVAL, "lmax must be 0, 1 or 2");
     if (edge < 1 || edge % (1 << lmax) != 0 || edge / (1 << lmax) < 2)
@@ -714,6 +883,7 @@ int build(Mesh **out, const int nb[3], int edge, int lmax, const int8_t *leaf, d
     for (int a = 0; a < 3; ++a) m->nb[a] = nb[a];
     m->edge = edge;
     m->lmax = lmax;
+    m->fusion = fusion;
     m->nblk = nb[0] * nb[1] * nb[2];
     m->leaf.assign(leaf, leaf + m->nblk);
     for (int a = 0; a < 3; ++a) m->lid[a] = lid[a];
@@ -882,6 +1052,15 @@ int info(const Mesh *m, int l, int *n, double *tau, int *nslot, int *threads, in
     if (nslot) *nslot = L.nslot;
     if (threads) *threads = L.threads;
     if (cpt) *cpt = L.cpt;
+    return LBM_OK;
+}
+
+int schedule(const Mesh *m, int l, int *tiled, int *planes, int *fused) {
+    if (l < 0 || l > m->lmax) return report_error(LBM_EINVAL, "no such level");
+    const Level &L = m->lv[l];
+    if (tiled) *tiled = L.tiled ? 1 : 0;
+    if (planes) *planes = L.tiled ? L.zc : 0;
+    if (fused) *fused = L.fuse ? L.fuse_zc : 0;
     return LBM_OK;
 }
 

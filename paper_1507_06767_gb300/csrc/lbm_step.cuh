@@ -137,12 +137,13 @@ __device__ __forceinline__ void gather_interior(const typename Storage<DT>::T *_
     }
 }
 
-// Moments, equilibrium, sensor and BGK collision of one cell from its gathered deviations df, and
-// the store of the post-collision populations at linear index idx.  Returns the sensor K (MODE != 0).
-template <class L, int DT, int MODE>
-__device__ __forceinline__ typename Storage<DT>::R relax_store_cell(
-    const typename Storage<DT>::R *df, typename Storage<DT>::R omega,
-    typename Storage<DT>::T *__restrict__ fout, size_t N, int idx) {
+// Moments, equilibrium, sensor and BGK collision of one cell from its gathered deviations df;
+// emit(i, d) receives the post-collision deviation d = f*_i - w_i of every population.  Returns
+// the sensor K (MODE != 0).
+template <class L, int DT, int MODE, class Emit>
+__device__ __forceinline__ typename Storage<DT>::R relax_cell(const typename Storage<DT>::R *df,
+                                                              typename Storage<DT>::R omega,
+                                                              Emit &&emit) {
     using S = Storage<DT>;
     using R = typename S::R;
     constexpr int Q = L::Q;
@@ -177,10 +178,22 @@ __device__ __forceinline__ typename Storage<DT>::R relax_store_cell(
                 ksum += fabs(fneq) / feq;
             }
         }
-        const R dnew = df[i] - omega * fneq;
-        store_pop(fout + (size_t)i * N + idx, S::from_r(S::SHIFTED ? dnew : dnew + w));
+        emit(i, df[i] - omega * fneq);
     }
     return ksum * (R(1) / R(Q));
+}
+
+// relax_cell with the store of the post-collision populations at linear index idx.
+template <class L, int DT, int MODE>
+__device__ __forceinline__ typename Storage<DT>::R relax_store_cell(
+    const typename Storage<DT>::R *df, typename Storage<DT>::R omega,
+    typename Storage<DT>::T *__restrict__ fout, size_t N, int idx) {
+    using S = Storage<DT>;
+    using R = typename S::R;
+    return relax_cell<L, DT, MODE>(df, omega, [&](int i, R dnew) {
+        store_pop(fout + (size_t)i * N + idx,
+                  S::from_r(S::SHIFTED ? dnew : dnew + weight<L, R>(i)));
+    });
 }
 
 // MODE 0: no sensor.  MODE 1: sensor and per-tile max.  MODE 2: MODE 1 plus per-cell K.

@@ -94,6 +94,9 @@ _SIGS = {
     "lbm_step_noalloc": (_i, [_i, _i, _i, _i, _i, _d, _d, _d, _i, _vp, _vp, _i, _vp, _vp]),
     "lbm_regrid": (_i, [_h, _vp, _vp, _vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_ll), _vp]),
     "lbm_block_features": (_i, [_h, _i, _vp]),
+    "lbm_blocks_set_fusion": (_i, [_h, _i]),
+    "lbm_blocks_schedule": (_i, [_h, _i, ctypes.POINTER(_i), ctypes.POINTER(_i),
+                                 ctypes.POINTER(_i)]),
     "lbm_net_create": (_vp, [_i, _i]),
     "lbm_net_destroy": (None, [_vp]),
     "lbm_net_set_stream": (_i, [_vp, _vp]),
@@ -335,6 +338,18 @@ def lbm_blocks_info(h, level: int):
     return n.value, tau.value, nb.value, th.value, cpt.value, cu.value
 
 
+def lbm_blocks_set_fusion(h, mode: int) -> int:
+    return _ck(_lib.lbm_blocks_set_fusion(h, int(mode)), "lbm_blocks_set_fusion")
+
+
+def lbm_blocks_schedule(h, level: int):
+    """(tiled, planes, fused planes) of a level's step schedule."""
+    t, p, f = _i(), _i(), _i()
+    _ck(_lib.lbm_blocks_schedule(h, int(level), ctypes.byref(t), ctypes.byref(p), ctypes.byref(f)),
+        "lbm_blocks_schedule")
+    return t.value, p.value, f.value
+
+
 class RegridParams(ctypes.Structure):
     """struct lbm_regrid_params of include/lbm.h."""
     _fields_ = [("coarsen", _i), ("threshold", _d), ("buffer", _i), ("allowed", ctypes.c_void_p),
@@ -512,7 +527,8 @@ class Net:
 class BlockMesh:
     """Multi-level block mesh on a handle: leaf[nbz, nby, nbx] leaf levels, block edge `edge`."""
 
-    def __init__(self, leaf, edge, lmax, tau_fine, lid=(0.0, 0.0), periodic=0, graphs=True):
+    def __init__(self, leaf, edge, lmax, tau_fine, lid=(0.0, 0.0), periodic=0, graphs=True,
+                 fusion=None):
         import torch  # noqa: F401  (the caller's CUDA context)
 
         self.leaf = np.ascontiguousarray(leaf, dtype=np.int8)
@@ -523,7 +539,12 @@ class BlockMesh:
         lbm_set_lid(self.h, float(lid[0]), float(lid[1]))
         lbm_set_periodic(self.h, int(periodic))
         lbm_set_graphs(self.h, 1 if graphs else 0)
+        if fusion is not None:
+            lbm_blocks_set_fusion(self.h, int(fusion))
         self.step(0)
+
+    def schedule(self, level):
+        return lbm_blocks_schedule(self.h, level)
 
     def _batch(self, cycles, out):
         return LevelBatch(self.nb[0], self.nb[1], self.nb[2], self.edge, self.lmax,
