@@ -309,6 +309,8 @@ def run_blocks(args, w, ws, rank, local):
                    "cells_per_level": [info[l][2] * info[l][0] ** 3 for l in range(w["lmax"] + 1)],
                    "tau_per_level": [round(info[l][1], 6) for l in range(w["lmax"] + 1)],
                    "step_launch_shape": [[info[l][3], info[l][4]] for l in range(w["lmax"] + 1)],
+                   "step_schedule": [dict(zip(("tiled", "planes", "fused_planes"),
+                                              mesh.schedule(l))) for l in range(w["lmax"] + 1)],
                    "cell_updates_per_cycle": updates, "n_eff": n_eff,
                    "uniform_finest_cells": w["n"] ** 3, "step": "one level-0 cycle (graph)",
                    "l2": "level buffers > 129 MB L2, no flush"},
