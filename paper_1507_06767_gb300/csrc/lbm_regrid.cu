@@ -61,6 +61,29 @@ __global__ void k_tag(const T *__restrict__ K, int nx, int ny, int nz, int r, in
     tags[t] = hit;
 }
 
+// The same for FP32 fields whose tag cells span whole groups of 4 cells along x (r % 4 == 0,
+// nx % 4 == 0): 16-byte loads, all of a row's loads issued before any test.
+__global__ void k_tag_f4(const float *__restrict__ K, int nx, int ny, int nz, int r, int rz,
+                         int tx, int ty, long long ntag, double thr, uint8_t *__restrict__ tags) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntag) return;
+    const int x = (int)(t % tx), y = (int)((t / tx) % ty), z = (int)(t / ((long long)tx * ty));
+    const int x0 = x * r, y0 = y * r, z0 = z * rz;
+    const int x1 = min(x0 + r, nx), y1 = min(y0 + r, ny), z1 = min(z0 + rz, nz);
+    int hit = 0;
+    for (int cz = z0; cz < z1; ++cz)
+        for (int cy = y0; cy < y1; ++cy) {
+            const float4 *row = reinterpret_cast<const float4 *>(K + ((size_t)cz * ny + cy) * nx);
+            for (int c4 = x0 / 4; c4 < x1 / 4; ++c4) {
+                const float4 v = __ldg(row + c4);
+                // NaN fails every comparison: !(v <= thr) is true for v > thr and for NaN
+                hit |= !((double)v.x <= thr) | !((double)v.y <= thr) | !((double)v.z <= thr) |
+                       !((double)v.w <= thr);
+            }
+        }
+    tags[t] = (uint8_t)(hit != 0);
+}
+
 // One 1-D pass along an axis of extent n and element stride `stride`: dilation (op 0: OR over the
 // segment, nothing beyond a non-periodic edge) or erosion (op 1: AND over the segment, covered
 // beyond a non-periodic edge).  Periodic axes wrap.
@@ -266,6 +289,9 @@ int regrid(const void *field, int field_type, int nx, int ny, int nz, int period
     if (field_type == LBM_F64)
         k_tag<double><<<nblk(ntag, 256), 256, 0, s>>>((const double *)field, nx, ny, nz, r, rz, tx,
                                                       ty, ntag, p.threshold, ta);
+    else if (r % 4 == 0 && nx % 4 == 0 && ((uintptr_t)field & 15) == 0)
+        k_tag_f4<<<nblk(ntag, 256), 256, 0, s>>>((const float *)field, nx, ny, nz, r, rz, tx, ty,
+                                                  ntag, p.threshold, ta);
     else
         k_tag<float><<<nblk(ntag, 256), 256, 0, s>>>((const float *)field, nx, ny, nz, r, rz, tx,
                                                      ty, ntag, p.threshold, ta);

@@ -152,3 +152,29 @@ def test_regrid_edge_cases(L):
         lat.regrid(0.5)
     assert ei.value.status == L.LBM_ESTATE
     lat.close()
+
+
+def test_regrid_from_an_fp32_cavity_sensor(L):
+    """End to end on an FP32 D3Q19 handle (the FP32 field's 16-byte tag pass, tag cells of 4^3):
+    the threshold sits in a gap of the oracle's tag-cell maxima wider than the FP32 sensor error
+    (1e-4 relative), so both sides tag the same cells and must build the same boxes."""
+    nx, ny, nz, steps = 32, 40, 24, 300
+    tau = O.tau_from_re(0.1, ny, 400.0)
+    o = O.Oracle(19, nx, ny, nz, tau, lid=(0.1, 0.0, 0.0))
+    _, Kref = o.run(o.rest(), steps, sensor_last=True)
+    m = Kref.reshape(nz // 4, 4, ny // 4, 4, nx // 4, 4).max(axis=(1, 3, 5)).ravel()
+    v = np.unique(m)
+    gaps = v[1:] / v[:-1] - 1.0
+    lo = int(0.6 * len(v))
+    k = lo + int(np.argmax(gaps[lo:int(0.9 * len(v))]))
+    assert gaps[k] > 2e-3
+    T = float(np.sqrt(v[k] * v[k + 1]))
+    lat = L.Lattice(L.LBM_D3Q19, nx, ny, nz, tau, dtype=L.LBM_F32, lid=(0.1, 0.0))
+    L.lbm_set_sensor_field(lat.h, 1)
+    L.lbm_set_sensor_every(lat.h, 1)
+    lat.step(steps)
+    ref_boxes, ref_tags = R.regrid(Kref, T, coarsen=4, buffer=1, min_width=2)
+    boxes, tags = lat.regrid(T, coarsen=4, buffer=1, min_width=2)
+    assert np.array_equal(tags, ref_tags)
+    assert boxes.tolist() == ref_boxes.tolist() and len(boxes) >= 1
+    lat.close()
