@@ -2,6 +2,8 @@
 // tile-to-block sensor maxima and the refine / coarsen flag builders.
 #include <math.h>
 
+#include <algorithm>
+
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -338,36 +340,39 @@ __global__ void k_levels_affine(const R *m, int n, double a, double b, int lmin,
         out[k] = level_of((double)m[k], a, b, lmin, lmax);
 }
 
-// Single CTA: fit a, b to the range of phi over the blocks with a finite K > 0, then map.
+// Fit a, b to the range of phi over the blocks with a finite K > 0, then map.  phi = log2 K is
+// monotone, so its range is log2 of the range of K: every CTA finds the extreme maxima itself
+// (a scan of all n values, no logarithms), takes two logarithms and maps its own share of the
+// blocks (one logarithm each; double precision runs at a small fraction of the FP32 rate on this
+// GPU, so the logarithms are spread over the whole grid).
 template <class R>
-__global__ void __launch_bounds__(1024) k_levels_fit(const R *m, int n, int lmin, int lmax,
-                                                     int8_t *out) {
-    __shared__ double slo[1024], shi[1024];
+__global__ void __launch_bounds__(256) k_levels_fit(const R *m, int n, int lmin, int lmax,
+                                                    int8_t *out) {
+    __shared__ double slo[256], shi[256];
     double lo = INFINITY, hi = -INFINITY;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
         const double v = (double)m[k];
         if (v > 0.0 && isfinite(v)) {
-            const double ph = log2(v);
-            lo = fmin(lo, ph);
-            hi = fmax(hi, ph);
+            lo = fmin(lo, v);
+            hi = fmax(hi, v);
         }
     }
     slo[threadIdx.x] = lo;
     shi[threadIdx.x] = hi;
     __syncthreads();
-    for (int st = 512; st > 0; st >>= 1) {
+    for (int st = 128; st > 0; st >>= 1) {
         if (threadIdx.x < st) {
             slo[threadIdx.x] = fmin(slo[threadIdx.x], slo[threadIdx.x + st]);
             shi[threadIdx.x] = fmax(shi[threadIdx.x], shi[threadIdx.x + st]);
         }
         __syncthreads();
     }
-    lo = slo[0];
-    hi = shi[0];
-    const bool scale = hi > lo;
-    const double a = scale ? (double)(lmax - lmin + 1) / (hi - lo) : 0.0;
-    const double b = scale ? (double)lmin - a * lo : 0.0;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const bool any = slo[0] <= shi[0];
+    const double plo = any ? log2(slo[0]) : 0.0, phi = any ? log2(shi[0]) : 0.0;
+    const bool scale = phi > plo;
+    const double a = scale ? (double)(lmax - lmin + 1) / (phi - plo) : 0.0;
+    const double b = scale ? (double)lmin - a * plo : 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const double v = (double)m[k];
         out[k] = scale ? level_of(v, a, b, lmin, lmax)
                        : (isnan(v) ? (int8_t)lmax : (int8_t)lmin);
@@ -542,12 +547,14 @@ cudaError_t levels_affine(int rtype, const void *maxima, int n, double a, double
 
 cudaError_t levels_fit(int rtype, const void *maxima, int n, int lmin, int lmax, int8_t *out,
                        cudaStream_t s) {
+    // each CTA scans all n values once: keep the grid to about one CTA per SM
+    const unsigned g = (unsigned)std::min<long long>(((long long)n + 255) / 256, 152);
     if (rtype == 0)
-        k_levels_fit<double><<<1, 1024, 0, s>>>(static_cast<const double *>(maxima), n, lmin, lmax,
-                                                out);
-    else
-        k_levels_fit<float><<<1, 1024, 0, s>>>(static_cast<const float *>(maxima), n, lmin, lmax,
+        k_levels_fit<double><<<g, 256, 0, s>>>(static_cast<const double *>(maxima), n, lmin, lmax,
                                                out);
+    else
+        k_levels_fit<float><<<g, 256, 0, s>>>(static_cast<const float *>(maxima), n, lmin, lmax,
+                                              out);
     return cudaGetLastError();
 }
 
