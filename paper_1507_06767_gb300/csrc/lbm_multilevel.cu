@@ -93,6 +93,7 @@ struct Level {
     // step launch shape (autotuned): flat kernel with `threads` per CTA and `cpt` cells per
     // thread, or (tiled) the brick kernel walking `zc` planes
     bool tiled = false;
+    bool xsel = false;  // flat kernel with the address-select gather (XSEL)
     int threads = 256, cpt = 1, zc = 1;
     // finest level only: its second sub-step also restricts onto the next coarser level (tiled
     // brick kernel walking fuse_zc planes); the coarser level then skips k_restrict
@@ -203,7 +204,11 @@ struct StepArgs {
 struct NoVisit {
     __device__ __forceinline__ void operator()(int, float) const {}
 };
-template <int NT, class Also = NoVisit>
+// XSEL: cells whose y and z neighbours lie inside the block (whole rows for 32-cell rows, so
+// the branch is warp-uniform) take a gather where a pull along x that leaves the block selects its
+// address (x-neighbour block, interpolated x-ghost column or the wall's bounce-back) instead of
+// branching on it, so the two face lanes of a row do not split the warp.
+template <int NT, bool XSEL = false, class Also = NoVisit>
 __device__ __forceinline__ float step_cell(const float *__restrict__ in, const float *src,
                                            float *dst, const int *snb, bool top,
                                            const StepArgs &a, int x, int y, int z,
@@ -216,6 +221,31 @@ __device__ __forceinline__ float step_cell(const float *__restrict__ in, const f
     const bool xl = x == 0, xh = x == n - 1, yl = y == 0, yh = y == n - 1;
     const bool zl = z == 0, zh = z == n - 1;
     float df[Q];
+    if (XSEL && !(yl | yh | zl | zh)) {
+        const int nbm = snb[12], nbp = snb[14];  // the x - 1 and x + 1 neighbours
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+            const int off = cz * plane + cy * row + cx;
+            const float *p = src + (size_t)i * G + (g - off);
+            if (cx != 0) {
+                const int nb = cx == 1 ? nbm : nbp;
+                const float *q =
+                    nb >= 0 ? in + (size_t)nb * Q * G + (size_t)i * G + (g - off + cx * n)
+                    : nb == NB_GHOST
+                        ? src + (size_t)i * G +
+                              (side_base(n, cx < 0) + (z - cz + 1) * (n + 2) + (y - cy + 1))
+                        : src + (size_t)L::opp(i) * G + g;
+                p = (cx == 1 ? xl : xh) ? q : p;
+            }
+            df[i] = *p - weight<L, float>(i);
+        }
+        return relax_cell<L, 1, 1>(df, a.omega, [&](int i, float d) {
+            const float v = d + weight<L, float>(i);
+            dst[(size_t)i * G + g] = v;
+            also(i, v);
+        });
+    }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
@@ -259,7 +289,7 @@ __device__ __forceinline__ void block_max_flush(int km, float *kmax, int slot, i
 // Flat mapping: grid (slot, chunk), cells of a block in x-fastest order, each thread `cpt` cells.
 // NT is the block edge when it is one of the compiled sizes (shifts instead of divisions), 0
 // otherwise.
-template <int NT>
+template <int NT, bool XSEL = false>
 __global__ void k_step(const float *__restrict__ in, float *__restrict__ out,
                        const int *__restrict__ nbr, const StepArgs a, int cpt, float *kmax) {
     __shared__ int snb[27];
@@ -275,7 +305,8 @@ __global__ void k_step(const float *__restrict__ in, float *__restrict__ out,
     for (int r = 0; r < cpt; ++r) {
         const int c = (blockIdx.y * cpt + r) * blockDim.x + threadIdx.x;
         if (c >= ncell) break;
-        const float K = step_cell<NT>(in, src, dst, snb, top, a, c % n, (c / n) % n, c / (n * n));
+        const float K =
+            step_cell<NT, XSEL>(in, src, dst, snb, top, a, c % n, (c / n) % n, c / (n * n));
         km = max(km, __float_as_int(K));
     }
     block_max_flush(km, kmax, slot, threadIdx.x & 31);
@@ -625,7 +656,7 @@ cudaError_t launch_tiled(const Level &L, const StepArgs &a, int zc, cudaStream_t
 // tiled: zc planes per CTA (a multiple of the brick depth dividing n); else flat with
 // threads x cpt cells per CTA
 cudaError_t launch_step(const Mesh &m, int l, bool tiled, int threads, int cpt, int zc,
-                        cudaStream_t s, int src) {
+                        cudaStream_t s, int src, bool xsel = false) {
     const Level &L = m.lv[l];
     const StepArgs a = step_args(m, l);
     if (tiled) {
@@ -642,6 +673,15 @@ cudaError_t launch_step(const Mesh &m, int l, bool tiled, int threads, int cpt, 
     dim3 grid(L.nslot, chunks);
     const float *fin = L.buf[src];
     float *fout = L.buf[src ^ 1];
+    if (xsel) {
+        switch (L.n) {
+            case 16: k_step<16, true><<<grid, threads, 0, s>>>(fin, fout, L.nbr, a, cpt, L.kmax); break;
+            case 32: k_step<32, true><<<grid, threads, 0, s>>>(fin, fout, L.nbr, a, cpt, L.kmax); break;
+            case 64: k_step<64, true><<<grid, threads, 0, s>>>(fin, fout, L.nbr, a, cpt, L.kmax); break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     switch (L.n) {
         case 4: k_step<4><<<grid, threads, 0, s>>>(fin, fout, L.nbr, a, cpt, L.kmax); break;
         case 8: k_step<8><<<grid, threads, 0, s>>>(fin, fout, L.nbr, a, cpt, L.kmax); break;
@@ -718,7 +758,7 @@ int advance(Mesh &m, int l, float theta, cudaStream_t s) {
     if (L.fuse && theta > 0.f)  // the second sub-step of the finest level restricts as it steps
         MLCK(launch_step_restrict(m, l, L.fuse_zc, s, L.cur), "level step + restriction");
     else
-        MLCK(launch_step(m, l, L.tiled, L.threads, L.cpt, L.zc, s, L.cur), "level step");
+        MLCK(launch_step(m, l, L.tiled, L.threads, L.cpt, L.zc, s, L.cur, L.xsel), "level step");
     L.cur ^= 1;
     if (l < m.lmax) {
         int st = advance(m, l + 1, 0.f, s);
@@ -747,25 +787,28 @@ int autotune(Mesh &m, int l, cudaStream_t s) {
     struct Cand {
         bool tiled;
         int threads, cpt, zc;
+        bool xsel;
     };
     std::vector<Cand> cand;
     const int flat[][2] = {{128, 1}, {128, 2}, {256, 1}, {256, 2}, {256, 4}, {512, 1}, {512, 2}};
-    for (const auto &c : flat)
-        if (c[0] * c[1] <= 2 * ncell || (c[0] == 128 && c[1] == 1))
-            cand.push_back({false, c[0], c[1], 1});
+    const bool xsel_ok = L.n == 16 || L.n == 32 || L.n == 64;
+    for (int xs = 0; xs <= (xsel_ok ? 1 : 0); ++xs)
+        for (const auto &c : flat)
+            if (c[0] * c[1] <= 2 * ncell || (c[0] == 128 && c[1] == 1))
+                cand.push_back({false, c[0], c[1], 1, xs == 1});
     if (has_tiled(L.n))
         for (int zc = brick_depth(L.n); zc <= L.n; zc *= 2)
-            cand.push_back({true, 256, zc / brick_depth(L.n), zc});
+            cand.push_back({true, 256, zc / brick_depth(L.n), zc, false});
     cudaEvent_t e0, e1;
     MLCK(cudaEventCreate(&e0), "cudaEventCreate");
     MLCK(cudaEventCreate(&e1), "cudaEventCreate");
     float best = 1e30f;
     for (const Cand &c : cand) {
         for (int k = 0; k < 2; ++k)
-            MLCK(launch_step(m, l, c.tiled, c.threads, c.cpt, c.zc, s, L.cur), "autotune");
+            MLCK(launch_step(m, l, c.tiled, c.threads, c.cpt, c.zc, s, L.cur, c.xsel), "autotune");
         MLCK(cudaEventRecord(e0, s), "cudaEventRecord");
         for (int k = 0; k < 3; ++k)
-            MLCK(launch_step(m, l, c.tiled, c.threads, c.cpt, c.zc, s, L.cur), "autotune");
+            MLCK(launch_step(m, l, c.tiled, c.threads, c.cpt, c.zc, s, L.cur, c.xsel), "autotune");
         MLCK(cudaEventRecord(e1, s), "cudaEventRecord");
         MLCK(cudaEventSynchronize(e1), "cudaEventSynchronize");
         float ms = 0.f;
@@ -776,6 +819,7 @@ int autotune(Mesh &m, int l, cudaStream_t s) {
             L.threads = c.threads;
             L.cpt = c.cpt;
             L.zc = c.zc;
+            L.xsel = c.xsel;
         }
     }
     // finest level: the fused step + restriction against the best step plus k_restrict (or as
@@ -788,10 +832,10 @@ int autotune(Mesh &m, int l, cudaStream_t s) {
         Level &C = m.lv[l - 1];
         const float scale = (float)(2.0 * (C.tau - 1.0) / (L.tau - 1.0));
         for (int k = 0; k < 2; ++k)
-            MLCK(launch_step(m, l, L.tiled, L.threads, L.cpt, L.zc, s, L.cur), "autotune");
+            MLCK(launch_step(m, l, L.tiled, L.threads, L.cpt, L.zc, s, L.cur, L.xsel), "autotune");
         MLCK(cudaEventRecord(e0, s), "cudaEventRecord");
         for (int k = 0; k < 3; ++k) {
-            MLCK(launch_step(m, l, L.tiled, L.threads, L.cpt, L.zc, s, L.cur), "autotune");
+            MLCK(launch_step(m, l, L.tiled, L.threads, L.cpt, L.zc, s, L.cur, L.xsel), "autotune");
             k_restrict<<<blocks_for(C.nrestrict, 128), 128, 0, s>>>(
                 C.restricts, C.nrestrict, C.buf[C.cur], C.G, L.buf[L.cur ^ 1], L.P, L.plane, L.G,
                 scale);
@@ -1058,7 +1102,7 @@ int info(const Mesh *m, int l, int *n, double *tau, int *nslot, int *threads, in
 int schedule(const Mesh *m, int l, int *tiled, int *planes, int *fused) {
     if (l < 0 || l > m->lmax) return report_error(LBM_EINVAL, "no such level");
     const Level &L = m->lv[l];
-    if (tiled) *tiled = L.tiled ? 1 : 0;
+    if (tiled) *tiled = L.tiled ? 1 : (L.xsel ? 2 : 0);
     if (planes) *planes = L.tiled ? L.zc : 0;
     if (fused) *fused = L.fuse ? L.fuse_zc : 0;
     return LBM_OK;
