@@ -350,11 +350,10 @@ LBM_API int lbm_blocks_set(lbm_t *h, int level, int block, const double *in_host
 LBM_API int lbm_blocks_info(lbm_t *h, int level, int *n, double *tau, int *nblocks, int *threads,
                             int *cells_per_thread, long long *cell_updates_per_cycle);
 /* Restriction onto the next coarser level after the finest level's two sub-steps: a separate
- * kernel (LBM_FUSION_SEPARATE), fused into the finest level's second sub-step
- * (LBM_FUSION_FUSED, where that level's blocks have 16, 32 or 64 cells per edge; the same
- * average and f^neq rescaling, summed in another order), or whichever the build measures faster
- * (LBM_FUSION_AUTO, the default).  Applies from the next mesh build: an existing mesh is
- * discarded. */
+ * kernel (LBM_FUSION_SEPARATE, and LBM_FUSION_AUTO, the default: the fused form measured slower on
+ * the benchmark mesh) or fused into the finest level's second sub-step (LBM_FUSION_FUSED, where
+ * that level's blocks have 16, 32 or 64 cells per edge; the same average and f^neq rescaling,
+ * summed in another order).  Applies from the next mesh build: an existing mesh is discarded. */
 #define LBM_FUSION_AUTO 0
 #define LBM_FUSION_SEPARATE 1
 #define LBM_FUSION_FUSED 2

@@ -108,7 +108,7 @@ struct Mesh {
     double lid[3] = {0, 0, 0};
     int periodic = 0;
     Level lv[MAXL];
-    int fusion = 0;  // 0: timed choice, 1: separate restriction, 2: fused where possible
+    int fusion = 0;  // 0, 1: separate restriction, 2: fused where possible
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // by level-0 buffer parity
     long long cycles = 0;
 };
@@ -822,44 +822,13 @@ int autotune(Mesh &m, int l, cudaStream_t s) {
             L.xsel = c.xsel;
         }
     }
-    // finest level: the fused step + restriction against the best step plus k_restrict (or as
-    // the mesh's fusion setting forces)
+    // finest level: the restriction stays a separate kernel unless the mesh's fusion setting
+    // forces the fused step + restriction (measured slower on the benchmark mesh: 3.45 against
+    // 2.65 ms per cycle)
     L.fuse = false;
     if (can_fuse(m, l) && m.fusion == 2) {
         L.fuse = true;
         L.fuse_zc = 4;
-    } else if (can_fuse(m, l) && m.fusion == 0) {
-        Level &C = m.lv[l - 1];
-        const float scale = (float)(2.0 * (C.tau - 1.0) / (L.tau - 1.0));
-        for (int k = 0; k < 2; ++k)
-            MLCK(launch_step(m, l, L.tiled, L.threads, L.cpt, L.zc, s, L.cur, L.xsel), "autotune");
-        MLCK(cudaEventRecord(e0, s), "cudaEventRecord");
-        for (int k = 0; k < 3; ++k) {
-            MLCK(launch_step(m, l, L.tiled, L.threads, L.cpt, L.zc, s, L.cur, L.xsel), "autotune");
-            k_restrict<<<blocks_for(C.nrestrict, 128), 128, 0, s>>>(
-                C.restricts, C.nrestrict, C.buf[C.cur], C.G, L.buf[L.cur ^ 1], L.P, L.plane, L.G,
-                scale);
-        }
-        MLCK(cudaEventRecord(e1, s), "cudaEventRecord");
-        MLCK(cudaEventSynchronize(e1), "cudaEventSynchronize");
-        float separate = 0.f;
-        MLCK(cudaEventElapsedTime(&separate, e0, e1), "cudaEventElapsedTime");
-        for (int zc = 2; zc <= L.n; zc *= 2) {
-            for (int k = 0; k < 2; ++k)
-                MLCK(launch_step_restrict(m, l, zc, s, L.cur), "autotune");
-            MLCK(cudaEventRecord(e0, s), "cudaEventRecord");
-            for (int k = 0; k < 3; ++k)
-                MLCK(launch_step_restrict(m, l, zc, s, L.cur), "autotune");
-            MLCK(cudaEventRecord(e1, s), "cudaEventRecord");
-            MLCK(cudaEventSynchronize(e1), "cudaEventSynchronize");
-            float ms = 0.f;
-            MLCK(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
-            if (ms < separate) {
-                separate = ms;
-                L.fuse = true;
-                L.fuse_zc = zc;
-            }
-        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

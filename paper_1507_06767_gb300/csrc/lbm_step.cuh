@@ -46,6 +46,10 @@ constexpr int TILE = 8;
 #ifndef LBM_INTERIOR_FAST
 #define LBM_INTERIOR_FAST 1
 #endif
+// 1: rows inside in y and z but at an x face take gather_xsel (address selects, no branches)
+#ifndef LBM_XSEL_PATH
+#define LBM_XSEL_PATH 1
+#endif
 
 template <class T>
 __device__ __forceinline__ T load_pop(const T *p) {
@@ -132,6 +136,34 @@ __device__ __forceinline__ void gather_interior(const typename Storage<DT>::T *_
         const long long off =
             (long long)i * (long long)N - (long long)(L::cz(i) * plane + L::cy(i) * nx + L::cx(i));
         R v = S::to_r(load_pop(base + off));
+        if (!S::SHIFTED) v -= weight<L, R>(i);
+        df[i] = v;
+    }
+}
+
+// Pull-gather of a cell whose y and z sources lie inside the lattice: as gather_interior, except
+// that a pull along x that leaves the lattice (x = 0 pulling along +x, x = nx - 1 along -x)
+// selects its address instead of branching: the wrapped cell on a periodic x axis, else the
+// cell's own opposite population (bounce-back at a resting wall; the lid is a y wall).
+template <class L, int DT>
+__device__ __forceinline__ void gather_xsel(const typename Storage<DT>::T *__restrict__ fin,
+                                            size_t N, int nx, int plane, size_t idx, int x,
+                                            bool perx, typename Storage<DT>::R *df) {
+    using S = Storage<DT>;
+    using R = typename S::R;
+    const typename S::T *base = fin + idx;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        const int cx = L::cx(i);
+        const long long off =
+            (long long)i * (long long)N - (long long)(L::cz(i) * plane + L::cy(i) * nx + cx);
+        const typename S::T *src = base + off;
+        if (cx != 0) {
+            const bool face = cx == 1 ? x == 0 : x == nx - 1;
+            const typename S::T *alt = perx ? src + cx * nx : fin + (size_t)L::opp(i) * N + idx;
+            src = face ? alt : src;
+        }
+        R v = S::to_r(load_pop(src));
         if (!S::SHIFTED) v -= weight<L, R>(i);
         df[i] = v;
     }
@@ -241,9 +273,11 @@ __global__ void __launch_bounds__(CTA_X *CTA_Y, LBM_STEP_MIN_BLOCKS)
         if (active) {
             const int idx = (z * ny + y) * nx + x;
             R df[Q];
-            // (a third path for rows that touch only an x face measured slower: spills)
-            if (LBM_INTERIOR_FAST && inner_x && inner_y && (L::D == 2 || (z >= 1 && z <= nz - 2)))
+            const bool inner_yz = inner_y && (L::D == 2 || (z >= 1 && z <= nz - 2));
+            if (LBM_INTERIOR_FAST && inner_yz && inner_x)
                 gather_interior<L, DT>(fin, N, nx, nx * ny, (size_t)idx, df);
+            else if (LBM_XSEL_PATH && inner_yz)
+                gather_xsel<L, DT>(fin, N, nx, nx * ny, (size_t)idx, x, p.periodic & 1, df);
             else
                 gather_cell<L, DT>(fin, p, N, x, y, z, df);
             const R K = relax_store_cell<L, DT, MODE>(df, omega, fout, N, idx);
