@@ -24,16 +24,20 @@ constexpr int CTA_Y = 8;
 constexpr int TILE = 8;
 
 // Tuning knobs (compile-time): resident CTAs per SM requested from the register allocator (one-cell
-// kernel: 4 -> at most 64 registers, 1024 threads per SM; the two-cell kernel: 4 as well, measured
-// at 512^3 FP16 2.81 ms against 2.85 ms with 3 and 3.25 ms with 2, despite its spills), and
-// cache hints of the population loads / stores (0: default,
-// 1: read-only path / streaming store, 2: evict-first load).  Measured on GB300 at 256^3 D3Q19 FP32:
-// without a minimum the allocator takes 140 registers and the one-cell kernel runs at half speed.
+// kernel: 4 -> at most 64 registers, 1024 threads per SM; the two-cell kernel with 16-bit storage:
+// 4, no spills, measured at 512^3 FP16 1.91 ms against 2.00 ms with 3; with FP32 storage: 3 -> at
+// most 80 registers, no spills, 3.03 ms against 3.15 ms with 4), and cache hints of the population
+// loads / stores (0: default, 1: read-only path / streaming store, 2: evict-first load).  Measured
+// on GB300 at 256^3 D3Q19 FP32: without a minimum the allocator takes 140 registers and the
+// one-cell kernel runs at half speed.
 #ifndef LBM_STEP_MIN_BLOCKS
 #define LBM_STEP_MIN_BLOCKS 4
 #endif
 #ifndef LBM_PAIR_MIN_BLOCKS
 #define LBM_PAIR_MIN_BLOCKS 4
+#endif
+#ifndef LBM_PAIR_MIN_BLOCKS_F32
+#define LBM_PAIR_MIN_BLOCKS_F32 3
 #endif
 #ifndef LBM_LOAD_HINT
 #define LBM_LOAD_HINT 1

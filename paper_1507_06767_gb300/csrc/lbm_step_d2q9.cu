@@ -9,7 +9,7 @@ cudaError_t step_d2q9(int dtype, const void *fin, void *fout, const StepParams &
                       void *tile_max, void *k_field, cudaStream_t s, int variant) {
     // automatic choice, from GB300 measurements at 256^3 / 512^3: the one-cell kernel for FP32
     // and FP64, the two-cell packed kernel for 16-bit storage
-    const bool pair_ok = dtype != 0 && (p.nx % 2 == 0);
+    const bool pair_ok = dtype != 0 && pair_applicable<D2Q9>(p);
     const bool pair = pair_ok && (variant == KERNEL_PAIR || (variant == KERNEL_AUTO && dtype >= 2));
     if ((variant == KERNEL_PAIR && !pair_ok) || variant == KERNEL_TMA) return cudaErrorInvalidValue;
     switch (dtype) {

@@ -100,14 +100,15 @@ cudaError_t launch_fused_step_tma(const void *fin, void *fout, const StepParams 
 
 cudaError_t step_d3q19(int dtype, const void *fin, void *fout, const StepParams &p, int mode,
                        void *tile_max, void *k_field, cudaStream_t s, int variant) {
-    // automatic choice, from GB300 measurements at 256^3 / 512^3: the one-cell kernel for FP32
-    // and FP64, the two-cell packed kernel for 16-bit storage
-    const bool pair_ok = dtype != 0 && (p.nx % 2 == 0);
-    // with 16-bit storage the two-cell kernel wins on large lattices (512^3: 2.81 against 2.94 ms
-    // for the one-cell kernel) and loses on smaller ones (256^3: 0.407 against 0.389 ms)
-    const bool big = (long long)p.nx * p.ny * p.nz >= AUTO_PAIR_MIN_CELLS;
+    // automatic choice, from GB300 measurements (sensor steps, D3Q19 cavity): with 16-bit storage
+    // the two-cell kernel at every size measured (128^3 0.046 against 0.064 ms, 256^3 0.249
+    // against 0.367 ms, 512^3 1.91 against 2.83 ms); with FP32 storage the two-cell kernel on
+    // lattices of at least 2^24 cells (256^3 0.388 against 0.398 ms, 512^3 3.03 against 3.11 ms)
+    // and the one-cell kernel below (128^3 0.061 against 0.065 ms); FP64: the one-cell kernel
+    const bool pair_ok = dtype != 0 && pair_applicable<D3Q19>(p);
+    const bool big = (long long)p.nx * p.ny * p.nz >= AUTO_PAIR_MIN_CELLS_F32;
     const bool pair = pair_ok && (variant == KERNEL_PAIR ||
-                                  (variant == KERNEL_AUTO && dtype >= 2 && big));
+                                  (variant == KERNEL_AUTO && (dtype >= 2 || big)));
     const bool tma = tma_applicable(dtype, p.nx) && variant == KERNEL_TMA;
     if ((variant == KERNEL_PAIR && !pair_ok) || (variant == KERNEL_TMA && !tma))
         return cudaErrorInvalidValue;

@@ -3,14 +3,23 @@
 // Same computation as fused_step_kernel (lbm_step.cuh): pull-stream with moving-wall bounce-back
 // (Sec. 2.2 streaming, Sec. 4.1 lid), moments (Eqs. rho, u), equilibrium (Eq. feq_i), Knudsen
 // sensor (Eq. sensor / kkn) with per-tile max, BGK collision (Sec. 2.2).  Differences, all for
-// instruction economy (the one-cell kernel issues ~800 instructions per cell and is bound by issue
-// rate, not by HBM):
+// instruction economy (the one-cell kernel issues ~725 instructions per cell, most of them integer
+// address work; with 16-bit storage it is bound by issue rate, not by HBM):
 //   * each thread owns the cells (x0, x0 + 1), x0 even, so every population is loaded and stored
 //     as one aligned pair (8 bytes in FP32, 4 bytes in FP16/BF16) for the directions with c_x = 0,
-//     and as two scalar loads for c_x = +-1; the address arithmetic is shared by the two cells;
+//     and as two scalar loads for c_x = +-1;
+//   * addresses are a per-thread pointer plus a 32-bit per-direction element offset (one
+//     wide multiply-add each), which needs (q + 1) * cells < 2^32 (checked by the caller);
+//   * 16-bit populations stay packed in one 32-bit register per direction until they are used,
+//     and are widened twice (moments, then relaxation) instead of holding 2q floats;
 //   * the arithmetic of both cells runs in packed FP32 pairs (FFMA2 / FADD2 / FMUL2 of sm_100+);
+//     signed sums are split into positive and negative parts, so no operand needs a negation;
 //   * a warp whose cells are all at least one cell away from every wall takes a path without the
-//     wall tests (warp-uniform vote); the general path is the per-cell one of the scalar kernel.
+//     wall tests (warp-uniform vote), a row inside in y and z one whose x-face lanes select their
+//     source address; the general path takes the two cells one after the other through the
+//     one-cell kernel's gather and relaxation;
+//   * the sensor uses the approximate reciprocal (relative error ~1 ulp) of the one-cell kernel's
+//     approximate division.
 // Needs nx even; odd nx uses the one-cell kernel.
 #pragma once
 
@@ -20,92 +29,168 @@ namespace lbm {
 
 constexpr int PAIR_CTA_CELLS_X = 2 * CTA_X;  // 64 cells along x per CTA
 
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// The populations of the two cells of one direction as held in registers between the gather and
+// the relaxation (PairReg<DT>::V), how they are loaded, widened to FP32 and stored.
+//   FP32 storage: a float2.  FP16 / BF16 shifted storage: the two 16-bit values in one 32-bit word
+//   (low half: cell x0).  widen_a and widen_b compute the same value; they are written as distinct
+//   inline PTX so that the compiler keeps the packed word, not two floats, alive in between.
 template <int DT>
-struct PairIO;
+struct PairReg;
 template <>
-struct PairIO<1> {  // float pair
-    __device__ static float2 load2(const float *p) {
-        return load_pop(reinterpret_cast<const float2 *>(p));
+struct PairReg<1> {
+    using V = float2;
+    __device__ static V load2(const float *p) { return load_pop(reinterpret_cast<const float2 *>(p)); }
+    __device__ static V load_split(const float *a, const float *b) {
+        return make_float2(load_pop(a), load_pop(b));
     }
+    __device__ static float2 widen_a(V v) { return v; }
+    __device__ static float2 widen_b(V v) { return v; }
     __device__ static void store2(float *p, float2 v) { store_pop(reinterpret_cast<float2 *>(p), v); }
 };
 template <>
-struct PairIO<2> {  // half pair, shifted storage
-    __device__ static float2 load2(const __half *p) {
-        return __half22float2(load_pop(reinterpret_cast<const __half2 *>(p)));
+struct PairReg<2> {
+    using V = unsigned;
+    __device__ static V load2(const __half *p) {
+        return load_pop(reinterpret_cast<const unsigned *>(p));
+    }
+    __device__ static V load_split(const __half *a, const __half *b) {
+        const unsigned lo = load_pop(reinterpret_cast<const unsigned short *>(a));
+        const unsigned hi = load_pop(reinterpret_cast<const unsigned short *>(b));
+        return __byte_perm(lo, hi, 0x5410);
+    }
+    __device__ static float2 widen_a(V v) {
+        float a, b;
+        asm("{.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\tcvt.f32.f16 %0, l;\n\tcvt.f32.f16 %1, h;}"
+            : "=f"(a), "=f"(b) : "r"(v));
+        return make_float2(a, b);
+    }
+    __device__ static float2 widen_b(V v) {
+        float a, b;
+        asm("{.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\tcvt.f32.f16 %1, h;\n\tcvt.f32.f16 %0, l;}"
+            : "=f"(a), "=f"(b) : "r"(v));
+        return make_float2(a, b);
     }
     __device__ static void store2(__half *p, float2 v) {
         store_pop(reinterpret_cast<__half2 *>(p), __float22half2_rn(v));
     }
 };
 template <>
-struct PairIO<3> {  // bfloat16 pair, shifted storage
-    __device__ static float2 load2(const __nv_bfloat16 *p) {
-        return __bfloat1622float2(load_pop(reinterpret_cast<const __nv_bfloat162 *>(p)));
+struct PairReg<3> {
+    using V = unsigned;
+    __device__ static V load2(const __nv_bfloat16 *p) {
+        return load_pop(reinterpret_cast<const unsigned *>(p));
+    }
+    __device__ static V load_split(const __nv_bfloat16 *a, const __nv_bfloat16 *b) {
+        const unsigned lo = load_pop(reinterpret_cast<const unsigned short *>(a));
+        const unsigned hi = load_pop(reinterpret_cast<const unsigned short *>(b));
+        return __byte_perm(lo, hi, 0x5410);
+    }
+    // a BF16 value is the high half of the FP32 value with the same bits
+    __device__ static float2 widen_a(V v) {
+        unsigned a, b;
+        asm("shl.b32 %0, %2, 16;\n\tand.b32 %1, %2, 0xffff0000;" : "=r"(a), "=r"(b) : "r"(v));
+        return make_float2(__uint_as_float(a), __uint_as_float(b));
+    }
+    __device__ static float2 widen_b(V v) {
+        unsigned a, b;
+        asm("and.b32 %1, %2, 0xffff0000;\n\tshl.b32 %0, %2, 16;" : "=r"(a), "=r"(b) : "r"(v));
+        return make_float2(__uint_as_float(a), __uint_as_float(b));
     }
     __device__ static void store2(__nv_bfloat16 *p, float2 v) {
         store_pop(reinterpret_cast<__nv_bfloat162 *>(p), __float22bfloat162_rn(v));
     }
 };
 
-__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+// Approximate FP32 reciprocal (PTX rcp.approx, max relative error about 1 ulp; inputs here are
+// equilibrium populations, far from zero and from the subnormal range).
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Component of velocity i along axis a (0 x, 1 y, 2 z).
+template <class L>
+__host__ __device__ constexpr int comp(int a, int i) {
+    return a == 0 ? L::cx(i) : a == 1 ? L::cy(i) : L::cz(i);
+}
+// First direction (lowest index) whose component along axis a equals s.
+template <class L>
+__host__ __device__ constexpr int first_dir(int a, int s) {
+    for (int i = 1; i < L::Q; ++i)
+        if (comp<L>(a, i) == s) return i;
+    return -1;
+}
+// First axis along which velocity i has a non-zero component (-1 for the rest velocity).
+template <class L>
+__host__ __device__ constexpr int lead_axis(int i) {
+    return L::cx(i) ? 0 : L::cy(i) ? 1 : L::cz(i) ? 2 : -1;
+}
 
 // Moments, equilibrium, Knudsen sensor and BGK collision of two cells at once in packed FP32
-// pairs (FFMA2 / FADD2 / FMUL2 of sm_100+), from their gathered deviations df_i = f_i - w_i.
-// Calls store(i, v) with the post-collision value of direction i in the storage convention of DT
-// (f* for plain storage, f* - w_i for shifted storage) and returns the two sensors (MODE != 0).
-template <class L, int DT, int MODE, class Store>
-__device__ __forceinline__ float2 relax_pair(const float2 *df, float omega_s, Store &&store) {
+// pairs, from their deviations df_i = f_i - w_i: moments(i) and relax(i) return df_i (the same
+// value; see PairReg).  Calls store(i, v) with the post-collision value of direction i in the
+// storage convention of DT (f* for plain storage, f* - w_i for shifted storage) and returns the
+// two sensors (MODE != 0).
+template <class L, int DT, int MODE, class Get1, class Get2, class Store>
+__device__ __forceinline__ float2 relax_pair(Get1 &&moments, Get2 &&relax, float omega_s,
+                                             Store &&store) {
     using S = Storage<DT>;
     constexpr int Q = L::Q;
-    const float2 one = f2(1.f);
-    float2 drho = df[0], jx = f2(0.f), jy = f2(0.f), jz = f2(0.f);
-#pragma unroll
-    for (int i = 1; i < Q; ++i) drho = __fadd2_rn(drho, df[i]);
+    // rho - 1 and the positive / negative parts of rho u along each axis
+    float2 drho = moments(0);
+    float2 jp[3], jn[3];
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-        if (L::cx(i) == 1) jx = __fadd2_rn(jx, df[i]);
-        if (L::cx(i) == -1) jx = __fadd2_rn(jx, make_float2(-df[i].x, -df[i].y));
-        if (L::cy(i) == 1) jy = __fadd2_rn(jy, df[i]);
-        if (L::cy(i) == -1) jy = __fadd2_rn(jy, make_float2(-df[i].x, -df[i].y));
-        if (L::cz(i) == 1) jz = __fadd2_rn(jz, df[i]);
-        if (L::cz(i) == -1) jz = __fadd2_rn(jz, make_float2(-df[i].x, -df[i].y));
+        const float2 v = moments(i);
+        drho = __fadd2_rn(drho, v);
+#pragma unroll
+        for (int a = 0; a < L::D; ++a) {
+            if (comp<L>(a, i) == 1) jp[a] = (i == first_dir<L>(a, 1)) ? v : __fadd2_rn(jp[a], v);
+            if (comp<L>(a, i) == -1) jn[a] = (i == first_dir<L>(a, -1)) ? v : __fadd2_rn(jn[a], v);
+        }
     }
-    const float2 rho = __fadd2_rn(one, drho);
+    const float2 rho = __fadd2_rn(f2(1.f), drho);
     const float2 inv_rho = make_float2(__frcp_rn(rho.x), __frcp_rn(rho.y));
-    const float2 ux = __fmul2_rn(jx, inv_rho), uy = __fmul2_rn(jy, inv_rho),
-                 uz = __fmul2_rn(jz, inv_rho);
-    float2 usq = __fmul2_rn(ux, ux);
-    usq = __ffma2_rn(uy, uy, usq);
-    if (L::D == 3) usq = __ffma2_rn(uz, uz, usq);
+    float2 u[3];
+#pragma unroll
+    for (int a = 0; a < L::D; ++a) u[a] = __fmul2_rn(__ffma2_rn(jn[a], f2(-1.f), jp[a]), inv_rho);
+    float2 usq = __fmul2_rn(u[0], u[0]);
+#pragma unroll
+    for (int a = 1; a < L::D; ++a) usq = __ffma2_rn(u[a], u[a], usq);
     const float2 neg_usq15 = __fmul2_rn(f2(-1.5f), usq);
     const float2 neg_omega = f2(-omega_s);
 
     float2 ksum = f2(0.f);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-        // c.u with the constant components folded
-        float2 cu = f2(0.f);
-        if (cx == 1) cu = ux;
-        if (cx == -1) cu = make_float2(-ux.x, -ux.y);
-        if (cy != 0) cu = (cx == 0) ? (cy == 1 ? uy : make_float2(-uy.x, -uy.y))
-                                    : __ffma2_rn(f2((float)cy), uy, cu);
-        if (cz != 0) cu = (cx == 0 && cy == 0) ? (cz == 1 ? uz : make_float2(-uz.x, -uz.y))
-                                               : __ffma2_rn(f2((float)cz), uz, cu);
-        // P = c.u/cs2 + ((c.u)^2 - cs2 u.u)/(2 cs2^2) = cu (3 + 4.5 cu) - 1.5 u.u
-        const float2 t = __ffma2_rn(f2(4.5f), cu, f2(3.f));
-        const float2 P = __ffma2_rn(cu, t, neg_usq15);
-        const float w = weight<L, float>(i);
-        const float2 A = __ffma2_rn(rho, P, drho);       // (f^eq_i - w_i) / w_i
-        const float2 fneq = __ffma2_rn(f2(-w), A, df[i]);  // f_i - f^eq_i
-        if (MODE != 0) {
-            const float2 feqw = __ffma2_rn(rho, P, rho);   // f^eq_i / w_i
-            const float2 r = make_float2(fabsf(fneq.x) * __frcp_rn(feqw.x),
-                                         fabsf(fneq.y) * __frcp_rn(feqw.y));
-            ksum = __ffma2_rn(r, f2(1.f / w), ksum);
+        // c.u = s g with s the sign of the first non-zero component and g = u_a + (c_a c_b) u_b,
+        // shared by i and its opposite; P = c.u/cs2 + ((c.u)^2 - cs2 u.u)/(2 cs2^2)
+        //   = g (3 s + 4.5 g) - 1.5 u.u
+        float2 P = neg_usq15;
+        if (i != 0) {
+            const int a = lead_axis<L>(i);
+            const int s = comp<L>(a, i);
+            float2 g = u[a];
+#pragma unroll
+            for (int b = a + 1; b < L::D; ++b)
+                if (comp<L>(b, i) != 0)
+                    g = (s * comp<L>(b, i) == 1) ? __fadd2_rn(g, u[b]) : __ffma2_rn(u[b], f2(-1.f), g);
+            P = __ffma2_rn(g, __ffma2_rn(f2(4.5f), g, f2(3.f * s)), neg_usq15);
         }
-        float2 v = __ffma2_rn(neg_omega, fneq, df[i]);
+        const float w = weight<L, float>(i);
+        const float2 d = relax(i);
+        const float2 A = __ffma2_rn(rho, P, drho);  // (f^eq_i - w_i) / w_i
+        const float2 fneq = __ffma2_rn(f2(-w), A, d);  // f_i - f^eq_i
+        if (MODE != 0) {
+            // f^eq_i = w_i rho (1 + P) = w_i (A + 1)
+            const float2 feq = __ffma2_rn(f2(w), A, f2(w));
+            ksum.x = fmaf(fabsf(fneq.x), rcp_approx(feq.x), ksum.x);
+            ksum.y = fmaf(fabsf(fneq.y), rcp_approx(feq.y), ksum.y);
+        }
+        float2 v = __ffma2_rn(neg_omega, fneq, d);
         if (!S::SHIFTED) v = __fadd2_rn(v, f2(w));
         store(i, v);
     }
@@ -113,12 +198,14 @@ __device__ __forceinline__ float2 relax_pair(const float2 *df, float omega_s, St
 }
 
 template <class L, int DT, int MODE>
-__global__ void __launch_bounds__(CTA_X *CTA_Y, LBM_PAIR_MIN_BLOCKS)
+__global__ void __launch_bounds__(CTA_X *CTA_Y, DT == 1 ? LBM_PAIR_MIN_BLOCKS_F32 : LBM_PAIR_MIN_BLOCKS)
     fused_step_pair_kernel(const typename Storage<DT>::T *__restrict__ fin,
                            typename Storage<DT>::T *__restrict__ fout, const StepParams p,
                            float *__restrict__ tile_max, float *__restrict__ k_field) {
     using S = Storage<DT>;
     using T = typename S::T;
+    using RG = PairReg<DT>;
+    using V = typename RG::V;
     constexpr int Q = L::Q;
     constexpr int ZT = (L::D == 3) ? TILE : 1;
 
@@ -128,8 +215,9 @@ __global__ void __launch_bounds__(CTA_X *CTA_Y, LBM_PAIR_MIN_BLOCKS)
     const int z0 = blockIdx.z * ZT;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const bool active = (x0 < nx) && (y < ny);
-    const size_t N = (size_t)nx * ny * nz;
-    const size_t nxy = (size_t)nx * ny;
+    // element offsets fit in 32 bits: (q + 1) * cells < 2^32
+    const unsigned N = (unsigned)nx * (unsigned)ny * (unsigned)nz;
+    const unsigned nxy = (unsigned)nx * (unsigned)ny;
 
     int kmax = 0;
 
@@ -145,40 +233,73 @@ __global__ void __launch_bounds__(CTA_X *CTA_Y, LBM_PAIR_MIN_BLOCKS)
     for (int dz = 0; dz < ZT; ++dz) {
         const int z = z0 + dz;
         if (z >= nz) break;
-        const bool interior = (x0 > 0) && (x0 + 2 < nx) && (y > 0) && (y < ny - 1) &&
-                              (L::D == 2 || ((z > 0) && (z < nz - 1)));
+        // y and z are warp-uniform (a warp is one row); x0 is not
+        const bool inner_yz = (y > 0) && (y < ny - 1) && (L::D == 2 || ((z > 0) && (z < nz - 1)));
+        const bool interior = inner_yz && (x0 > 0) && (x0 + 2 < nx);
         const bool fast = __all_sync(0xffffffffu, !active || interior);
         if (!active) continue;
-        const int idx0 = (z * ny + y) * nx + x0;
+        const unsigned idx0 = ((unsigned)z * ny + y) * nx + x0;
+        const T *B = fin + idx0;
+        T *C = fout + idx0;
+        const auto store = [&](int i, float2 v) { RG::store2(C + (unsigned)i * N, v); };
 
-        float2 df[Q];
-        if (fast) {
+        float2 K;
+        if (fast || (LBM_XSEL_PATH && inner_yz)) {
+            // rows inside in y and z: only a pull along x can leave the lattice, at x0 = 0 (cell
+            // x0 along +x) or x0 + 2 = nx (cell x0 + 1 along -x); there the source address is
+            // selected: the wrapped cell on a periodic x axis, else the cell's own opposite
+            // population (bounce-back at a resting wall)
+            V raw[Q];
+            if (fast) {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-                const T *base = fin + (size_t)i * N + (size_t)idx0 -
-                                (ptrdiff_t)((ptrdiff_t)cz * (ptrdiff_t)nxy + (ptrdiff_t)cy * nx);
-                float2 v;
-                if (cx == 0) {
-                    v = PairIO<DT>::load2(base);
-                } else if (cx == 1) {
-                    v = make_float2(S::to_r(load_pop(base - 1)), S::to_r(load_pop(base)));
-                } else {
-                    v = make_float2(S::to_r(load_pop(base + 1)), S::to_r(load_pop(base + 2)));
+                for (int i = 0; i < Q; ++i) {
+                    const int cx = L::cx(i);
+                    const T *src = B + ((unsigned)i * N - (unsigned)(L::cz(i) * (int)nxy +
+                                                                     L::cy(i) * nx));
+                    raw[i] = cx == 0 ? RG::load2(src)
+                                     : RG::load_split(src - cx, src + 1 - cx);
                 }
-                if (!S::SHIFTED) v = __fadd2_rn(v, f2(-weight<L, float>(i)));
-                df[i] = v;
+            } else {
+                const bool lo_face = x0 == 0, hi_face = x0 + 2 == nx;
+                const bool perx = p.periodic & 1;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const int cx = L::cx(i);
+                    const T *src = B + ((unsigned)i * N - (unsigned)(L::cz(i) * (int)nxy +
+                                                                     L::cy(i) * nx));
+                    if (cx == 0) {
+                        raw[i] = RG::load2(src);
+                    } else if (cx == 1) {
+                        const T *a = src - 1;
+                        const T *alt = perx ? a + nx : B + (unsigned)L::opp(i) * N;
+                        raw[i] = RG::load_split(lo_face ? alt : a, src);
+                    } else {
+                        const T *b = src + 2;
+                        const T *alt = perx ? b - nx : B + ((unsigned)L::opp(i) * N + 1u);
+                        raw[i] = RG::load_split(src + 1, hi_face ? alt : b);
+                    }
+                }
             }
+            if constexpr (!S::SHIFTED) {
+                // plain storage holds f_i: the relaxation works on f_i - w_i
+#pragma unroll
+                for (int i = 0; i < Q; ++i) raw[i] = __fadd2_rn(raw[i], f2(-weight<L, float>(i)));
+            }
+            K = relax_pair<L, DT, MODE>([&](int i) { return RG::widen_a(raw[i]); },
+                                        [&](int i) { return RG::widen_b(raw[i]); }, p.omega_f,
+                                        store);
         } else {
-            // each cell of the pair straight into its lane of df (no staging array)
-            gather_cell<L, DT, 2>(fin, p, N, x0, y, z, reinterpret_cast<float *>(df));
-            gather_cell<L, DT, 2>(fin, p, N, x0 + 1, y, z, reinterpret_cast<float *>(df) + 1);
+            // one cell after the other, with the one-cell kernel's gather and relaxation (fewer
+            // live registers than a pair of gathered cells)
+            float kc[2];
+#pragma unroll 1
+            for (int c = 0; c < 2; ++c) {
+                float df[Q];
+                gather_cell<L, DT>(fin, p, N, x0 + c, y, z, df);
+                kc[c] = relax_store_cell<L, DT, MODE>(df, p.omega_f, fout, N, idx0 + c);
+            }
+            K = make_float2(kc[0], kc[1]);
         }
-
-        T *out0 = fout + idx0;
-        const float2 K = relax_pair<L, DT, MODE>(df, p.omega_f, [&](int i, float2 v) {
-            PairIO<DT>::store2(out0 + (size_t)i * N, v);
-        });
         if (MODE != 0) {
             const int kb = max(__float_as_int(K.x), __float_as_int(K.y));
             kmax = kb > kmax ? kb : kmax;
@@ -213,10 +334,18 @@ __global__ void __launch_bounds__(CTA_X *CTA_Y, LBM_PAIR_MIN_BLOCKS)
     }
 }
 
+// The two-cell kernel applies to an even nx and (q + 1) * cells < 2^32 (32-bit element offsets).
+template <class L>
+inline bool pair_applicable(const StepParams &p) {
+    const unsigned long long cells = (unsigned long long)p.nx * p.ny * p.nz;
+    return p.nx % 2 == 0 && (unsigned long long)(L::Q + 1) * cells < (1ULL << 32);
+}
+
 template <class L, int DT>
 cudaError_t launch_fused_step_pair(const void *fin, void *fout, const StepParams &p, int mode,
                                    void *tile_max, void *k_field, cudaStream_t stream) {
     using T = typename Storage<DT>::T;
+    if (!pair_applicable<L>(p)) return cudaErrorInvalidValue;
     const int zt = (L::D == 3) ? TILE : 1;
     dim3 block(CTA_X, CTA_Y, 1);
     dim3 grid((p.nx + PAIR_CTA_CELLS_X - 1) / PAIR_CTA_CELLS_X, (p.ny + CTA_Y - 1) / CTA_Y,
