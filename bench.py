@@ -274,7 +274,8 @@ def run_blocks(args, w, ws, rank, local):
     torch.cuda.set_device(local)
     leaf = block_placement(w, L)
     tau = tau_of(w)
-    mesh = L.BlockMesh(leaf, w["block"], w["lmax"], tau, lid=(w["u"], 0.0))
+    form = getattr(L, "LBM_STEP_FORM_" + args.step_form.upper())
+    mesh = L.BlockMesh(leaf, w["block"], w["lmax"], tau, lid=(w["u"], 0.0), step_form=form)
     info = [mesh.info(l) for l in range(w["lmax"] + 1)]
     updates = info[0][5]  # cell updates per cycle over all levels
     for _ in range(args.warmup):
@@ -318,7 +319,7 @@ def run_blocks(args, w, ws, rank, local):
                    "cells_per_level": [info[l][2] * info[l][0] ** 3 for l in range(w["lmax"] + 1)],
                    "tau_per_level": [round(info[l][1], 6) for l in range(w["lmax"] + 1)],
                    "step_launch_shape": [[info[l][3], info[l][4]] for l in range(w["lmax"] + 1)],
-                   "step_schedule": [dict(zip(("tiled", "planes", "fused_planes"),
+                   "step_schedule": [dict(zip(("form", "planes", "fused_planes"),
                                               mesh.schedule(l))) for l in range(w["lmax"] + 1)],
                    "cell_updates_per_cycle": updates, "n_eff": n_eff,
                    "uniform_finest_cells": w["n"] ** 3, "step": "one level-0 cycle (graph)",
@@ -787,6 +788,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel", default="auto", choices=["auto", "cell", "pair", "tma"],
                     help="fused step kernel (default: the library's automatic choice)")
+    ap.add_argument("--step-form", default="auto",
+                    choices=["auto", "flat", "tiled", "select", "pair"],
+                    help="multi-level workload: force one form of the level step kernel on the "
+                         "levels it applies to (default: timed per level at mesh build)")
     ap.add_argument("--edge", type=int, default=None,
                     help="run the workload on a lattice of this edge instead (small profiling "
                          "captures); the JSON line then names the edge in its config")

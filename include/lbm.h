@@ -346,8 +346,8 @@ LBM_API int lbm_blocks_step(lbm_t *h, const lbm_level_batch *batch);
 LBM_API int lbm_blocks_get(lbm_t *h, int level, int block, double *out_host);
 LBM_API int lbm_blocks_set(lbm_t *h, int level, int block, const double *in_host);
 /* Level facts: cells per block edge, tau, blocks at the level, the step kernel's threads per CTA
- * and cells per thread, and the cell updates of one cycle over all levels (any pointer may be
- * NULL). */
+ * and cells (cell pairs for the two-cell form) per thread, and the cell updates of one cycle over
+ * all levels (any pointer may be NULL). */
 LBM_API int lbm_blocks_info(lbm_t *h, int level, int *n, double *tau, int *nblocks, int *threads,
                             int *cells_per_thread, long long *cell_updates_per_cycle);
 /* Restriction onto the next coarser level after the finest level's two sub-steps: a separate
@@ -359,10 +359,26 @@ LBM_API int lbm_blocks_info(lbm_t *h, int level, int *n, double *tau, int *nbloc
 #define LBM_FUSION_SEPARATE 1
 #define LBM_FUSION_FUSED 2
 LBM_API int lbm_blocks_set_fusion(lbm_t *h, int mode);
-/* The schedule picked for a level: the step kernel's mapping (tiled 1: bricks of whole rows
- * walking `planes` planes; 0: flat) and, for the finest level, the planes of the fused
- * step + restriction kernel (0: not fused).  Any pointer may be NULL; LBM_ESTATE without a mesh. */
-LBM_API int lbm_blocks_schedule(lbm_t *h, int level, int *tiled, int *planes, int *fused);
+/* Form of every level's step kernel: LBM_STEP_FORM_AUTO (default) times the candidate forms and
+ * launch shapes of each level when the mesh is built and keeps the fastest; the others force one
+ * form on every level whose block edge it applies to (the remaining levels stay timed):
+ * LBM_STEP_FORM_FLAT one cell per thread in x-fastest order (any edge), LBM_STEP_FORM_TILED bricks
+ * of whole rows walking z planes (edges 8, 16, 32, 64), LBM_STEP_FORM_SELECT flat with an
+ * address-select gather for the rows inside the block in y and z (16, 32, 64),
+ * LBM_STEP_FORM_PAIR two x-adjacent cells per thread with packed FP32 arithmetic (8, 16, 32, 64).
+ * All compute the same step; they differ in rounding order only.  Applies from the next mesh
+ * build: an existing mesh is discarded. */
+#define LBM_STEP_FORM_AUTO 0
+#define LBM_STEP_FORM_FLAT 1
+#define LBM_STEP_FORM_TILED 2
+#define LBM_STEP_FORM_SELECT 3
+#define LBM_STEP_FORM_PAIR 4
+LBM_API int lbm_blocks_set_step_form(lbm_t *h, int form);
+/* The schedule picked for a level: the step kernel's form (0 flat, 1 tiled, 2 flat with the
+ * address-select gather, 3 two cells per thread: LBM_STEP_FORM_* minus one), the planes a tiled
+ * CTA walks (0 otherwise) and, for the finest level, the planes of the fused step + restriction
+ * kernel (0: not fused).  Any pointer may be NULL; LBM_ESTATE without a mesh. */
+LBM_API int lbm_blocks_schedule(lbm_t *h, int level, int *form, int *planes, int *fused);
 
 /*
  * Regridding of one refinement level from the sensor (Sec. 5.2: cells flagged by the sensor, one

@@ -112,6 +112,7 @@ struct lbm_s {
     // multi-level block mesh of lbm_blocks_step (built on first use)
     lbm::ml::Mesh *mesh = nullptr;
     int blocks_fusion = 0;  // LBM_FUSION_* for the next mesh build
+    int blocks_step_form = 0;  // LBM_STEP_FORM_* for the next mesh build
 
     // graph cache: runs of RUN_LEN[k] plain steps (k = 0: 2 steps, 1: 16 steps), by starting
     // buffer
@@ -981,7 +982,8 @@ LBM_API int lbm_blocks_step(lbm_t *h, const lbm_level_batch *batch) {
     if (!h->mesh) {
         const double lid[3] = {h->lid_x, 0.0, h->lid_z};
         int st = lbm::ml::build(&h->mesh, nb, batch->edge, batch->lmax, batch->leaf, h->tau, lid,
-                                h->periodic, h->blocks_fusion, h->stream);
+                                h->periodic, h->blocks_fusion, h->blocks_step_form - 1,
+                                h->stream);
         if (st != LBM_OK) return st;
     }
     int st = lbm::ml::run_cycles(h->mesh, batch->cycles, h->stream, h->graphs != 0);
@@ -1039,10 +1041,23 @@ LBM_API int lbm_blocks_set_fusion(lbm_t *h, int mode) {
     return LBM_OK;
 }
 
-LBM_API int lbm_blocks_schedule(lbm_t *h, int level, int *tiled, int *planes, int *fused) {
+LBM_API int lbm_blocks_set_step_form(lbm_t *h, int form) {
+    CHECK_H(h);
+    if (form < LBM_STEP_FORM_AUTO || form > LBM_STEP_FORM_PAIR)
+        return fail(LBM_EINVAL, "step form must be one of LBM_STEP_FORM_*");
+    if (h->mesh) {  // applies to the next build
+        CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+        lbm::ml::destroy(h->mesh);
+        h->mesh = nullptr;
+    }
+    h->blocks_step_form = form;
+    return LBM_OK;
+}
+
+LBM_API int lbm_blocks_schedule(lbm_t *h, int level, int *form, int *planes, int *fused) {
     CHECK_H(h);
     if (!h->mesh) return fail(LBM_ESTATE, "no multi-level mesh (call lbm_blocks_step first)");
-    return lbm::ml::schedule(h->mesh, level, tiled, planes, fused);
+    return lbm::ml::schedule(h->mesh, level, form, planes, fused);
 }
 
 LBM_API int lbm_regrid(lbm_t *h, const double *field_dev, const lbm_regrid_params *p,

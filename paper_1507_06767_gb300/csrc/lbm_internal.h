@@ -68,9 +68,11 @@ cudaError_t scale_f64(const double *in, double factor, double *out, size_t n, cu
 // Multi-level block mesh (lbm_multilevel.cu).
 namespace ml {
 struct Mesh;
-// fusion: 0 automatic (timed), 1 separate restriction, 2 fused into the finest level's step
+// fusion: 0 automatic (separate), 1 separate restriction, 2 fused into the finest level's step;
+// step_form: -1 autotuned, else the step kernel form forced where it applies (LBM_STEP_FORM_*
+// minus one)
 int build(Mesh **out, const int nb[3], int edge, int lmax, const int8_t *leaf, double tau_fine,
-          const double lid[3], int periodic, int fusion, cudaStream_t s);
+          const double lid[3], int periodic, int fusion, int step_form, cudaStream_t s);
 void destroy(Mesh *m);
 bool same_layout(const Mesh *m, const int nb[3], int edge, int lmax, const int8_t *leaf);
 int run_cycles(Mesh *m, int cycles, cudaStream_t s, bool graphs);
@@ -78,7 +80,7 @@ int block_max(Mesh *m, double *out_host, cudaStream_t s);
 int get_block(Mesh *m, int l, int b, double *out, cudaStream_t s);
 int set_block(Mesh *m, int l, int b, const double *in, cudaStream_t s);
 int info(const Mesh *m, int l, int *n, double *tau, int *nslot, int *threads, int *cpt);
-int schedule(const Mesh *m, int l, int *tiled, int *planes, int *fused);
+int schedule(const Mesh *m, int l, int *form, int *planes, int *fused);
 long long cells_per_cycle(const Mesh *m);
 }  // namespace ml
 

@@ -37,7 +37,7 @@
 
 #include "../../include/lbm.h"
 #include "lbm_internal.h"
-#include "lbm_step.cuh"
+#include "lbm_step_pair.cuh"
 
 namespace lbm {
 namespace ml {
@@ -65,6 +65,12 @@ __host__ __device__ __forceinline__ int cell_index(int n, int x, int y, int z) {
     return ((z + 1) * (n + 2) + (y + 1)) * n + x;
 }
 
+// Forms of a level's step kernel (also the values lbm_blocks_schedule reports):
+constexpr int FORM_FLAT = 0;    // k_step: one cell per thread, x-fastest
+constexpr int FORM_TILED = 1;   // k_step_tiled: bricks of whole rows walking z planes
+constexpr int FORM_SELECT = 2;  // k_step<XSEL>: flat, address-select gather for y/z-inner rows
+constexpr int FORM_PAIR = 3;    // k_step_pair: two cells per thread, packed FP32 arithmetic
+
 struct InterpTask {
     int dst;
     int src[8];
@@ -90,10 +96,9 @@ struct Level {
     RestrictTask *restricts = nullptr;  // level cells under level + 1
     int nrestrict = 0;
     float *kmax = nullptr;  // device: per-slot sensor max of the level's last step (int bits)
-    // step launch shape (autotuned): flat kernel with `threads` per CTA and `cpt` cells per
-    // thread, or (tiled) the brick kernel walking `zc` planes
-    bool tiled = false;
-    bool xsel = false;  // flat kernel with the address-select gather (XSEL)
+    // step launch shape (autotuned): the form (FORM_*), `threads` per CTA and `cpt` cells (pairs
+    // for FORM_PAIR) per thread of the flat kernels, `zc` planes of the tiled one
+    int form = 0;
     int threads = 256, cpt = 1, zc = 1;
     // finest level only: its second sub-step also restricts onto the next coarser level (tiled
     // brick kernel walking fuse_zc planes); the coarser level then skips k_restrict
@@ -109,6 +114,7 @@ struct Mesh {
     int periodic = 0;
     Level lv[MAXL];
     int fusion = 0;  // 0, 1: separate restriction, 2: fused where possible
+    int step_form = -1;  // FORM_* forced on every level where it applies, -1: autotuned
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // by level-0 buffer parity
     long long cycles = 0;
 };
@@ -345,6 +351,78 @@ __global__ void __launch_bounds__(256, 4) k_step_tiled(const float *__restrict__
         km = max(km, __float_as_int(K));
     }
     block_max_flush(km, kmax, slot, tid & 31);
+}
+
+// Two x-adjacent cells per thread (x0 even) for NT = 8, 16, 32, 64: the moments, equilibrium,
+// sensor and collision of both cells in packed FP32 pairs (relax_pair of the uniform two-cell
+// kernel), 8-byte loads and stores for the directions with c_x = 0.  Rows inside the block in y
+// and z take the address-select gather (a face lane pulling along x reads the x-neighbour block,
+// the interpolated x-ghost column or its own opposite population at a wall); rows on a y or z
+// face take the per-cell gather of step_cell.  Flat mapping: grid (slot, chunk), `cpt` pairs per
+// thread in x-fastest order.
+template <int NT>
+__global__ void __launch_bounds__(256, 3) k_step_pair(const float *__restrict__ in,
+                                                   float *__restrict__ out,
+                                                   const int *__restrict__ nbr, const StepArgs a,
+                                                   int cpt, float *kmax) {
+    using L = D3Q19;
+    __shared__ int snb[27];
+    const int slot = blockIdx.x;
+    if (threadIdx.x < 27) snb[threadIdx.x] = nbr[27 * slot + threadIdx.x];
+    __syncthreads();
+    constexpr int n = NT, half = NT / 2, npair = NT * NT * NT / 2;
+    constexpr int row = n, plane = n * (n + 2);
+    const bool top = snb[NB_TOP] == NB_WALL;
+    const int G = a.G;
+    const float *src = in + (size_t)slot * Q * G;
+    float *dst = out + (size_t)slot * Q * G;
+    const int nbm = snb[12], nbp = snb[14];  // the x - 1 and x + 1 neighbours
+    int km = 0;
+    for (int r = 0; r < cpt; ++r) {
+        const int pidx = (blockIdx.y * cpt + r) * blockDim.x + threadIdx.x;
+        if (pidx >= npair) break;
+        const int x0 = 2 * (pidx % half), y = (pidx / half) % n, z = pidx / (half * n);
+        if (y == 0 || y == n - 1 || z == 0 || z == n - 1) {
+            const float K0 = step_cell<NT>(in, src, dst, snb, top, a, x0, y, z);
+            const float K1 = step_cell<NT>(in, src, dst, snb, top, a, x0 + 1, y, z);
+            km = max(km, max(__float_as_int(K0), __float_as_int(K1)));
+            continue;
+        }
+        const int g = (z + 1) * plane + (y + 1) * row + x0;
+        const bool lo = x0 == 0, hi = x0 + 2 == n;
+        float2 df[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+            const int off = cz * plane + cy * row;
+            const float *base = src + (i * G + g - off);
+            float2 v;
+            if (cx == 0) {
+                v = *reinterpret_cast<const float2 *>(base);
+            } else {
+                const int ghost = (z - cz + 1) * (n + 2) + (y - cy + 1);
+                if (cx == 1) {  // cell x0 pulls from x0 - 1, cell x0 + 1 from x0
+                    const float *alt = nbm >= 0 ? in + ((size_t)nbm * Q * G + (i * G + g - off - 1 + n))
+                                       : nbm == NB_GHOST ? src + (i * G + side_base(n, 0) + ghost)
+                                                         : src + (L::opp(i) * G + g);
+                    v = make_float2(*(lo ? alt : base - 1), *base);
+                } else {  // cell x0 pulls from x0 + 1, cell x0 + 1 from x0 + 2
+                    const float *alt = nbp >= 0 ? in + ((size_t)nbp * Q * G + (i * G + g - off + 2 - n))
+                                       : nbp == NB_GHOST ? src + (i * G + side_base(n, 1) + ghost)
+                                                         : src + (L::opp(i) * G + g + 1);
+                    v = make_float2(base[1], *(hi ? alt : base + 2));
+                }
+            }
+            df[i] = __fadd2_rn(v, f2(-weight<L, float>(i)));
+        }
+        const float2 K = relax_pair<L, 1, 1>([&](int i) { return df[i]; },
+                                             [&](int i) { return df[i]; }, a.omega,
+                                             [&](int i, float2 v) {
+                                                 *reinterpret_cast<float2 *>(dst + (i * G + g)) = v;
+                                             });
+        km = max(km, max(__float_as_int(K.x), __float_as_int(K.y)));
+    }
+    block_max_flush(km, kmax, slot, threadIdx.x & 31);
 }
 
 // Where the fused restriction writes: the coarser level's current buffer, the coarse slot of every
@@ -653,13 +731,13 @@ cudaError_t launch_tiled(const Level &L, const StepArgs &a, int zc, cudaStream_t
     return cudaGetLastError();
 }
 
-// tiled: zc planes per CTA (a multiple of the brick depth dividing n); else flat with
-// threads x cpt cells per CTA
-cudaError_t launch_step(const Mesh &m, int l, bool tiled, int threads, int cpt, int zc,
-                        cudaStream_t s, int src, bool xsel = false) {
+// FORM_TILED: zc planes per CTA (a multiple of the brick depth dividing n); else a flat kernel
+// with threads x cpt cells (pairs for FORM_PAIR) per CTA
+cudaError_t launch_step(const Mesh &m, int l, int form, int threads, int cpt, int zc,
+                        cudaStream_t s, int src) {
     const Level &L = m.lv[l];
     const StepArgs a = step_args(m, l);
-    if (tiled) {
+    if (form == FORM_TILED) {
         switch (L.n) {
             case 8: return launch_tiled<8>(L, a, zc, s, src);
             case 16: return launch_tiled<16>(L, a, zc, s, src);
@@ -669,11 +747,22 @@ cudaError_t launch_step(const Mesh &m, int l, bool tiled, int threads, int cpt, 
         }
     }
     const int ncell = L.n * L.n * L.n;
-    const int chunks = (ncell + threads * cpt - 1) / (threads * cpt);
+    const int units = form == FORM_PAIR ? ncell / 2 : ncell;
+    const int chunks = (units + threads * cpt - 1) / (threads * cpt);
     dim3 grid(L.nslot, chunks);
     const float *fin = L.buf[src];
     float *fout = L.buf[src ^ 1];
-    if (xsel) {
+    if (form == FORM_PAIR) {
+        switch (L.n) {
+            case 8: k_step_pair<8><<<grid, threads, 0, s>>>(fin, fout, L.nbr, a, cpt, L.kmax); break;
+            case 16: k_step_pair<16><<<grid, threads, 0, s>>>(fin, fout, L.nbr, a, cpt, L.kmax); break;
+            case 32: k_step_pair<32><<<grid, threads, 0, s>>>(fin, fout, L.nbr, a, cpt, L.kmax); break;
+            case 64: k_step_pair<64><<<grid, threads, 0, s>>>(fin, fout, L.nbr, a, cpt, L.kmax); break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
+    if (form == FORM_SELECT) {
         switch (L.n) {
             case 16: k_step<16, true><<<grid, threads, 0, s>>>(fin, fout, L.nbr, a, cpt, L.kmax); break;
             case 32: k_step<32, true><<<grid, threads, 0, s>>>(fin, fout, L.nbr, a, cpt, L.kmax); break;
@@ -758,7 +847,7 @@ int advance(Mesh &m, int l, float theta, cudaStream_t s) {
     if (L.fuse && theta > 0.f)  // the second sub-step of the finest level restricts as it steps
         MLCK(launch_step_restrict(m, l, L.fuse_zc, s, L.cur), "level step + restriction");
     else
-        MLCK(launch_step(m, l, L.tiled, L.threads, L.cpt, L.zc, s, L.cur, L.xsel), "level step");
+        MLCK(launch_step(m, l, L.form, L.threads, L.cpt, L.zc, s, L.cur), "level step");
     L.cur ^= 1;
     if (l < m.lmax) {
         int st = advance(m, l + 1, 0.f, s);
@@ -785,41 +874,51 @@ int autotune(Mesh &m, int l, cudaStream_t s) {
     if (L.nslot == 0) return LBM_OK;
     const int ncell = L.n * L.n * L.n;
     struct Cand {
-        bool tiled;
-        int threads, cpt, zc;
-        bool xsel;
+        int form, threads, cpt, zc;
     };
     std::vector<Cand> cand;
     const int flat[][2] = {{128, 1}, {128, 2}, {256, 1}, {256, 2}, {256, 4}, {512, 1}, {512, 2}};
-    const bool xsel_ok = L.n == 16 || L.n == 32 || L.n == 64;
-    for (int xs = 0; xs <= (xsel_ok ? 1 : 0); ++xs)
-        for (const auto &c : flat)
-            if (c[0] * c[1] <= 2 * ncell || (c[0] == 128 && c[1] == 1))
-                cand.push_back({false, c[0], c[1], 1, xs == 1});
+    const bool select_ok = L.n == 16 || L.n == 32 || L.n == 64;
+    const bool pair_ok = has_tiled(L.n);  // edges 8, 16, 32, 64
+    for (int form : {FORM_FLAT, FORM_SELECT})
+        if (form == FORM_FLAT || select_ok)
+            for (const auto &c : flat)
+                if (c[0] * c[1] <= 2 * ncell || (c[0] == 128 && c[1] == 1))
+                    cand.push_back({form, c[0], c[1], 1});
+    if (pair_ok)
+        for (const auto &c : flat)  // k_step_pair takes at most 256 threads per CTA
+            if (c[0] <= 256 && (c[0] * c[1] <= ncell || (c[0] == 128 && c[1] == 1)))
+                cand.push_back({FORM_PAIR, c[0], c[1], 1});
     if (has_tiled(L.n))
         for (int zc = brick_depth(L.n); zc <= L.n; zc *= 2)
-            cand.push_back({true, 256, zc / brick_depth(L.n), zc, false});
+            cand.push_back({FORM_TILED, 256, zc / brick_depth(L.n), zc});
+    // a forced form keeps only its own candidates, where it applies to this level's edge
+    if (m.step_form >= 0) {
+        std::vector<Cand> keep;
+        for (const Cand &c : cand)
+            if (c.form == m.step_form) keep.push_back(c);
+        if (!keep.empty()) cand.swap(keep);
+    }
     cudaEvent_t e0, e1;
     MLCK(cudaEventCreate(&e0), "cudaEventCreate");
     MLCK(cudaEventCreate(&e1), "cudaEventCreate");
     float best = 1e30f;
     for (const Cand &c : cand) {
         for (int k = 0; k < 2; ++k)
-            MLCK(launch_step(m, l, c.tiled, c.threads, c.cpt, c.zc, s, L.cur, c.xsel), "autotune");
+            MLCK(launch_step(m, l, c.form, c.threads, c.cpt, c.zc, s, L.cur), "autotune");
         MLCK(cudaEventRecord(e0, s), "cudaEventRecord");
         for (int k = 0; k < 3; ++k)
-            MLCK(launch_step(m, l, c.tiled, c.threads, c.cpt, c.zc, s, L.cur, c.xsel), "autotune");
+            MLCK(launch_step(m, l, c.form, c.threads, c.cpt, c.zc, s, L.cur), "autotune");
         MLCK(cudaEventRecord(e1, s), "cudaEventRecord");
         MLCK(cudaEventSynchronize(e1), "cudaEventSynchronize");
         float ms = 0.f;
         MLCK(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
         if (ms < best) {
             best = ms;
-            L.tiled = c.tiled;
+            L.form = c.form;
             L.threads = c.threads;
             L.cpt = c.cpt;
             L.zc = c.zc;
-            L.xsel = c.xsel;
         }
     }
     // finest level: the restriction stays a separate kernel unless the mesh's fusion setting
@@ -884,7 +983,7 @@ bool same_layout(const Mesh *m, const int nb[3], int edge, int lmax, const int8_
 }
 
 int build(Mesh **out, const int nb[3], int edge, int lmax, const int8_t *leaf, double tau_fine,
-          const double lid[3], int periodic, int fusion, cudaStream_t s) {
+          const double lid[3], int periodic, int fusion, int step_form, cudaStream_t s) {
     *out = nullptr;
     if (lmax < 0 || lmax >= MAXL) return report_error(LBM_EINVAL, "lmax must be 0, 1 or 2");
     if (edge < 1 || edge % (1 << lmax) != 0 || edge / (1 << lmax) < 2)
@@ -897,6 +996,7 @@ int build(Mesh **out, const int nb[3], int edge, int lmax, const int8_t *leaf, d
     m->edge = edge;
     m->lmax = lmax;
     m->fusion = fusion;
+    m->step_form = step_form;
     m->nblk = nb[0] * nb[1] * nb[2];
     m->leaf.assign(leaf, leaf + m->nblk);
     for (int a = 0; a < 3; ++a) m->lid[a] = lid[a];
@@ -1068,11 +1168,11 @@ int info(const Mesh *m, int l, int *n, double *tau, int *nslot, int *threads, in
     return LBM_OK;
 }
 
-int schedule(const Mesh *m, int l, int *tiled, int *planes, int *fused) {
+int schedule(const Mesh *m, int l, int *form, int *planes, int *fused) {
     if (l < 0 || l > m->lmax) return report_error(LBM_EINVAL, "no such level");
     const Level &L = m->lv[l];
-    if (tiled) *tiled = L.tiled ? 1 : (L.xsel ? 2 : 0);
-    if (planes) *planes = L.tiled ? L.zc : 0;
+    if (form) *form = L.form;
+    if (planes) *planes = L.form == FORM_TILED ? L.zc : 0;
     if (fused) *fused = L.fuse ? L.fuse_zc : 0;
     return LBM_OK;
 }

@@ -95,6 +95,7 @@ _SIGS = {
     "lbm_regrid": (_i, [_h, _vp, _vp, _vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_ll), _vp]),
     "lbm_block_features": (_i, [_h, _i, _vp]),
     "lbm_blocks_set_fusion": (_i, [_h, _i]),
+    "lbm_blocks_set_step_form": (_i, [_h, _i]),
     "lbm_blocks_schedule": (_i, [_h, _i, ctypes.POINTER(_i), ctypes.POINTER(_i),
                                  ctypes.POINTER(_i)]),
     "lbm_net_create": (_vp, [_i, _i]),
@@ -342,8 +343,13 @@ def lbm_blocks_set_fusion(h, mode: int) -> int:
     return _ck(_lib.lbm_blocks_set_fusion(h, int(mode)), "lbm_blocks_set_fusion")
 
 
+def lbm_blocks_set_step_form(h, form: int) -> int:
+    return _ck(_lib.lbm_blocks_set_step_form(h, int(form)), "lbm_blocks_set_step_form")
+
+
 def lbm_blocks_schedule(h, level: int):
-    """(tiled, planes, fused planes) of a level's step schedule."""
+    """(form, planes, fused planes) of a level's step schedule; form 0 flat, 1 tiled, 2 flat with
+    the address-select gather, 3 two cells per thread."""
     t, p, f = _i(), _i(), _i()
     _ck(_lib.lbm_blocks_schedule(h, int(level), ctypes.byref(t), ctypes.byref(p), ctypes.byref(f)),
         "lbm_blocks_schedule")
@@ -528,7 +534,7 @@ class BlockMesh:
     """Multi-level block mesh on a handle: leaf[nbz, nby, nbx] leaf levels, block edge `edge`."""
 
     def __init__(self, leaf, edge, lmax, tau_fine, lid=(0.0, 0.0), periodic=0, graphs=True,
-                 fusion=None):
+                 fusion=None, step_form=None):
         import torch  # noqa: F401  (the caller's CUDA context)
 
         self.leaf = np.ascontiguousarray(leaf, dtype=np.int8)
@@ -541,6 +547,8 @@ class BlockMesh:
         lbm_set_graphs(self.h, 1 if graphs else 0)
         if fusion is not None:
             lbm_blocks_set_fusion(self.h, int(fusion))
+        if step_form is not None:
+            lbm_blocks_set_step_form(self.h, int(step_form))
         self.step(0)
 
     def schedule(self, level):

@@ -61,6 +61,35 @@ def test_three_level_cavity_matches_oracle(L, graphs):
     g.close()
 
 
+FORM_APPLIES = {"FLAT": (0, lambda n: True), "TILED": (1, lambda n: n in (8, 16, 32, 64)),
+                "SELECT": (2, lambda n: n in (16, 32, 64)), "PAIR": (3, lambda n: n in (8, 16, 32, 64))}
+
+
+@pytest.mark.parametrize("form", list(FORM_APPLIES))
+def test_step_forms_match_oracle(L, form):
+    """Every form of the level step kernel, forced on the levels whose block edge it applies to,
+    against the FP64 oracle: a 3-level mesh with 4 / 8 / 16 cells per block edge, where the face
+    lanes of the finest level meet a same-level x-neighbour, an interpolated x ghost and an x
+    wall, and the finest blocks touch the moving lid."""
+    leaf = three_level_leaf()
+    leaf[2, 2, 2] = 2  # an x-neighbour on the finest level, at the x wall
+    edge, lmax, tau, cycles = 16, 2, 0.6, 6
+    g = L.BlockMesh(leaf, edge, lmax, tau, lid=(0.1, 0.02),
+                    step_form=getattr(L, "LBM_STEP_FORM_" + form))
+    want, applies = FORM_APPLIES[form]
+    for level in range(lmax + 1):
+        n = g.info(level)[0]
+        if applies(n):
+            assert g.schedule(level)[0] == want, level
+    o = O.MultiLevel(leaf, edge, lmax, tau, lid=(0.1, 0.0, 0.02))
+    bm = g.step(cycles, block_max=True)
+    o.cycles(cycles)
+    for level in range(lmax + 1):
+        assert rel(g.leaf_field(level), o.leaf_field(level)) < 2e-6, level
+    assert rel(bm, o.block_max()) < 1e-4
+    g.close()
+
+
 def test_graph_replay_is_bitwise_direct_launches(L):
     leaf = three_level_leaf()
     out = []
@@ -119,6 +148,10 @@ def test_block_mesh_argument_errors(L):
         with pytest.raises(L.LbmError) as ei:
             L.lbm_blocks_get(h, 0, 0, np.empty(1))
         assert ei.value.status == L.LBM_ESTATE
+        for form in (-1, L.LBM_STEP_FORM_PAIR + 1):
+            with pytest.raises(L.LbmError) as ei:
+                L.lbm_blocks_set_step_form(h, form)
+            assert ei.value.status == L.LBM_EINVAL
     finally:
         L.lbm_destroy(h)
 
