@@ -524,8 +524,13 @@ LBM_API int lbm_set_kernel_variant(lbm_t *h, int variant) {
     CHECK_H(h);
     if (variant < LBM_KERNEL_AUTO || variant > LBM_KERNEL_TMA)
         return fail(LBM_EINVAL, "unknown kernel variant %d", variant);
-    if (variant == LBM_KERNEL_PAIR && (h->dtype == LBM_F64 || h->nx % 2 != 0))
-        return fail(LBM_EINVAL, "the two-cell kernel needs FP32 arithmetic and an even nx");
+    if (variant == LBM_KERNEL_PAIR &&
+        (h->dtype == LBM_F64 || h->nx % 2 != 0 ||
+         (unsigned long long)(h->q + 1) * ((unsigned long long)h->nx * h->ny * h->nz) >=
+             (1ULL << 32)))
+        return fail(LBM_EINVAL,
+                    "the two-cell kernel needs FP32 arithmetic, an even nx and (q + 1) * cells "
+                    "< 2^32");
     if (variant == LBM_KERNEL_TMA &&
         (h->q != LBM_D3Q19 || h->dtype == LBM_F64 ||
          (long long)h->nx * (h->dtype == LBM_F32 ? 4 : 2) % 16 != 0))

@@ -1,7 +1,8 @@
 """Seeded synthetic inputs shared by the oracle tests and the GPU parity tests.
 
-This module only draws random numbers; it holds none of the lattice Boltzmann arithmetic.  Callers
-turn the draws into populations themselves (f_i = w_i (1 + a * delta_i) with the oracle's weights).
+This module only draws random numbers (and encodes draws in the 16-bit storage formats); it holds
+none of the lattice Boltzmann arithmetic.  Callers turn the draws into populations themselves
+(f_i = w_i (1 + a * delta_i) with the oracle's weights).
 """
 from __future__ import annotations
 
@@ -87,3 +88,23 @@ def uniform_arrays(seed: int, shapes, limits):
     """One uniform draw in [-lim, lim] per (shape, lim) pair, in order (e.g. network weights)."""
     g = rng(seed)
     return [g.uniform(-lim, lim, size=shp) for shp, lim in zip(shapes, limits)]
+
+
+def stored_deviations16(seed: int, w, n: int, amplitude: float, dtype_name: str,
+                        pool: int = 1 << 22) -> np.ndarray:
+    """Stored 16-bit populations of a perturbed state in the shifted form f_i - w_i, one row of n
+    values per direction: deviations w_i * U(-amplitude, amplitude) rounded to FP16 ("F16S") or
+    BF16 ("BF16S", round to nearest even on the upper 16 bits).  Each row repeats a pool of `pool`
+    seeded draws (cheap at 10^8 cells and above), started at a seeded offset."""
+    g = rng(seed)
+    out = np.empty((len(w), n), dtype=np.uint16)
+    for i, wi in enumerate(w):
+        d = (wi * g.uniform(-amplitude, amplitude, size=pool)).astype(np.float32)
+        if dtype_name == "F16S":
+            p16 = d.astype(np.float16).view(np.uint16)
+        else:
+            b = d.view(np.uint32)
+            p16 = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16).astype(np.uint16)
+        p16 = np.roll(p16, int(g.integers(0, pool)))
+        out[i] = np.resize(p16, n)
+    return out

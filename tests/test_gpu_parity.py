@@ -360,6 +360,24 @@ def test_kernel_variants_match_oracle(L, dtype, q, dims, periodic):
 
 
 
+def test_kernel_variant_applicability(L):
+    """A variant that does not apply is refused when it is set (LBM_EINVAL), before any buffer is
+    allocated: the two-cell kernel with FP64 storage, an odd nx, or (q + 1) * cells >= 2^32 (its
+    32-bit offsets); the TMA kernel on D2Q9."""
+    cases = [(19, (33, 8, 8), "F32", "PAIR"), (19, (32, 8, 8), "F64", "PAIR"),
+             (19, (1024, 1024, 208), "F16S", "PAIR"), (9, (64, 64, 1), "F32", "TMA")]
+    for q, (nx, ny, nz), dt, variant in cases:
+        h = L.lbm_create(q, nx, ny, nz, 0.6)
+        try:
+            L.lbm_set_dtype(h, getattr(L, "LBM_" + dt))
+            with pytest.raises(L.LbmError) as ei:
+                L.lbm_set_kernel_variant(h, getattr(L, "LBM_KERNEL_" + variant))
+            assert ei.value.status == L.LBM_EINVAL, (q, nx, dt, variant)
+            L.lbm_set_kernel_variant(h, L.LBM_KERNEL_CELL)  # always applies
+        finally:
+            L.lbm_destroy(h)
+
+
 def test_tma_kernel_long_run_and_sensor_steps(L):
     """The TMA kernel over many steps with mixed sensor / non-sensor steps and graph replay, on a
     lattice with several work units per CTA and an odd plane count per unit: it follows the
@@ -435,53 +453,49 @@ def decode16(raw16, dtype_name):
     return (raw16.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
 
 
-@pytest.mark.parametrize("dtype_name,rel_store", [("F16S", 2.0 ** -10), ("BF16S", 2.0 ** -7)])
-def test_cavity_d3q19_512_16bit_full_size_sampled(L, dtype_name, rel_store):
+@pytest.mark.parametrize("dims,dtype_name,rel_store", [
+    ((512, 512, 512), "F16S", 2.0 ** -10), ((512, 512, 512), "BF16S", 2.0 ** -7),
+    ((1024, 1024, 208), "F16S", 2.0 ** -10)])
+def test_cavity_d3q19_16bit_full_size_sampled(L, dims, dtype_name, rel_store):
     """The 512^3 D3Q19 mixed-precision workloads in the benchmark's launch configuration (the
-    two-cell kernel, sensor every step): one step from a seeded perturbed 16-bit state.  The oracle
-    evaluates sampled sub-boxes of 20^3 cells taken from the decoded state (corners under the lid,
-    edges, faces, the middle): every cell whose pull sources lie in the sub-box, or beyond a face
-    that is a wall of the full lattice, has the same inputs as in the full lattice.  Outputs are
-    compared in deviation form within the 16-bit storage rounding (2^-11 / 2^-8 of the value, with
-    a factor 2 margin, plus 1e-7 absolute for values in the half subnormal range), and the block
-    maxima of 16^3 blocks against the oracle's within 1e-5 (FP32 arithmetic on identical stored
-    inputs)."""
-    n, q = 512, 19
-    tau = O.tau_from_re(0.1, n, 1000.0)
-    lat = L.Lattice(q, n, n, n, tau, dtype=getattr(L, "LBM_" + dtype_name), lid=(0.1, 0.0))
+    two-cell kernel, sensor every step), and a 1024 x 1024 x 208 lattice where 20 x cells exceeds
+    2^32, so the automatic choice falls back to the one-cell kernel with 64-bit offsets: one step
+    from a seeded perturbed 16-bit state.  The oracle evaluates sampled sub-boxes of 20^3 cells
+    taken from the decoded state (corners under the lid, edges, faces, the middle): every cell
+    whose pull sources lie in the sub-box, or beyond a face that is a wall of the full lattice, has
+    the same inputs as in the full lattice.  Outputs are compared in deviation form within the
+    16-bit storage rounding (2^-11 / 2^-8 of the value, with a factor 2 margin, plus 1e-7 absolute
+    for values in the half subnormal range), and the block maxima of 16^3 blocks against the
+    oracle's within 1e-5 (FP32 arithmetic on identical stored inputs)."""
+    nx, ny, nz = dims
+    q = 19
+    tau = O.tau_from_re(0.1, nx, 1000.0)
+    lat = L.Lattice(q, nx, ny, nz, tau, dtype=getattr(L, "LBM_" + dtype_name), lid=(0.1, 0.0))
     L.lbm_set_sensor_every(lat.h, 1)
     c, w, _ = O.lattice(q)
-    N = n ** 3
-    g = seeded.rng(512)
-    raw = np.empty((q, N), dtype=np.uint16)
-    for i in range(q):  # stored deviations w_i * U(-0.03, 0.03), drawn population by population
-        d = (w[i] * g.uniform(-0.03, 0.03, size=N)).astype(np.float32)
-        if dtype_name == "F16S":
-            raw[i] = d.astype(np.float16).view(np.uint16)
-        else:  # round to nearest even on the upper 16 bits
-            b = d.view(np.uint32)
-            raw[i] = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16).astype(np.uint16)
-        del d
+    N = nx * ny * nz
+    raw = seeded.stored_deviations16(512 + nz, w, N, 0.03, dtype_name)
     lat.set_raw(raw.view(np.uint8).reshape(-1))
     lat.step(1)
-    out = lat.raw().view(np.uint16).reshape(q, n, n, n)
+    out = lat.raw().view(np.uint16).reshape(q, nz, ny, nx)
     gmax = lat.sensor(16)
     lat.close()
-    raw = raw.reshape(q, n, n, n)
+    raw = raw.reshape(q, nz, ny, nx)
     S = 20
-    origins = [(0, 0, 0), (n - S, n - S, n - S), (0, n - S, 0), (n - S, n - S, 0), (n - S, 0, n - S),
-               (n // 2, n // 2, n // 2), (0, n // 3, n - S), (n // 4, n - S, n // 2)]
+    origins = [(0, 0, 0), (nx - S, ny - S, nz - S), (0, ny - S, 0), (nx - S, ny - S, 0),
+               (nx - S, 0, nz - S), (nx // 2, ny // 2, nz // 2), (0, ny // 3, nz - S),
+               (nx // 4, ny - S, nz // 2)]
     checked = 0
     for (x0, y0, z0) in origins:
         sub = decode16(raw[:, z0:z0 + S, y0:y0 + S, x0:x0 + S].copy(), dtype_name)
         f_sub = sub + w[:, None, None, None]
-        o = O.Oracle(q, S, S, S, tau, lid=(0.1, 0.0, 0.0) if y0 + S == n else (0.0, 0.0, 0.0))
+        o = O.Oracle(q, S, S, S, tau, lid=(0.1, 0.0, 0.0) if y0 + S == ny else (0.0, 0.0, 0.0))
         ok = []
-        for a, a0 in ((0, x0), (1, y0), (2, z0)):
+        for a0, n_ax in ((x0, nx), (y0, ny), (z0, nz)):
             loc = np.arange(S)
             good = (loc >= 1) & (loc <= S - 2)
             good |= (loc == 0) & (a0 == 0)
-            good |= (loc == S - 1) & (a0 + S == n)
+            good |= (loc == S - 1) & (a0 + S == n_ax)
             ok.append(good)
         zz, yy, xx = np.meshgrid(np.where(ok[2])[0], np.where(ok[1])[0], np.where(ok[0])[0],
                                  indexing="ij")
@@ -496,14 +510,15 @@ def test_cavity_d3q19_512_16bit_full_size_sampled(L, dtype_name, rel_store):
         checked += len(cells)
     assert checked > 30000
     # sampled 16^3 blocks with their one-cell margin (or a real wall) inside an 18^3 sub-box
-    nb = n // 16
-    for (bx, by, bz) in ((0, 0, 0), (nb - 1, nb - 1, nb - 1), (0, nb - 1, nb - 1), (nb // 2, nb - 1, 3),
-                         (7, 11, 13)):
-        x0, y0, z0 = [max(0, min(n - 18, 16 * b - 1)) for b in (bx, by, bz)]
+    nbx, nby, nbz = nx // 16, ny // 16, nz // 16
+    for (bx, by, bz) in ((0, 0, 0), (nbx - 1, nby - 1, nbz - 1), (0, nby - 1, nbz - 1),
+                         (nbx // 2, nby - 1, 3), (7, 11, 12)):
+        x0, y0, z0 = [max(0, min(n_ax - 18, 16 * b - 1))
+                      for b, n_ax in ((bx, nx), (by, ny), (bz, nz))]
         sub = decode16(raw[:, z0:z0 + 18, y0:y0 + 18, x0:x0 + 18].copy(), dtype_name)
-        o = O.Oracle(q, 18, 18, 18, tau, lid=(0.1, 0.0, 0.0) if y0 + 18 == n else (0.0, 0.0, 0.0))
+        o = O.Oracle(q, 18, 18, 18, tau, lid=(0.1, 0.0, 0.0) if y0 + 18 == ny else (0.0, 0.0, 0.0))
         zz, yy, xx = np.meshgrid(np.arange(16) + 16 * bz - z0, np.arange(16) + 16 * by - y0,
                                  np.arange(16) + 16 * bx - x0, indexing="ij")
         _, K = o.step_cells(sub + w[:, None, None, None], ((zz * 18 + yy) * 18 + xx).reshape(-1))
-        bidx = (bz * nb + by) * nb + bx
+        bidx = (bz * nby + by) * nbx + bx
         assert abs(gmax[bidx] - K.max()) / K.max() < 1e-5, (bx, by, bz)
