@@ -619,21 +619,33 @@ def run_ours(args, w, ws, rank, local):
     value = cells * args.steps * ws / (ms_max / 1e3) / 1e6
 
     # ---- end to end through the C ABI with host buffers: the job's initial state goes up from
-    # pinned host memory, every step's flags come back to the host, the final state comes back
+    # pinned host memory, every sensor step's flags come back to pinned host memory, the final
+    # state comes back.  The flags of a step are copied while the next step runs (two flag
+    # buffers); the host waits for step k's flags after launching step k + 1, as a driver that
+    # regrids from them would.
     nbytes = L.lbm_population_bytes(h)
     host_state = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
     L.lbm_get_raw(h, host_state.data_ptr(), nbytes)
-    host_flags = torch.empty(nb, dtype=torch.int8, pin_memory=True)
-    flag_call = L.lbm_flag_top if w["rule"] == "top" else L.lbm_flag
+    host_flags = [torch.empty(nb, dtype=torch.int8, pin_memory=True) for _ in range(2)]
+    dev_flags = [torch.empty(nb, dtype=torch.int8, device="cuda") for _ in range(2)]
+    flag_ready = [torch.cuda.Event() for _ in range(2)]
+    flag_dev = L.lbm_flag_top_dev if w["rule"] == "top" else L.lbm_flag_dev
     e2e_steps = args.steps
     barrier(ws)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     L.lbm_set_raw(h, host_state.data_ptr(), nbytes)
+    pending = None
     for k in range(e2e_steps):
         L.lbm_step(h, 1)
         if w["sensor_every"] == 1 or (k + 1) % w["sensor_every"] == 0:
-            flag_call(h, param, host_flags.data_ptr())
+            j = k & 1
+            flag_dev(h, param, dev_flags[j])
+            host_flags[j].copy_(dev_flags[j], non_blocking=True)
+            flag_ready[j].record(stream)
+            if pending is not None:
+                flag_ready[pending].synchronize()  # the previous sensor step's flags are home
+            pending = j
     L.lbm_get_raw(h, host_state.data_ptr(), nbytes)
     torch.cuda.synchronize()
     e2e_s = reduce_max(time.perf_counter() - t0, ws)
