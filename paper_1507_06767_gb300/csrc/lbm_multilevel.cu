@@ -285,6 +285,28 @@ __device__ __forceinline__ float step_cell(const float *__restrict__ in, const f
     });
 }
 
+// Row r (0 <= r < n^2) of a block in the order interior rows first, then face rows: rows with
+// 1 <= y, z <= n - 2 (y fastest), then the planes z = 0 and z = n - 1, then the rows y = 0 and
+// y = n - 1 of the planes in between.
+template <int n>
+__device__ __forceinline__ void face_row_order(int r, int &y, int &z) {
+    constexpr int ni = (n - 2) * (n - 2);
+    if (r < ni) {
+        y = 1 + r % (n - 2);
+        z = 1 + r / (n - 2);
+        return;
+    }
+    const int f = r - ni;
+    if (f < 2 * n) {
+        z = f < n ? 0 : n - 1;
+        y = f < n ? f : f - n;
+        return;
+    }
+    const int k = f - 2 * n;
+    z = 1 + (k >> 1);
+    y = (k & 1) ? n - 1 : 0;
+}
+
 // warp max of the sensor bits, one atomic per warp (every lane of the warp must call this)
 __device__ __forceinline__ void block_max_flush(int km, float *kmax, int slot, int lane) {
 #pragma unroll
@@ -292,9 +314,9 @@ __device__ __forceinline__ void block_max_flush(int km, float *kmax, int slot, i
     if (lane == 0) atomicMax(reinterpret_cast<int *>(kmax) + slot, km);
 }
 
-// Flat mapping: grid (slot, chunk), cells of a block in x-fastest order, each thread `cpt` cells.
-// NT is the block edge when it is one of the compiled sizes (shifts instead of divisions), 0
-// otherwise.
+// Flat mapping: grid (slot, chunk), cells of a block in x-fastest order, each thread `cpt` cells;
+// with XSEL the rows come interior rows first (face_row_order).  NT is the block edge when it is
+// one of the compiled sizes (shifts instead of divisions), 0 otherwise (never with XSEL).
 template <int NT, bool XSEL = false>
 __global__ void k_step(const float *__restrict__ in, float *__restrict__ out,
                        const int *__restrict__ nbr, const StepArgs a, int cpt, float *kmax) {
@@ -311,8 +333,14 @@ __global__ void k_step(const float *__restrict__ in, float *__restrict__ out,
     for (int r = 0; r < cpt; ++r) {
         const int c = (blockIdx.y * cpt + r) * blockDim.x + threadIdx.x;
         if (c >= ncell) break;
-        const float K =
-            step_cell<NT, XSEL>(in, src, dst, snb, top, a, c % n, (c / n) % n, c / (n * n));
+        int y, z;
+        if (XSEL) {  // interior rows first, so that a warp's rows take one gather only
+            face_row_order<(NT ? NT : 16)>(c / n, y, z);
+        } else {
+            y = (c / n) % n;
+            z = c / (n * n);
+        }
+        const float K = step_cell<NT, XSEL>(in, src, dst, snb, top, a, c % n, y, z);
         km = max(km, __float_as_int(K));
     }
     block_max_flush(km, kmax, slot, threadIdx.x & 31);
@@ -359,7 +387,9 @@ __global__ void __launch_bounds__(256, 4) k_step_tiled(const float *__restrict__
 // and z take the address-select gather (a face lane pulling along x reads the x-neighbour block,
 // the interpolated x-ghost column or its own opposite population at a wall); rows on a y or z
 // face take the per-cell gather of step_cell.  Flat mapping: grid (slot, chunk), `cpt` pairs per
-// thread in x-fastest order.
+// thread, x fastest; the rows of a block are ordered interior rows first ((n - 2)^2 rows, y
+// fastest), then the rows on a y or z face, so that a warp holds rows of one kind only (except one
+// warp for n = 8) and does not run both the select gather and the per-cell one.
 template <int NT>
 __global__ void __launch_bounds__(256, 3) k_step_pair(const float *__restrict__ in,
                                                    float *__restrict__ out,
@@ -381,40 +411,40 @@ __global__ void __launch_bounds__(256, 3) k_step_pair(const float *__restrict__ 
     for (int r = 0; r < cpt; ++r) {
         const int pidx = (blockIdx.y * cpt + r) * blockDim.x + threadIdx.x;
         if (pidx >= npair) break;
-        const int x0 = 2 * (pidx % half), y = (pidx / half) % n, z = pidx / (half * n);
+        const int x0 = 2 * (pidx % half);
+        int y, z;
+        face_row_order<n>(pidx / half, y, z);
+        const int g = (z + 1) * plane + (y + 1) * row + x0;
+        const bool lo = x0 == 0, hi = x0 + 2 == n;
         if (y == 0 || y == n - 1 || z == 0 || z == n - 1) {
             const float K0 = step_cell<NT>(in, src, dst, snb, top, a, x0, y, z);
             const float K1 = step_cell<NT>(in, src, dst, snb, top, a, x0 + 1, y, z);
             km = max(km, max(__float_as_int(K0), __float_as_int(K1)));
             continue;
         }
-        const int g = (z + 1) * plane + (y + 1) * row + x0;
-        const bool lo = x0 == 0, hi = x0 + 2 == n;
-        float2 df[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
+        // the pull of direction i for a row whose y and z sources lie in this block (or its
+        // ghost rows): the x-face lanes select their x neighbour
+        const auto inner = [&](int i) -> float2 {
             const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
             const int off = cz * plane + cy * row;
             const float *base = src + (i * G + g - off);
-            float2 v;
-            if (cx == 0) {
-                v = *reinterpret_cast<const float2 *>(base);
-            } else {
-                const int ghost = (z - cz + 1) * (n + 2) + (y - cy + 1);
-                if (cx == 1) {  // cell x0 pulls from x0 - 1, cell x0 + 1 from x0
-                    const float *alt = nbm >= 0 ? in + ((size_t)nbm * Q * G + (i * G + g - off - 1 + n))
-                                       : nbm == NB_GHOST ? src + (i * G + side_base(n, 0) + ghost)
-                                                         : src + (L::opp(i) * G + g);
-                    v = make_float2(*(lo ? alt : base - 1), *base);
-                } else {  // cell x0 pulls from x0 + 1, cell x0 + 1 from x0 + 2
-                    const float *alt = nbp >= 0 ? in + ((size_t)nbp * Q * G + (i * G + g - off + 2 - n))
-                                       : nbp == NB_GHOST ? src + (i * G + side_base(n, 1) + ghost)
-                                                         : src + (L::opp(i) * G + g + 1);
-                    v = make_float2(base[1], *(hi ? alt : base + 2));
-                }
+            if (cx == 0) return *reinterpret_cast<const float2 *>(base);
+            const int ghost = (z - cz + 1) * (n + 2) + (y - cy + 1);
+            if (cx == 1) {  // cell x0 pulls from x0 - 1, cell x0 + 1 from x0
+                const float *alt = nbm >= 0 ? in + ((size_t)nbm * Q * G + (i * G + g - off - 1 + n))
+                                   : nbm == NB_GHOST ? src + (i * G + side_base(n, 0) + ghost)
+                                                     : src + (L::opp(i) * G + g);
+                return make_float2(*(lo ? alt : base - 1), *base);
             }
-            df[i] = __fadd2_rn(v, f2(-weight<L, float>(i)));
-        }
+            // cell x0 pulls from x0 + 1, cell x0 + 1 from x0 + 2
+            const float *alt = nbp >= 0 ? in + ((size_t)nbp * Q * G + (i * G + g - off + 2 - n))
+                               : nbp == NB_GHOST ? src + (i * G + side_base(n, 1) + ghost)
+                                                 : src + (L::opp(i) * G + g + 1);
+            return make_float2(base[1], *(hi ? alt : base + 2));
+        };
+        float2 df[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) df[i] = __fadd2_rn(inner(i), f2(-weight<L, float>(i)));
         const float2 K = relax_pair<L, 1, 1>([&](int i) { return df[i]; },
                                              [&](int i) { return df[i]; }, a.omega,
                                              [&](int i, float2 v) {

@@ -65,23 +65,27 @@ FORM_APPLIES = {"FLAT": (0, lambda n: True), "TILED": (1, lambda n: n in (8, 16,
                 "SELECT": (2, lambda n: n in (16, 32, 64)), "PAIR": (3, lambda n: n in (8, 16, 32, 64))}
 
 
-@pytest.mark.parametrize("form", list(FORM_APPLIES))
-def test_step_forms_match_oracle(L, form):
+@pytest.mark.parametrize("form,periodic", [(f, 0) for f in FORM_APPLIES] +
+                         [("SELECT", "XZ"), ("PAIR", "XZ")])
+def test_step_forms_match_oracle(L, form, periodic):
     """Every form of the level step kernel, forced on the levels whose block edge it applies to,
     against the FP64 oracle: a 3-level mesh with 4 / 8 / 16 cells per block edge, where the face
-    lanes of the finest level meet a same-level x-neighbour, an interpolated x ghost and an x
-    wall, and the finest blocks touch the moving lid."""
+    lanes and face rows of the finest level meet a same-level neighbour, an interpolated ghost and
+    a wall, and the finest blocks touch the moving lid; with periodic x and z axes the neighbours
+    across the domain's x and z faces are the wrapped blocks."""
     leaf = three_level_leaf()
     leaf[2, 2, 2] = 2  # an x-neighbour on the finest level, at the x wall
     edge, lmax, tau, cycles = 16, 2, 0.6, 6
-    g = L.BlockMesh(leaf, edge, lmax, tau, lid=(0.1, 0.02),
+    per = (L.LBM_PERIODIC_X | L.LBM_PERIODIC_Z) if periodic else 0
+    g = L.BlockMesh(leaf, edge, lmax, tau, lid=(0.1, 0.02), periodic=per,
                     step_form=getattr(L, "LBM_STEP_FORM_" + form))
     want, applies = FORM_APPLIES[form]
     for level in range(lmax + 1):
         n = g.info(level)[0]
         if applies(n):
             assert g.schedule(level)[0] == want, level
-    o = O.MultiLevel(leaf, edge, lmax, tau, lid=(0.1, 0.0, 0.02))
+    o = O.MultiLevel(leaf, edge, lmax, tau, lid=(0.1, 0.0, 0.02),
+                     periodic=(O.PERIODIC_X | O.PERIODIC_Z) if periodic else 0)
     bm = g.step(cycles, block_max=True)
     o.cycles(cycles)
     for level in range(lmax + 1):
