@@ -27,9 +27,11 @@ constexpr int TILE = 8;
 // kernel: 4 -> at most 64 registers, 1024 threads per SM; the two-cell kernel with 16-bit storage:
 // 4, no spills, measured at 512^3 FP16 1.91 ms against 2.00 ms with 3; with FP32 storage: 3 -> at
 // most 80 registers, no spills, 3.03 ms against 3.15 ms with 4), and cache hints of the population
-// loads / stores (0: default, 1: read-only path / streaming store, 2: evict-first load).  Measured
-// on GB300 at 256^3 D3Q19 FP32: without a minimum the allocator takes 140 registers and the
-// one-cell kernel runs at half speed.
+// loads / stores (0: default, 1: read-only path / streaming store, 2: evict-first load, 3:
+// read-only path asking L2 for the 256-byte group around each address: 512^3 FP16 two-cell 1.912
+// -> 1.887 ms, FP32 one-cell 3.109 -> 3.074 ms, FP32 two-cell unchanged).  Measured on GB300 at
+// 256^3 D3Q19 FP32: without a minimum the allocator takes 140 registers and the one-cell kernel
+// runs at half speed.
 #ifndef LBM_STEP_MIN_BLOCKS
 #define LBM_STEP_MIN_BLOCKS 4
 #endif
@@ -40,7 +42,7 @@ constexpr int TILE = 8;
 #define LBM_PAIR_MIN_BLOCKS_F32 3
 #endif
 #ifndef LBM_LOAD_HINT
-#define LBM_LOAD_HINT 1
+#define LBM_LOAD_HINT 3
 #endif
 #ifndef LBM_STORE_HINT
 #define LBM_STORE_HINT 0
@@ -57,7 +59,7 @@ constexpr int TILE = 8;
 
 template <class T>
 __device__ __forceinline__ T load_pop(const T *p) {
-#if LBM_LOAD_HINT == 1
+#if LBM_LOAD_HINT == 1 || LBM_LOAD_HINT == 3
     return __ldg(p);
 #elif LBM_LOAD_HINT == 2
     return __ldcs(p);
@@ -65,6 +67,34 @@ __device__ __forceinline__ T load_pop(const T *p) {
     return *p;
 #endif
 }
+
+#if LBM_LOAD_HINT == 3
+// read-only loads that also ask L2 to fetch the whole 256-byte sector group around the address
+template <>
+__device__ __forceinline__ float load_pop<float>(const float *p) {
+    float v;
+    asm("ld.global.nc.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+template <>
+__device__ __forceinline__ float2 load_pop<float2>(const float2 *p) {
+    float2 v;
+    asm("ld.global.nc.L2::256B.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+}
+template <>
+__device__ __forceinline__ unsigned load_pop<unsigned>(const unsigned *p) {
+    unsigned v;
+    asm("ld.global.nc.L2::256B.b32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+template <>
+__device__ __forceinline__ unsigned short load_pop<unsigned short>(const unsigned short *p) {
+    unsigned short v;
+    asm("ld.global.nc.L2::256B.u16 %0, [%1];" : "=h"(v) : "l"(p));
+    return v;
+}
+#endif
 
 template <class T>
 __device__ __forceinline__ void store_pop(T *p, T v) {
