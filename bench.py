@@ -635,6 +635,7 @@ def run_ours(args, w, ws, rank, local):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     L.lbm_set_raw(h, host_state.data_ptr(), nbytes)
+    t_up = time.perf_counter() - t0
     pending = None
     for k in range(e2e_steps):
         L.lbm_step(h, 1)
@@ -646,14 +647,21 @@ def run_ours(args, w, ws, rank, local):
             if pending is not None:
                 flag_ready[pending].synchronize()  # the previous sensor step's flags are home
             pending = j
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
     L.lbm_get_raw(h, host_state.data_ptr(), nbytes)
     torch.cuda.synchronize()
-    e2e_s = reduce_max(time.perf_counter() - t0, ws)
+    t2 = time.perf_counter()
+    t_down = t2 - t1
+    e2e_s = reduce_max(t2 - t0, ws)
     barrier(ws)
     n_flag_reads = e2e_steps // w["sensor_every"]
     e2e = {"value": round(cells * e2e_steps * ws / e2e_s / 1e6, 1), "unit": "MLUPS",
            "h2d_bytes_per_step": int(round(nbytes / e2e_steps)),
-           "d2h_bytes_per_step": int(round((nbytes + n_flag_reads * nb) / e2e_steps))}
+           "d2h_bytes_per_step": int(round((nbytes + n_flag_reads * nb) / e2e_steps)),
+           # host link rates seen by the state copies of this run (they vary with the host)
+           "state_h2d_gbs": round(nbytes / t_up / 1e9, 1),
+           "state_d2h_gbs": round(nbytes / t_down / 1e9, 1)}
 
     peak, peak_kind = load_peaks()
     per_launch_bytes = algorithmic_bytes_per_cell(w) * cells
