@@ -685,14 +685,18 @@ static int flag_common(lbm_t *h, int rule, double param, int8_t *out, bool host)
         return fail(LBM_EINVAL, "threshold must be finite");
     if (rule == LBM_FLAG_TOP && !(param >= 0.0 && param <= 1.0))
         return fail(LBM_EINVAL, "fraction must be in [0, 1] (got %g)", param);
-    int nb = 0;
-    int st = reduce_blocks(h, h->block, &nb);
+    if (!h->have_sensor) return fail(LBM_ESTATE, "no sensor step since the last reset");
+    int nbx, nby, nbz, m, mz;
+    int st = check_block(h, h->block, &nbx, &nby, &nbz, &m, &mz);
     if (st != LBM_OK) return st;
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    const int nb = nbx * nby * nbz;
     int8_t *dst = host ? h->flags : out;
-    if (rule == LBM_FLAG_THRESHOLD)
-        CK(lbm::flags_threshold(h->rtype(), h->blocks, nb, param, dst, h->stream), "flags");
-    else
-        CK(lbm::flags_top(h->rtype(), h->blocks, nb, top_count(param, nb), dst, h->stream), "flags");
+    // block maxima (kept in h->blocks, as reduce_blocks leaves them) and flags
+    CK(lbm::flags_from_tiles(h->rtype(), h->tiles, h->ntx, h->nty, h->ntz, m, mz, h->blocks, nbx,
+                             nby, nbz, rule == LBM_FLAG_THRESHOLD ? 0 : 1, param,
+                             rule == LBM_FLAG_TOP ? top_count(param, nb) : 0, dst, h->stream),
+       "flags");
     if (host) {
         CK(cudaMemcpyAsync(out, h->flags, (size_t)nb, cudaMemcpyDeviceToHost, h->stream),
            "cudaMemcpyAsync");

@@ -199,25 +199,47 @@ __global__ void __launch_bounds__(1024) k_cons_final(const double *partial, int 
     if (threadIdx.x < 5) result[threadIdx.x] = sh[threadIdx.x][0];
 }
 
+// Block maximum of K over the tiles of block b (tile maxima compared as order-preserving bits, so
+// a NaN tile makes the block NaN).
+template <class R>
+__device__ __forceinline__ R block_of_tiles(const R *tiles, int ntx, int nty, int ntz, int m, int mz,
+                                            int nbx, int nby, long long b) {
+    using B = typename Bits<R>::type;
+    const int bx = (int)(b % nbx);
+    const int by = (int)((b / nbx) % nby);
+    const int bz = (int)(b / ((long long)nbx * nby));
+    B mx = 0;
+    if (m == 2 && mz <= 2) {
+        // blocks of 2 x 2 (x 2) tiles (the 16-cell block on 8-cell tiles): the tile loads are
+        // independent, so they are issued together
+        B v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int tx = 2 * bx + (j & 1), ty = 2 * by + ((j >> 1) & 1);
+            const int tz = bz * mz + (j >> 2);
+            const bool ok = tx < ntx && ty < nty && (j >> 2) < mz && tz < ntz;
+            v[j] = ok ? max_bits(tiles[((size_t)tz * nty + ty) * ntx + tx]) : B(0);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) mx = v[j] > mx ? v[j] : mx;
+        return from_bits(mx, R(0));
+    }
+    for (int tz = bz * mz; tz < min(bz * mz + mz, ntz); ++tz)
+        for (int ty = by * m; ty < min(by * m + m, nty); ++ty)
+            for (int tx = bx * m; tx < min(bx * m + m, ntx); ++tx) {
+                const B v = max_bits(tiles[((size_t)tz * nty + ty) * ntx + tx]);
+                mx = v > mx ? v : mx;
+            }
+    return from_bits(mx, R(0));
+}
+
 template <class R>
 __global__ void k_tiles_to_blocks(const R *tiles, int ntx, int nty, int ntz, int m, int mz,
                                   R *blocks, int nbx, int nby, int nbz) {
-    using B = typename Bits<R>::type;
     const long long nb = (long long)nbx * nby * nbz;
     for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
-         b += (long long)gridDim.x * blockDim.x) {
-        const int bx = (int)(b % nbx);
-        const int by = (int)((b / nbx) % nby);
-        const int bz = (int)(b / ((long long)nbx * nby));
-        B mx = 0;
-        for (int tz = bz * mz; tz < min(bz * mz + mz, ntz); ++tz)
-            for (int ty = by * m; ty < min(by * m + m, nty); ++ty)
-                for (int tx = bx * m; tx < min(bx * m + m, ntx); ++tx) {
-                    const B v = max_bits(tiles[((size_t)tz * nty + ty) * ntx + tx]);
-                    mx = v > mx ? v : mx;
-                }
-        blocks[b] = from_bits(mx, R(0));
-    }
+         b += (long long)gridDim.x * blockDim.x)
+        blocks[b] = block_of_tiles(tiles, ntx, nty, ntz, m, mz, nbx, nby, b);
 }
 
 template <class R>
@@ -313,6 +335,114 @@ __global__ void __launch_bounds__(TOP_THREADS) k_flags_top(const R *m, int n, in
     int before = scan[tid] - eq;
     for (int e = start; e < end; ++e) {
         const K key = sort_key(m[e]);
+        int8_t fl = 0;
+        if (key > prefix) {
+            fl = 1;
+        } else if (key == prefix) {
+            fl = (before < remaining) ? int8_t(1) : int8_t(0);
+            ++before;
+        }
+        out[e] = fl;
+    }
+}
+
+// Threshold flags straight from the tile maxima: the block maxima (also written to `blocks`) and
+// their flags (+1 refine if max > T or NaN, -1 coarsen if max < T/2, else 0) in one pass.
+template <class R>
+__global__ void k_flags_threshold_tiles(const R *tiles, int ntx, int nty, int ntz, int m, int mz,
+                                        R *blocks, int nbx, int nby, int nbz, double T,
+                                        double half_T, int8_t *out) {
+    const long long nb = (long long)nbx * nby * nbz;
+    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
+         b += (long long)gridDim.x * blockDim.x) {
+        const R mx = block_of_tiles(tiles, ntx, nty, ntz, m, mz, nbx, nby, b);
+        blocks[b] = mx;
+        const double v = (double)mx;
+        out[b] = (isnan(v) || v > T) ? int8_t(1) : (v < half_T ? int8_t(-1) : int8_t(0));
+    }
+}
+
+// Top-k flags of n block maxima in one CTA with their order-preserving keys held in shared memory
+// for the 8-bit radix passes that find the k-th largest key (the global-memory form, k_flags_top,
+// reads the maxima again on every pass); keys above it are flagged, and of the keys equal to it
+// the lowest indices, as many as remain.  Needs n * sizeof(K) bytes of dynamic shared memory (at
+// most TOP_SMEM_BYTES) and 0 < k < n.
+constexpr int TOP_SMEM_BYTES = 64 * 1024;
+
+template <class R, class K>
+__global__ void __launch_bounds__(TOP_THREADS) k_flags_top_keys(const R *maxima, int n, int k,
+                                                               int8_t *out) {
+    extern __shared__ __align__(16) unsigned char top_smem[];
+    K *keys = reinterpret_cast<K *>(top_smem);
+    __shared__ unsigned hist[256];
+    __shared__ int s_digit, s_remaining;
+    __shared__ int wsum[TOP_THREADS / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int b = tid; b < n; b += TOP_THREADS) keys[b] = sort_key(maxima[b]);
+    K prefix = 0, mask = 0;
+    int remaining = k;
+    for (int shift = 8 * (int)sizeof(K) - 8; shift >= 0; shift -= 8) {
+        for (int b = tid; b < 256; b += TOP_THREADS) hist[b] = 0;
+        __syncthreads();  // also orders the key writes above before the first pass
+        for (int e = tid; e < n; e += TOP_THREADS) {
+            const K key = keys[e];
+            if ((key & mask) == prefix) atomicAdd(&hist[(unsigned)(key >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (tid < 32) {
+            const int hi = 255 - 8 * tid;  // this lane's bins: hi, hi-1, ..., hi-7
+            unsigned sum8 = 0;
+            for (int j = 0; j < 8; ++j) sum8 += hist[hi - j];
+            unsigned incl = sum8;
+            for (int off = 1; off < 32; off <<= 1) {
+                const unsigned o = __shfl_up_sync(0xffffffffu, incl, off);
+                if (tid >= off) incl += o;
+            }
+            const unsigned ballot = __ballot_sync(0xffffffffu, incl >= (unsigned)remaining);
+            const int first = __ffs(ballot) - 1;
+            if (tid == first) {
+                unsigned c = incl - sum8;
+                for (int j = 0; j < 8; ++j) {
+                    const unsigned h = hist[hi - j];
+                    if (c + h >= (unsigned)remaining) {
+                        s_digit = hi - j;
+                        s_remaining = remaining - (int)c;
+                        break;
+                    }
+                    c += h;
+                }
+            }
+        }
+        __syncthreads();
+        prefix |= (K)s_digit << shift;
+        mask |= (K)0xFF << shift;
+        remaining = s_remaining;
+        __syncthreads();
+    }
+    // keys equal to the k-th largest: exclusive count over the threads' contiguous chunks
+    const int chunk = (n + TOP_THREADS - 1) / TOP_THREADS;
+    const int start = min(tid * chunk, n), end = min(start + chunk, n);
+    int eq = 0;
+    for (int e = start; e < end; ++e) eq += (keys[e] == prefix);
+    int incl = eq;
+    for (int off = 1; off < 32; off <<= 1) {
+        const int o = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += o;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int v = wsum[lane];
+        for (int off = 1; off < 32; off <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, v, off);
+            if (lane >= off) v += o;
+        }
+        wsum[lane] = v;
+    }
+    __syncthreads();
+    int before = (warp > 0 ? wsum[warp - 1] : 0) + incl - eq;
+    for (int e = start; e < end; ++e) {
+        const K key = keys[e];
         int8_t fl = 0;
         if (key > prefix) {
             fl = 1;
@@ -515,6 +645,57 @@ cudaError_t flags_threshold(int rtype, const void *maxima, int n, double T, int8
     else
         k_flags_threshold<float><<<g, 256, 0, s>>>(static_cast<const float *>(maxima), n, T,
                                                    T / 2.0, out);
+    return cudaGetLastError();
+}
+
+// Block maxima of the last sensor step's tiles and their flags (rule 0: threshold `param`, one
+// launch; 1: the k largest: the block maxima, then the one-CTA select over shared-memory keys, or
+// over global memory where the keys do not fit).
+cudaError_t flags_from_tiles(int rtype, const void *tiles, int ntx, int nty, int ntz, int m, int mz,
+                             void *blocks, int nbx, int nby, int nbz, int rule, double param, int k,
+                             int8_t *out, cudaStream_t s) {
+    const long long nb = (long long)nbx * nby * nbz;
+    if (nb <= 0) return cudaSuccess;
+    if (rule == 0) {
+        const unsigned g = small_grid(nb, 256);
+        if (rtype == 0)
+            k_flags_threshold_tiles<double><<<g, 256, 0, s>>>(
+                static_cast<const double *>(tiles), ntx, nty, ntz, m, mz,
+                static_cast<double *>(blocks), nbx, nby, nbz, param, param / 2.0, out);
+        else
+            k_flags_threshold_tiles<float><<<g, 256, 0, s>>>(
+                static_cast<const float *>(tiles), ntx, nty, ntz, m, mz,
+                static_cast<float *>(blocks), nbx, nby, nbz, param, param / 2.0, out);
+        return cudaGetLastError();
+    }
+    cudaError_t e = tiles_to_blocks(rtype, tiles, ntx, nty, ntz, m, mz, blocks, nbx, nby, nbz, s);
+    if (e != cudaSuccess) return e;
+    const size_t key_bytes = rtype == 0 ? sizeof(unsigned long long) : sizeof(uint32_t);
+    if (k <= 0 || k >= nb || (size_t)nb * key_bytes > (size_t)TOP_SMEM_BYTES)
+        return flags_top(rtype, blocks, (int)nb, k, out, s);
+    // the dynamic shared memory above 48 KB is granted per function and device, once
+    static bool granted[2][64] = {};
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!granted[rtype == 0][dev]) {
+        e = rtype == 0 ? cudaFuncSetAttribute(k_flags_top_keys<double, unsigned long long>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              TOP_SMEM_BYTES)
+                       : cudaFuncSetAttribute(k_flags_top_keys<float, uint32_t>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              TOP_SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        granted[rtype == 0][dev] = true;
+    }
+    const size_t smem = (size_t)nb * key_bytes;
+    if (rtype == 0)
+        k_flags_top_keys<double, unsigned long long><<<1, TOP_THREADS, smem, s>>>(
+            static_cast<const double *>(blocks), (int)nb, k, out);
+    else
+        k_flags_top_keys<float, uint32_t><<<1, TOP_THREADS, smem, s>>>(
+            static_cast<const float *>(blocks), (int)nb, k, out);
     return cudaGetLastError();
 }
 

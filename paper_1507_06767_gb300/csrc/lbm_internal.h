@@ -55,6 +55,12 @@ cudaError_t to_f64(int rtype, const void *in, double *out, size_t n, cudaStream_
 cudaError_t flags_threshold(int rtype, const void *maxima, int n, double T, int8_t *out,
                             cudaStream_t s);
 cudaError_t flags_top(int rtype, const void *maxima, int n, int k, int8_t *out, cudaStream_t s);
+// block maxima from the tile maxima (written to blocks) and their flags: rule 0 threshold
+// `param` in one launch; rule 1 the k largest (block maxima, then a one-CTA select with the keys
+// in shared memory where they fit)
+cudaError_t flags_from_tiles(int rtype, const void *tiles, int ntx, int nty, int ntz, int m, int mz,
+                             void *blocks, int nbx, int nby, int nbz, int rule, double param, int k,
+                             int8_t *out, cudaStream_t s);
 
 // Level map (Sec. 3.4) of n block maxima, affine (a, b given) or fitted to their range.
 cudaError_t levels_affine(int rtype, const void *maxima, int n, double a, double b, int lmin,

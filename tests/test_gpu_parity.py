@@ -522,3 +522,55 @@ def test_cavity_d3q19_16bit_full_size_sampled(L, dims, dtype_name, rel_store):
         _, K = o.step_cells(sub + w[:, None, None, None], ((zz * 18 + yy) * 18 + xx).reshape(-1))
         bidx = (bz * nby + by) * nbx + bx
         assert abs(gmax[bidx] - K.max()) / K.max() < 1e-5, (bx, by, bz)
+
+
+# ------------------------------------------------- flag calls: block maxima and flags in one launch
+@pytest.mark.parametrize("q,dims,dtype,block,state", [
+    (19, (48, 40, 32), "F32", 8, "rest"),        # every K is 0: all keys tie
+    (19, (48, 40, 32), "F32", 16, "perturbed"),
+    (19, (48, 40, 32), "F32", 8, "nan"),         # one NaN population: its block's max is NaN
+    (9, (96, 80, 1), "F64", 8, "perturbed"),
+    (9, (2048, 1024, 1), "F32", 8, "perturbed"),  # 32768 blocks: the two-launch fallback
+])
+def test_flag_calls_match_the_flag_builder(L, q, dims, dtype, block, state):
+    """lbm_flag / lbm_flag_top form the block maxima from the tile maxima and the flags in one
+    launch (one CTA with the keys in shared memory for the top fraction).  On the lattice's own
+    block maxima (lbm_sensor_dev) they must equal lbm_flags_from_maxima, the separate flag builder
+    that the oracle tests pin bit for bit: both rules, ties (ordered by block index), NaN blocks,
+    FP32 and FP64 maxima, and a block count above the one-CTA limit."""
+    import torch
+
+    nx, ny, nz = dims
+    lid = (0.0, 0.0) if state == "rest" else (0.1, 0.0)  # at rest with a resting lid K = 0
+    lat = L.Lattice(q, nx, ny, nz, 0.7, dtype=getattr(L, "LBM_" + dtype), lid=lid)
+    if state != "rest":
+        c, w, _ = O.lattice(q)
+        f = w[:, None, None, None] * (1.0 + seeded.relative_perturbation(
+            31 + nx, (q, nz, ny, nx), 0.02))
+        if state == "nan":
+            f[3, nz // 2, ny // 3, nx // 4] = np.nan
+        lat.set_populations(f)
+    L.lbm_set_sensor_every(lat.h, 1)
+    lat.step(1)
+    nb = L.lbm_nblocks(lat.h, block)
+    maxima = torch.empty(nb, dtype=torch.float64, device="cuda")
+    L.lbm_sensor_dev(lat.h, block, maxima)
+    ref = torch.empty(nb, dtype=torch.int8, device="cuda")
+    m = maxima.cpu().numpy()
+    finite = m[np.isfinite(m)]
+    T = float(np.median(finite)) if finite.size else 1.0
+    for rule, param, call in ((L.LBM_FLAG_TOP, 0.1, lat.flag_top), (L.LBM_FLAG_TOP, 0.5, lat.flag_top),
+                              (L.LBM_FLAG_THRESHOLD, T, lat.flag)):
+        got = call(param, block=block)
+        L.lbm_flags_from_maxima(maxima, L.LBM_F64, nb, rule, param, ref)
+        torch.cuda.synchronize()
+        assert np.array_equal(got, ref.cpu().numpy()), (rule, param)
+        if rule == L.LBM_FLAG_TOP:
+            assert int((got == 1).sum()) == int(np.ceil(param * nb))
+    if state == "rest":
+        assert (m == 0).all()
+        top = lat.flag_top(0.1, block=block)
+        assert top[:int(np.ceil(0.1 * nb))].all() and not top[int(np.ceil(0.1 * nb)):].any()
+    if state == "nan":
+        assert np.isnan(m).sum() == 1 and lat.flag_top(0.1, block=block)[np.isnan(m)].all()
+    lat.close()
