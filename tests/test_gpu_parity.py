@@ -360,6 +360,40 @@ def test_kernel_variants_match_oracle(L, dtype, q, dims, periodic):
 
 
 
+@pytest.mark.parametrize("dtype", ["F32", "F16S", "BF16S"])
+@pytest.mark.parametrize("q,dims,periodic", [(19, (2, 5, 4), 0), (19, (2, 4, 5), O.PERIODIC_X),
+                                             (19, (4, 3, 3), O.PERIODIC_X | O.PERIODIC_Z),
+                                             (19, (6, 2, 3), 0), (9, (2, 7, 1), 0),
+                                             (9, (4, 2, 1), O.PERIODIC_X)])
+def test_two_cell_kernel_tiny_lattices(L, dtype, q, dims, periodic):
+    """The two-cell kernel on the smallest lattices it takes: nx = 2 puts both x faces in one
+    lane (the address-select path serves both of its cells), ny or nz below 3 leaves no interior
+    row (every row takes the per-cell gather).  Against the oracle from the same storage-rounded
+    input, within the storage type's tolerance, and against the one-cell kernel."""
+    dt = getattr(L, "LBM_" + dtype)
+    lid = (0.1, 0.0, 0.02 if q == 19 else 0.0)
+    o = O.Oracle(q, *dims, tau=0.6, lid=lid, periodic=periodic)
+    f0 = perturbed(o, seed=91 + q + dims[1], amp=0.02)
+    res = {}
+    for variant in (L.LBM_KERNEL_CELL, L.LBM_KERNEL_PAIR):
+        lat = L.Lattice(q, *dims, 0.6, dtype=dt, lid=(lid[0], lid[2]), periodic=periodic)
+        L.lbm_set_kernel_variant(lat.h, variant)
+        L.lbm_set_sensor_field(lat.h, 1)
+        lat.set_populations(f0)
+        f_in = lat.populations()
+        lat.step(3)
+        res[variant] = (f_in, lat.populations(), lat.sensor_field())
+        lat.close()
+    tol_f, tol_k = STORAGE_TOL[dtype]
+    f_in = res[L.LBM_KERNEL_CELL][0]
+    assert np.array_equal(f_in, res[L.LBM_KERNEL_PAIR][0])
+    f_ref, K = o.run(f_in, 3, sensor_last=True)
+    for variant, (_, f, k) in res.items():
+        assert rel(f, f_ref) < tol_f, variant
+        assert rel(k, K) < tol_k, variant
+    assert rel(res[L.LBM_KERNEL_PAIR][1], res[L.LBM_KERNEL_CELL][1]) < tol_f
+
+
 def test_kernel_variant_applicability(L):
     """A variant that does not apply is refused when it is set (LBM_EINVAL), before any buffer is
     allocated: the two-cell kernel with FP64 storage, an odd nx, or (q + 1) * cells >= 2^32 (its
