@@ -115,6 +115,12 @@ struct Mesh {
     Level lv[MAXL];
     int fusion = 0;  // 0, 1: separate restriction, 2: fused where possible
     int step_form = -1;  // FORM_* forced on every level where it applies, -1: autotuned
+    // a cycle runs level l's work on stream ss[l] (level 0 on the caller's stream, the finer
+    // levels on the mesh's own streams), ordered by events: ev_pre[l] before level l's step,
+    // ev_post[l] after it, ev_done[l] after the restriction onto it
+    cudaStream_t lst[MAXL] = {};
+    cudaEvent_t ev_pre[MAXL] = {}, ev_post[MAXL] = {}, ev_done[MAXL] = {}, ev_join[MAXL] = {};
+    cudaEvent_t ev_fork = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // by level-0 buffer parity
     long long cycles = 0;
 };
@@ -856,34 +862,47 @@ int brick_depth(int n) {
 inline unsigned blocks_for(int n, int t) { return (unsigned)((n + t - 1) / t); }
 
 // One level-l step with its ghost fill at time fraction theta, then the two sub-steps of the finer
-// level and the restriction onto this one.
-int advance(Mesh &m, int l, float theta, cudaStream_t s) {
+// level and the restriction onto this one.  Level l's work goes to stream ss[l].  Dependencies
+// between levels are events: a finer level's first sub-step (theta 0) reads the coarser state
+// from before the coarser step, so its ghost fill and step run beside that step; its second
+// sub-step (theta 1/2) waits for the coarser step; the restriction onto level l waits for the
+// finer level's second sub-step and the restriction onto the finer level.  The coarser level's
+// next step waits for that restriction, which covers every read of the buffer it overwrites.
+int advance(Mesh &m, int l, float theta, cudaStream_t *ss) {
     Level &L = m.lv[l];
     if (L.nslot == 0) return LBM_OK;  // no block reaches this level (nor a finer one)
-    if (l > 0 && L.ninterp) {
-        const Level &C = m.lv[l - 1];
-        const float scale = (float)((L.tau - 1.0) / (2.0 * (C.tau - 1.0)));
-        if (theta > 0.f)
-            k_interp<true><<<blocks_for(L.ninterp, 128), 128, 0, s>>>(
-                L.interps, L.ninterp, L.buf[L.cur], L.G, C.buf[C.cur ^ 1], C.buf[C.cur], C.G,
-                theta, scale);
-        else
-            k_interp<false><<<blocks_for(L.ninterp, 128), 128, 0, s>>>(
-                L.interps, L.ninterp, L.buf[L.cur], L.G, C.buf[C.cur ^ 1], C.buf[C.cur], C.G,
-                theta, scale);
+    cudaStream_t s = ss[l];
+    if (l > 0) {
+        MLCK(cudaStreamWaitEvent(s, theta > 0.f ? m.ev_post[l - 1] : m.ev_pre[l - 1], 0),
+             "cudaStreamWaitEvent");
+        if (L.ninterp) {
+            const Level &C = m.lv[l - 1];
+            const float scale = (float)((L.tau - 1.0) / (2.0 * (C.tau - 1.0)));
+            if (theta > 0.f)
+                k_interp<true><<<blocks_for(L.ninterp, 128), 128, 0, s>>>(
+                    L.interps, L.ninterp, L.buf[L.cur], L.G, C.buf[C.cur ^ 1], C.buf[C.cur], C.G,
+                    theta, scale);
+            else  // the coarser step (enqueued, maybe still running) leaves this buffer unchanged
+                k_interp<false><<<blocks_for(L.ninterp, 128), 128, 0, s>>>(
+                    L.interps, L.ninterp, L.buf[L.cur], L.G, C.buf[C.cur ^ 1], C.buf[C.cur], C.G,
+                    theta, scale);
+        }
     }
     MLCK(cudaGetLastError(), "ghost fill");
     MLCK(cudaMemsetAsync(L.kmax, 0, sizeof(float) * L.nslot, s), "memset(kmax)");
+    MLCK(cudaEventRecord(m.ev_pre[l], s), "cudaEventRecord");
     if (L.fuse && theta > 0.f)  // the second sub-step of the finest level restricts as it steps
         MLCK(launch_step_restrict(m, l, L.fuse_zc, s, L.cur), "level step + restriction");
     else
         MLCK(launch_step(m, l, L.form, L.threads, L.cpt, L.zc, s, L.cur), "level step");
     L.cur ^= 1;
+    MLCK(cudaEventRecord(m.ev_post[l], s), "cudaEventRecord");
     if (l < m.lmax) {
-        int st = advance(m, l + 1, 0.f, s);
-        if (st == LBM_OK) st = advance(m, l + 1, 0.5f, s);
+        int st = advance(m, l + 1, 0.f, ss);
+        if (st == LBM_OK) st = advance(m, l + 1, 0.5f, ss);
         if (st != LBM_OK) return st;
         const Level &F = m.lv[l + 1];
+        if (F.nslot > 0) MLCK(cudaStreamWaitEvent(s, m.ev_done[l + 1], 0), "cudaStreamWaitEvent");
         if (L.nrestrict && !F.fuse) {
             const float scale = (float)(2.0 * (L.tau - 1.0) / (F.tau - 1.0));
             k_restrict<<<blocks_for(L.nrestrict, 128), 128, 0, s>>>(
@@ -892,7 +911,26 @@ int advance(Mesh &m, int l, float theta, cudaStream_t s) {
             MLCK(cudaGetLastError(), "restriction");
         }
     }
+    MLCK(cudaEventRecord(m.ev_done[l], s), "cudaEventRecord");
     return LBM_OK;
+}
+
+// One level-0 cycle on stream s: the finer levels' streams join s at the start and s waits for
+// them at the end.
+int cycle(Mesh &m, cudaStream_t s) {
+    cudaStream_t ss[MAXL];
+    ss[0] = s;
+    MLCK(cudaEventRecord(m.ev_fork, s), "cudaEventRecord");
+    for (int l = 1; l <= m.lmax; ++l) {
+        ss[l] = m.lst[l];
+        MLCK(cudaStreamWaitEvent(ss[l], m.ev_fork, 0), "cudaStreamWaitEvent");
+    }
+    int st = advance(m, 0, 0.f, ss);
+    for (int l = 1; l <= m.lmax; ++l) {
+        MLCK(cudaEventRecord(m.ev_join[l], ss[l]), "cudaEventRecord");
+        MLCK(cudaStreamWaitEvent(s, m.ev_join[l], 0), "cudaStreamWaitEvent");
+    }
+    return st;
 }
 
 // Time each launch shape of the level step once and keep the fastest: the flat kernel with
@@ -971,7 +1009,7 @@ int capture(Mesh &m, cudaGraphExec_t *out) {
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     int st = LBM_OK;
     if (e == cudaSuccess) {
-        st = advance(m, 0, 0.f, cap);
+        st = cycle(m, cap);
         cudaError_t e2 = cudaStreamEndCapture(cap, &g);
         if (e2 != cudaSuccess && st == LBM_OK) st = report_cuda_error(e2, "graph capture");
     } else {
@@ -992,7 +1030,11 @@ void destroy(Mesh *m) {
     if (!m) return;
     for (int k = 0; k < 2; ++k)
         if (m->graph[k]) cudaGraphExecDestroy(m->graph[k]);
+    if (m->ev_fork) cudaEventDestroy(m->ev_fork);
     for (int l = 0; l < MAXL; ++l) {
+        for (cudaEvent_t e : {m->ev_pre[l], m->ev_post[l], m->ev_done[l], m->ev_join[l]})
+            if (e) cudaEventDestroy(e);
+        if (m->lst[l]) cudaStreamDestroy(m->lst[l]);
         Level &L = m->lv[l];
         cudaFree(L.buf[0]);
         cudaFree(L.buf[1]);
@@ -1031,6 +1073,19 @@ int build(Mesh **out, const int nb[3], int edge, int lmax, const int8_t *leaf, d
     m->leaf.assign(leaf, leaf + m->nblk);
     for (int a = 0; a < 3; ++a) m->lid[a] = lid[a];
     m->periodic = periodic;
+    // streams of the finer levels and the events that order a cycle (see advance)
+    bool ok = cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int l = 0; l < MAXL && ok; ++l) {
+        ok = cudaEventCreateWithFlags(&m->ev_pre[l], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&m->ev_post[l], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&m->ev_done[l], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&m->ev_join[l], cudaEventDisableTiming) == cudaSuccess;
+        if (ok && l > 0) ok = cudaStreamCreateWithFlags(&m->lst[l], cudaStreamNonBlocking) == cudaSuccess;
+    }
+    if (!ok) {
+        destroy(m);
+        return report_error(LBM_ECUDA, "cannot create the mesh's streams and events");
+    }
     for (int b = 0; b < m->nblk; ++b)
         if (leaf[b] < 0 || leaf[b] > lmax) {
             destroy(m);
@@ -1109,7 +1164,7 @@ int run_cycles(Mesh *m, int cycles, cudaStream_t s, bool graphs) {
             // a cycle flips level 0 once; finer levels step an even number of times
             m->lv[0].cur ^= 1;
         } else {
-            const int st = advance(*m, 0, 0.f, s);
+            const int st = cycle(*m, s);
             if (st != LBM_OK) return st;
         }
         m->cycles += 1;
