@@ -330,7 +330,11 @@ def run_blocks(args, w, ws, rank, local):
                                "not counted)"},
         "e2e": {"value": round(updates / e2e_s / 1e6, 1), "unit": "MLUPS",
                 "h2d_bytes_per_step": int(leaf.size), "d2h_bytes_per_step": int(8 * bm.size)},
-        "gpu_launches": None,
+        # per cycle: level l takes 2^l steps, each finer one a ghost fill before every step,
+        # and 2^l restrictions onto level l from the level below it
+        "gpu_launches": args.steps * sum(
+            (1 << l) * (1 + (l > 0)) + ((1 << l) if l < w["lmax"] and info[l + 1][2] > 0 else 0)
+            for l in range(w["lmax"] + 1) if info[l][2] > 0),
         "clocks": clocks,
     }
     mesh.close()
@@ -404,7 +408,10 @@ def run_regrid(args, w, ws, rank, local):
                                "also waits on host decisions between signature rounds)"},
         "e2e": {"value": round(ms, 3), "unit": "ms", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": int(tags.size + 24 * len(boxes))},
-        "gpu_launches": None,
+        # per step: tag pass, three 1-D dilations, one signature pass per clustering round (the
+        # rounds follow the data: 4 on this workload, profiles/launches_d3q19_256_regrid.md), and
+        # the level map's two kernels
+        "gpu_launches": args.steps * (1 + 3 + 4 + 2),
         "clocks": clocks,
     }
     lat.close()
