@@ -3,6 +3,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "lbm_internal.h"
 
@@ -674,12 +675,12 @@ cudaError_t flags_from_tiles(int rtype, const void *tiles, int ntx, int nty, int
     if (k <= 0 || k >= nb || (size_t)nb * key_bytes > (size_t)TOP_SMEM_BYTES)
         return flags_top(rtype, blocks, (int)nb, k, out, s);
     // the dynamic shared memory above 48 KB is granted per function and device, once
-    static bool granted[2][64] = {};
+    static std::atomic<bool> granted[2][64] = {};  // setting the attribute twice is harmless
     int dev = 0;
     e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!granted[rtype == 0][dev]) {
+    if (!granted[rtype == 0][dev].load(std::memory_order_acquire)) {
         e = rtype == 0 ? cudaFuncSetAttribute(k_flags_top_keys<double, unsigned long long>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               TOP_SMEM_BYTES)
@@ -687,7 +688,7 @@ cudaError_t flags_from_tiles(int rtype, const void *tiles, int ntx, int nty, int
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               TOP_SMEM_BYTES);
         if (e != cudaSuccess) return e;
-        granted[rtype == 0][dev] = true;
+        granted[rtype == 0][dev].store(true, std::memory_order_release);
     }
     const size_t smem = (size_t)nb * key_bytes;
     if (rtype == 0)
