@@ -275,7 +275,9 @@ def run_blocks(args, w, ws, rank, local):
     leaf = block_placement(w, L)
     tau = tau_of(w)
     form = getattr(L, "LBM_STEP_FORM_" + args.step_form.upper())
-    mesh = L.BlockMesh(leaf, w["block"], w["lmax"], tau, lid=(w["u"], 0.0), step_form=form)
+    fusion = getattr(L, "LBM_FUSION_" + args.fusion.upper())
+    mesh = L.BlockMesh(leaf, w["block"], w["lmax"], tau, lid=(w["u"], 0.0), step_form=form,
+                       fusion=fusion)
     info = [mesh.info(l) for l in range(w["lmax"] + 1)]
     updates = info[0][5]  # cell updates per cycle over all levels
     for _ in range(args.warmup):
@@ -815,6 +817,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel", default="auto", choices=["auto", "cell", "pair", "tma"],
                     help="fused step kernel (default: the library's automatic choice)")
+    ap.add_argument("--fusion", default="auto", choices=["auto", "separate", "fused"],
+                    help="multi-level workload: the finest level's restriction as a separate "
+                         "kernel or fused into its second sub-step (default: the library's)")
     ap.add_argument("--step-form", default="auto",
                     choices=["auto", "flat", "tiled", "select", "pair"],
                     help="multi-level workload: force one form of the level step kernel on the "
