@@ -479,30 +479,48 @@ __global__ void k_levels_affine(const R *m, int n, double a, double b, int lmin,
 template <class R>
 __global__ void __launch_bounds__(256) k_levels_fit(const R *m, int n, int lmin, int lmax,
                                                     int8_t *out) {
-    __shared__ double slo[256], shi[256];
-    double lo = INFINITY, hi = -INFINITY;
+    // smallest and largest positive finite maximum, compared in the maxima's own type (exact: the
+    // conversion to double is monotonic), reduced by warp shuffles
+    __shared__ R slo[8], shi[8];
+    R lo = R(INFINITY), hi = R(-INFINITY);
+#pragma unroll 4
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        const double v = (double)m[k];
-        if (v > 0.0 && isfinite(v)) {
-            lo = fmin(lo, v);
-            hi = fmax(hi, v);
+        const R v = m[k];
+        if (v > R(0) && isfinite(v)) {
+            lo = v < lo ? v : lo;
+            hi = v > hi ? v : hi;
         }
     }
-    slo[threadIdx.x] = lo;
-    shi[threadIdx.x] = hi;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        const R ol = __shfl_xor_sync(0xffffffffu, lo, off), oh = __shfl_xor_sync(0xffffffffu, hi, off);
+        lo = ol < lo ? ol : lo;
+        hi = oh > hi ? oh : hi;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        slo[threadIdx.x >> 5] = lo;
+        shi[threadIdx.x >> 5] = hi;
+    }
     __syncthreads();
-    for (int st = 128; st > 0; st >>= 1) {
-        if (threadIdx.x < st) {
-            slo[threadIdx.x] = fmin(slo[threadIdx.x], slo[threadIdx.x + st]);
-            shi[threadIdx.x] = fmax(shi[threadIdx.x], shi[threadIdx.x + st]);
+    // the fit (two double logarithms and a division) once per CTA, shared with its threads
+    __shared__ double s_a, s_b;
+    __shared__ bool s_scale;
+    if (threadIdx.x == 0) {
+        lo = slo[0];
+        hi = shi[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            lo = slo[w] < lo ? slo[w] : lo;
+            hi = shi[w] > hi ? shi[w] : hi;
         }
-        __syncthreads();
+        const bool any = lo <= hi;
+        const double plo = any ? log2((double)lo) : 0.0, phi = any ? log2((double)hi) : 0.0;
+        s_scale = phi > plo;
+        s_a = s_scale ? (double)(lmax - lmin + 1) / (phi - plo) : 0.0;
+        s_b = s_scale ? (double)lmin - s_a * plo : 0.0;
     }
-    const bool any = slo[0] <= shi[0];
-    const double plo = any ? log2(slo[0]) : 0.0, phi = any ? log2(shi[0]) : 0.0;
-    const bool scale = phi > plo;
-    const double a = scale ? (double)(lmax - lmin + 1) / (phi - plo) : 0.0;
-    const double b = scale ? (double)lmin - a * plo : 0.0;
+    __syncthreads();
+    const bool scale = s_scale;
+    const double a = s_a, b = s_b;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const double v = (double)m[k];
         out[k] = scale ? level_of(v, a, b, lmin, lmax)
