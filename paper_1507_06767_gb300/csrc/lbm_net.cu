@@ -51,41 +51,94 @@ template <>
 __device__ __forceinline__ void store_out<bf16>(bf16 *p, float v) { *p = __float2bfloat16_rn(v); }
 
 // out[b, o, y, x] = bias[o] + sum_{c,i,j} W[o, c, i, j] in[b, c, y+i-1, x+j-1] (ReLU if RELU)
+//
+// One CTA computes FWD_TX consecutive pixels of one row of one batch item.  It stages the
+// 3 x (FWD_TX + 2) input window of every channel in shared memory once (one round of independent
+// loads instead of 9 dependent rounds per channel), with the weights transposed to [c][tap][o] so
+// that a thread reads its output channels' weights as one vector.  Each of the FWD_WARPS warps
+// takes a quarter of the work: COUT / 4 output channels, or, for the one-channel output layer, a
+// quarter of the input channels, whose partial sums are added in a fixed order (deterministic).
+constexpr int FWD_TX = 32;
+constexpr int FWD_WARPS = 4;
+
+template <int N>
+__device__ __forceinline__ void fma_row(const float *__restrict__ wp, float v, float (&acc)[N]) {
+    if constexpr (N == 4) {
+        const float4 w = *reinterpret_cast<const float4 *>(wp);
+        acc[0] = fmaf(w.x, v, acc[0]);
+        acc[1] = fmaf(w.y, v, acc[1]);
+        acc[2] = fmaf(w.z, v, acc[2]);
+        acc[3] = fmaf(w.w, v, acc[3]);
+    } else if constexpr (N == 2) {
+        const float2 w = *reinterpret_cast<const float2 *>(wp);
+        acc[0] = fmaf(w.x, v, acc[0]);
+        acc[1] = fmaf(w.y, v, acc[1]);
+    } else {
+#pragma unroll
+        for (int o = 0; o < N; ++o) acc[o] = fmaf(wp[o], v, acc[o]);
+    }
+}
+
 template <int CIN, int COUT, bool RELU, class OutT>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(FWD_TX * FWD_WARPS)
     k_conv_fwd(const bf16 *__restrict__ in, const bf16 *__restrict__ W, const bf16 *__restrict__ bias,
                int B, int H, int Wd, OutT *__restrict__ out) {
-    __shared__ float ws[COUT * CIN * 9];
-    __shared__ float bs[COUT];
-    for (int k = threadIdx.x; k < COUT * CIN * 9; k += blockDim.x) ws[k] = __bfloat162float(W[k]);
-    for (int k = threadIdx.x; k < COUT; k += blockDim.x) bs[k] = __bfloat162float(bias[k]);
-    __syncthreads();
-    const int hw = H * Wd;
-    const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (pix >= (long long)B * hw) return;
-    const int b = (int)(pix / hw), p = (int)(pix % hw), y = p / Wd, x = p % Wd;
-    float acc[COUT];
-#pragma unroll
-    for (int o = 0; o < COUT; ++o) acc[o] = bs[o];
-    for (int c = 0; c < CIN; ++c) {
-        const bf16 *plane = in + ((size_t)b * CIN + c) * hw;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const int yy = y + i - 1;
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const int xx = x + j - 1;
-                const float v = (yy >= 0 && yy < H && xx >= 0 && xx < Wd)
-                                    ? __bfloat162float(plane[yy * Wd + xx])
-                                    : 0.f;
-#pragma unroll
-                for (int o = 0; o < COUT; ++o) acc[o] = fmaf(ws[(o * CIN + c) * 9 + i * 3 + j], v, acc[o]);
-            }
-        }
+    constexpr bool SPLIT = COUT < FWD_WARPS;
+    static_assert(SPLIT ? (COUT == 1 && CIN % FWD_WARPS == 0) : COUT % FWD_WARPS == 0,
+                  "unsupported layer shape");
+    constexpr int OPT = SPLIT ? 1 : COUT / FWD_WARPS;  // output channels per thread
+    constexpr int CPT = SPLIT ? CIN / FWD_WARPS : CIN;  // input channels per thread
+    constexpr int TW = FWD_TX + 2;
+    __shared__ __align__(16) float ws[CIN * 9 * COUT];
+    __shared__ float xs[CIN][3][TW];
+    __shared__ float part[FWD_WARPS][FWD_TX];
+    const int tiles_x = (Wd + FWD_TX - 1) / FWD_TX;
+    const long long t = blockIdx.x;
+    const int tx = (int)(t % tiles_x), y = (int)((t / tiles_x) % H), b = (int)(t / ((long long)tiles_x * H));
+    const int x0 = tx * FWD_TX;
+    const size_t hw = (size_t)H * Wd;
+    for (int k = threadIdx.x; k < COUT * CIN * 9; k += blockDim.x) {
+        const int o = k / (CIN * 9), r = k % (CIN * 9);  // W is [o][c][tap]
+        ws[r * COUT + o] = __bfloat162float(W[k]);
     }
+    for (int k = threadIdx.x; k < CIN * 3 * TW; k += blockDim.x) {
+        const int c = k / (3 * TW), i = (k / TW) % 3, col = k % TW;
+        const int yy = y + i - 1, xx = x0 + col - 1;
+        xs[c][i][col] = (yy >= 0 && yy < H && xx >= 0 && xx < Wd)
+                            ? __bfloat162float(in[((size_t)b * CIN + c) * hw + (size_t)yy * Wd + xx])
+                            : 0.f;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x % FWD_TX, g = threadIdx.x / FWD_TX;
+    const int x = x0 + lane;
+    const int c0 = SPLIT ? g * CPT : 0, o0 = SPLIT ? 0 : g * OPT;
+    float acc[OPT];
 #pragma unroll
-    for (int o = 0; o < COUT; ++o)
-        store_out<OutT>(out + ((size_t)b * COUT + o) * hw + p, RELU ? fmaxf(acc[o], 0.f) : acc[o]);
+    for (int o = 0; o < OPT; ++o) acc[o] = SPLIT ? 0.f : __bfloat162float(bias[o0 + o]);
+#pragma unroll 4
+    for (int cc = 0; cc < CPT; ++cc) {
+        const int c = c0 + cc;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                fma_row<OPT>(ws + (c * 9 + i * 3 + j) * COUT + o0, xs[c][i][lane + j], acc);
+    }
+    if constexpr (SPLIT) {
+        part[g][lane] = acc[0];
+        __syncthreads();
+        if (g == 0 && x < Wd) {
+            float v = __bfloat162float(bias[0]);
+#pragma unroll
+            for (int k = 0; k < FWD_WARPS; ++k) v += part[k][lane];
+            store_out<OutT>(out + (size_t)b * hw + (size_t)y * Wd + x, RELU ? fmaxf(v, 0.f) : v);
+        }
+    } else if (x < Wd) {
+#pragma unroll
+        for (int o = 0; o < OPT; ++o)
+            store_out<OutT>(out + ((size_t)b * COUT + o0 + o) * hw + (size_t)y * Wd + x,
+                            RELU ? fmaxf(acc[o], 0.f) : acc[o]);
+    }
 }
 
 // dY = 2 (Y - T) / n and per-CTA partial sums of (Y - T)^2 (fixed grid: deterministic)
@@ -327,12 +380,14 @@ int run_forward(lbm_net *n, const float *x, int B, int H, int W, float *y_out) {
     unsigned gn = grid_for((long long)total, NT);
     if (gn > 4096) gn = 4096;
     k_normalise<<<gn, NT, 0, s>>>(x, CI, (size_t)H * W, total, n->norm, n->x0);
-    const unsigned g = grid_for(pos, NT);
-    k_conv_fwd<CI, HD, true, __nv_bfloat16><<<g, NT, 0, s>>>(n->x0, tb + n->off[0], tb + n->off[1],
+    const long long rows = (long long)B * H * ((W + FWD_TX - 1) / FWD_TX);
+    if (rows > 0x7fffffffLL) return lbm::report_error(LBM_EINVAL, "network input too large");
+    const unsigned g = (unsigned)rows, nt = FWD_TX * FWD_WARPS;
+    k_conv_fwd<CI, HD, true, __nv_bfloat16><<<g, nt, 0, s>>>(n->x0, tb + n->off[0], tb + n->off[1],
                                                              B, H, W, n->a1);
-    k_conv_fwd<HD, HD, true, __nv_bfloat16><<<g, NT, 0, s>>>(n->a1, tb + n->off[2], tb + n->off[3],
+    k_conv_fwd<HD, HD, true, __nv_bfloat16><<<g, nt, 0, s>>>(n->a1, tb + n->off[2], tb + n->off[3],
                                                              B, H, W, n->a2);
-    k_conv_fwd<HD, 1, false, float><<<g, NT, 0, s>>>(n->a2, tb + n->off[4], tb + n->off[5], B, H, W,
+    k_conv_fwd<HD, 1, false, float><<<g, nt, 0, s>>>(n->a2, tb + n->off[4], tb + n->off[5], B, H, W,
                                                      y_out);
     NETCK(cudaGetLastError(), "network forward");
     return LBM_OK;
