@@ -97,9 +97,10 @@ def load_peaks():
 
 
 def step_kernel_of(w, variant="auto"):
-    """Name of the fused step kernel the library picks for the workload (LBM_KERNEL_AUTO: the
-    two-cell packed kernel with an even nx and (q + 1) * cells < 2^32 for 16-bit storage, and for
-    FP32 storage on D3Q19 lattices of at least 2^24 cells; else the one-cell kernel) and the
+    """Name of the fused step kernel the library picks for the workload's sensor steps
+    (LBM_KERNEL_AUTO: the two-cell packed kernel with an even nx and (q + 1) * cells < 2^32 for
+    16-bit storage, for FP32 storage on D2Q9 lattices of at least 2^17 cells, and for the FP32
+    sensor steps of D3Q19 lattices of at least 2^24 cells; else the one-cell kernel) and the
     headers that define it."""
     cells = w["n"] ** (3 if w["q"] == 19 else 2)
     pair = ("fused_step_pair_kernel", ("lbm_step_pair.cuh", "lbm_step.cuh", "lbm_traits.cuh"))
@@ -108,9 +109,9 @@ def step_kernel_of(w, variant="auto"):
     if variant == "tma":
         return "fused_step_tma_kernel", ("lbm_step_tma.cuh", "lbm_step.cuh", "lbm_traits.cuh")
     applicable = w["n"] % 2 == 0 and (w["q"] + 1) * cells < 1 << 32
+    fp32_pair = cells >= (1 << 17 if w["q"] == 9 else 1 << 24)
     if variant == "auto" and applicable and (
-            w["dtype"] in ("F16S", "BF16S") or (w["dtype"] == "F32" and w["q"] == 19
-                                                 and cells >= 1 << 24)):
+            w["dtype"] in ("F16S", "BF16S") or (w["dtype"] == "F32" and fp32_pair)):
         return pair
     return "fused_step_kernel", ("lbm_step.cuh", "lbm_traits.cuh")
 
@@ -483,6 +484,7 @@ def run_learned(args, w, ws, rank, local):
     re = 0.5 * (w["re_range"][0] + w["re_range"][1])
     tau = 3.0 * w["u"] * n / re + 0.5
     lat = L.Lattice(L.LBM_D2Q9, n, n, 1, tau, dtype=L.LBM_F32, lid=(w["u"], 0.0))
+    L.lbm_set_kernel_variant(lat.h, getattr(L, "LBM_KERNEL_" + args.kernel.upper()))
     L.lbm_set_sensor_every(lat.h, hz)
     side = n // b
     feats = torch.empty((1, 3, side, side), dtype=torch.float32, device="cuda")
@@ -576,7 +578,7 @@ def run_learned(args, w, ws, rank, local):
                       "regrid_ms": round(regrid_ms, 4), **{k: round(v, 4) for k, v in summary.items()}},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
-                     "kernel": "fused_step_kernel (D2Q9 FP32, 72 B per cell)",
+                     "kernel": step_kernel_of(w, args.kernel)[0] + " (D2Q9 FP32, 72 B per cell)",
                      "kernel_ms": round(avg_kernel_ms, 5),
                      "note": "kernel_ms from a pass with per-launch events, which lengthen a "
                              "~12 us launch; the loop's own time per step bounds it from above",

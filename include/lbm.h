@@ -156,7 +156,8 @@ LBM_API int lbm_set_block(lbm_t *h, int block);
  * lbm_kernel_time); turning it on clears the counters. */
 LBM_API int lbm_set_profiling(lbm_t *h, int on);
 /* Kernel variant of the fused step: LBM_KERNEL_AUTO (default) picks the fastest measured kernel that
- * applies, LBM_KERNEL_CELL forces the one-cell kernel, LBM_KERNEL_PAIR the two-cell kernel with
+ * applies (per lattice, storage, size and step kind: plain steps and sensor steps may differ),
+ * LBM_KERNEL_CELL forces the one-cell kernel, LBM_KERNEL_PAIR the two-cell kernel with
  * packed FP32 arithmetic (storage other than LBM_F64, an even nx and (q + 1) * cells < 2^32),
  * LBM_KERNEL_TMA the kernel that
  * stages the populations through shared memory with TMA copies (D3Q19, storage other than LBM_F64,

@@ -100,15 +100,18 @@ cudaError_t launch_fused_step_tma(const void *fin, void *fout, const StepParams 
 
 cudaError_t step_d3q19(int dtype, const void *fin, void *fout, const StepParams &p, int mode,
                        void *tile_max, void *k_field, cudaStream_t s, int variant) {
-    // automatic choice, from GB300 measurements (sensor steps, D3Q19 cavity): with 16-bit storage
-    // the two-cell kernel at every size measured (128^3 0.046 against 0.064 ms, 256^3 0.249
-    // against 0.367 ms, 512^3 1.91 against 2.83 ms); with FP32 storage the two-cell kernel on
-    // lattices of at least 2^24 cells (256^3 0.388 against 0.398 ms, 512^3 3.03 against 3.11 ms)
-    // and the one-cell kernel below (128^3 0.061 against 0.065 ms); FP64: the one-cell kernel
+    // automatic choice, from GB300 measurements (D3Q19 cavity, two-cell against one-cell time):
+    // with 16-bit storage the two-cell kernel at every size and step kind measured (sensor steps
+    // 128^3 0.046 against 0.057 ms, 256^3 0.247 against 0.370 ms, 512^3 1.89 against 2.86 ms;
+    // plain steps 0.041 / 0.045, 0.236 / 0.310, 1.90 / 2.42 ms); with FP32 storage the two-cell
+    // kernel on the sensor steps of lattices of at least 2^24 cells (256^3 0.389 against 0.395 ms,
+    // 512^3 3.03 against 3.08 ms) and the one-cell kernel on plain steps (256^3 0.380 against
+    // 0.384 ms, 512^3 3.025 against 3.037 ms) and on smaller lattices (128^3 sensor steps 0.060
+    // against 0.066 ms); FP64: the one-cell kernel
     const bool pair_ok = dtype != 0 && pair_applicable<D3Q19>(p);
     const bool big = (long long)p.nx * p.ny * p.nz >= AUTO_PAIR_MIN_CELLS_F32;
     const bool pair = pair_ok && (variant == KERNEL_PAIR ||
-                                  (variant == KERNEL_AUTO && (dtype >= 2 || big)));
+                                  (variant == KERNEL_AUTO && (dtype >= 2 || (big && mode != 0))));
     const bool tma = tma_applicable(dtype, p.nx) && variant == KERNEL_TMA;
     if ((variant == KERNEL_PAIR && !pair_ok) || (variant == KERNEL_TMA && !tma))
         return cudaErrorInvalidValue;
