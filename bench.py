@@ -97,11 +97,10 @@ def load_peaks():
 
 
 def step_kernel_of(w, variant="auto"):
-    """Name of the fused step kernel the library picks for the workload's sensor steps
-    (LBM_KERNEL_AUTO: the two-cell packed kernel with an even nx and (q + 1) * cells < 2^32 for
-    16-bit storage, for FP32 storage on D2Q9 lattices of at least 2^17 cells, and for the FP32
-    sensor steps of D3Q19 lattices of at least 2^24 cells; else the one-cell kernel) and the
-    headers that define it."""
+    """Name of the fused step kernel the library picks for the workload (LBM_KERNEL_AUTO: the
+    two-cell packed kernel with an even nx and (q + 1) * cells < 2^32 for 16-bit storage and for
+    FP32 storage on D2Q9 lattices of at least 2^17 cells; else the one-cell kernel) and the headers
+    that define it."""
     cells = w["n"] ** (3 if w["q"] == 19 else 2)
     pair = ("fused_step_pair_kernel", ("lbm_step_pair.cuh", "lbm_step.cuh", "lbm_traits.cuh"))
     if variant == "pair":
@@ -109,9 +108,9 @@ def step_kernel_of(w, variant="auto"):
     if variant == "tma":
         return "fused_step_tma_kernel", ("lbm_step_tma.cuh", "lbm_step.cuh", "lbm_traits.cuh")
     applicable = w["n"] % 2 == 0 and (w["q"] + 1) * cells < 1 << 32
-    fp32_pair = cells >= (1 << 17 if w["q"] == 9 else 1 << 24)
     if variant == "auto" and applicable and (
-            w["dtype"] in ("F16S", "BF16S") or (w["dtype"] == "F32" and fp32_pair)):
+            w["dtype"] in ("F16S", "BF16S") or (w["dtype"] == "F32" and w["q"] == 9
+                                                 and cells >= 1 << 17)):
         return pair
     return "fused_step_kernel", ("lbm_step.cuh", "lbm_traits.cuh")
 

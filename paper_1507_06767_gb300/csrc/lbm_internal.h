@@ -14,13 +14,10 @@ namespace lbm {
 // Fused step (lbm_step_d2q9.cu / lbm_step_d3q19.cu).  mode: 0 no sensor, 1 tile max, 2 + field.
 // variant: KERNEL_CELL: the one-cell kernel; KERNEL_PAIR: the two-cell packed one; KERNEL_TMA: the
 // TMA-staged one (D3Q19 only); the last two are errors where they do not apply.  KERNEL_AUTO picks
-// the two-cell kernel where it applies (even nx, (q + 1) * cells < 2^32) for 16-bit storage; for
-// FP32 storage on D2Q9 lattices of at least AUTO_PAIR_MIN_CELLS_D2Q9_F32 cells; and for the FP32
-// sensor steps (mode != 0) of D3Q19 lattices of at least AUTO_PAIR_MIN_CELLS_F32 cells (below
-// that its grid is about one wave; plain FP32 D3Q19 steps run about 1 % faster one cell per
-// thread); else the one-cell kernel.  It never picks the TMA kernel, whose tile maxima need a
-// cleared buffer (lbm_step_noalloc relies on this).
-constexpr long long AUTO_PAIR_MIN_CELLS_F32 = 1LL << 24;
+// the two-cell kernel where it applies (even nx, (q + 1) * cells < 2^32) for 16-bit storage and
+// for FP32 storage on D2Q9 lattices of at least AUTO_PAIR_MIN_CELLS_D2Q9_F32 cells, else the
+// one-cell kernel (FP64, FP32 D3Q19, small FP32 D2Q9).  It never picks the TMA kernel, whose tile
+// maxima need a cleared buffer (lbm_step_noalloc relies on this).
 constexpr long long AUTO_PAIR_MIN_CELLS_D2Q9_F32 = 1LL << 17;
 constexpr int KERNEL_AUTO = 0;
 constexpr int KERNEL_CELL = 1;

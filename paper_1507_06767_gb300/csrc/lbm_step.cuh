@@ -203,6 +203,14 @@ __device__ __forceinline__ void gather_xsel(const typename Storage<DT>::T *__res
     }
 }
 
+// Approximate FP32 reciprocal (PTX rcp.approx, max relative error about 1 ulp; inputs here are
+// equilibrium populations, far from zero and from the subnormal range).
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Moments, equilibrium, sensor and BGK collision of one cell from its gathered deviations df;
 // emit(i, d) receives the post-collision deviation d = f*_i - w_i of every population.  Returns
 // the sensor K (MODE != 0).
@@ -237,10 +245,11 @@ __device__ __forceinline__ typename Storage<DT>::R relax_cell(const typename Sto
         const R dfeq = w * (drho + rho * P);  // f^eq_i - w_i
         const R fneq = df[i] - dfeq;
         if (MODE != 0) {
-            const R feq = w * rho * (R(1) + P);
             if constexpr (sizeof(R) == 4) {
-                ksum += __fdividef(fabsf(fneq), feq);
+                // f^eq_i = (f^eq_i - w_i) + w_i: one add, one reciprocal, one fused multiply-add
+                ksum = fmaf(fabsf(fneq), rcp_approx(dfeq + w), ksum);
             } else {
+                const R feq = w * rho * (R(1) + P);
                 ksum += fabs(fneq) / feq;
             }
         }

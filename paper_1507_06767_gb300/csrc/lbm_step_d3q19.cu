@@ -103,15 +103,12 @@ cudaError_t step_d3q19(int dtype, const void *fin, void *fout, const StepParams 
     // automatic choice, from GB300 measurements (D3Q19 cavity, two-cell against one-cell time):
     // with 16-bit storage the two-cell kernel at every size and step kind measured (sensor steps
     // 128^3 0.046 against 0.057 ms, 256^3 0.247 against 0.370 ms, 512^3 1.89 against 2.86 ms;
-    // plain steps 0.041 / 0.045, 0.236 / 0.310, 1.90 / 2.42 ms); with FP32 storage the two-cell
-    // kernel on the sensor steps of lattices of at least 2^24 cells (256^3 0.389 against 0.395 ms,
-    // 512^3 3.03 against 3.08 ms) and the one-cell kernel on plain steps (256^3 0.380 against
-    // 0.384 ms, 512^3 3.025 against 3.037 ms) and on smaller lattices (128^3 sensor steps 0.060
-    // against 0.066 ms); FP64: the one-cell kernel
+    // plain steps 0.041 / 0.045, 0.236 / 0.310, 1.90 / 2.42 ms); with FP32 storage the one-cell
+    // kernel (sensor steps 128^3 0.0644 against 0.0575 ms, 256^3 0.387 against 0.383 ms, 512^3
+    // 3.034 against 3.027 ms; plain steps 0.0607 / 0.0545, 0.385 / 0.379, 3.039 / 3.025 ms);
+    // FP64: the one-cell kernel
     const bool pair_ok = dtype != 0 && pair_applicable<D3Q19>(p);
-    const bool big = (long long)p.nx * p.ny * p.nz >= AUTO_PAIR_MIN_CELLS_F32;
-    const bool pair = pair_ok && (variant == KERNEL_PAIR ||
-                                  (variant == KERNEL_AUTO && (dtype >= 2 || (big && mode != 0))));
+    const bool pair = pair_ok && (variant == KERNEL_PAIR || (variant == KERNEL_AUTO && dtype >= 2));
     const bool tma = tma_applicable(dtype, p.nx) && variant == KERNEL_TMA;
     if ((variant == KERNEL_PAIR && !pair_ok) || (variant == KERNEL_TMA && !tma))
         return cudaErrorInvalidValue;

@@ -103,14 +103,6 @@ struct PairReg<3> {
     }
 };
 
-// Approximate FP32 reciprocal (PTX rcp.approx, max relative error about 1 ulp; inputs here are
-// equilibrium populations, far from zero and from the subnormal range).
-__device__ __forceinline__ float rcp_approx(float x) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
 // Component of velocity i along axis a (0 x, 1 y, 2 z).
 template <class L>
 __host__ __device__ constexpr int comp(int a, int i) {

@@ -35,7 +35,8 @@ def L():
     (19, (40, 36, 33), "F32", 16),
     (9, (70, 45, 1), "F64", 8),
     (19, (24, 16, 20), "BF16S", 8),
-    (19, (256, 256, 256), "F32", 16),  # the benchmark lattice: the two-cell FP32 kernel
+    (19, (256, 256, 256), "F32", 16),  # the benchmark lattice (one-cell FP32 kernel)
+    (9, (512, 384, 1), "F32", 16),  # FP32 D2Q9 above 2^17 cells: the two-cell kernel
 ])
 def test_noalloc_matches_handle_path_two_calls(L, q, dims, dtype, block):
     import torch
