@@ -6,9 +6,10 @@
 // Precision: weights, biases and activations are stored in BF16; every product is accumulated in
 // FP32; the master copy of the parameters, their gradients and the Adam moments are FP32, as are
 // the gradients of the activations and the network output.  The layers are small (at most 16 x 16
-// x 9 weights), so each kernel keeps its weights in shared memory and gives one thread one output
-// pixel (forward, input gradient) or one CTA one (out, in) channel pair (weight gradient, reduced
-// in a fixed order so that a training step is deterministic).
+// x 9 weights), so each kernel keeps its weights in shared memory; the forward pass gives a CTA a
+// row tile of pixels with its input window staged in shared memory, the input gradient one
+// thread one pixel, and the weight gradient one CTA one (out, in) channel pair (reduced in a
+// fixed order so that a training step is deterministic).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
