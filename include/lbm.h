@@ -294,9 +294,13 @@ LBM_API int lbm_kernel_time(lbm_t *h, double *ms_total, long long *launches);
  * without waiting.
  *
  * Limit: at most LBM_NOALLOC_MAX_TILES tiles of 8^d cells (512^3 D3Q19, 4096^2 D2Q9); a larger
- * lattice gets LBM_EINVAL and a message naming the limit.  The first call on a device looks up the
- * array's device address (once per device, with that device current); make that first call before
- * any stream capture on the device.  Calls share the array and it keeps the last call's contents;
+ * lattice gets LBM_EINVAL and a message naming the limit.  The first call in a CUDA context looks
+ * up the array's device address in that context (the calling thread's current one) and caches it
+ * under the context's unique ID; make that first call before any stream capture on the device.  A
+ * context created later on the same device (after cudaDeviceReset, or a caller's own context) gets
+ * its own lookup on its first call, so a stale address is never used.  An error left pending on
+ * the thread by earlier CUDA work is reported (LBM_ECUDA, not cleared) before anything is
+ * launched.  Calls share the array and it keeps the last call's contents;
  * nothing in it needs clearing, since each call writes every tile it reads.  Calls whose kernels
  * overlap on the GPU race on the array: serialise them (one stream per process, or synchronise).
  */

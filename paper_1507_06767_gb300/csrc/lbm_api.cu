@@ -350,6 +350,17 @@ int sync(lbm_t *h) {
         if (!(h)) return fail(LBM_EINVAL, "NULL handle");          \
     } while (0)
 
+// An error left pending on the thread by earlier CUDA work (the caller's or ours) is reported as
+// such before a call launches anything, and is not cleared; otherwise the launch's own status check
+// (cudaGetLastError after the launch) would report, and clear, it as this call's failure.
+#define CHECK_PENDING(where)                                                              \
+    do {                                                                                  \
+        cudaError_t pe_ = cudaPeekAtLastError();                                          \
+        if (pe_ != cudaSuccess)                                                           \
+            return fail(LBM_ECUDA, "error pending before %s (left by earlier CUDA work on " \
+                                   "this thread): %s", (where), cudaGetErrorString(pe_)); \
+    } while (0)
+
 }  // namespace
 
 namespace lbm {
@@ -609,6 +620,7 @@ LBM_API int lbm_reset(lbm_t *h) {
 LBM_API int lbm_step(lbm_t *h, int n) {
     CHECK_H(h);
     if (n < 0) return fail(LBM_EINVAL, "step count must be >= 0 (got %d)", n);
+    CHECK_PENDING("lbm_step");
     int st = ensure_buffers(h);
     if (st != LBM_OK) return st;
     CK(cudaSetDevice(h->device), "cudaSetDevice");
@@ -689,6 +701,7 @@ static int flag_common(lbm_t *h, int rule, double param, int8_t *out, bool host)
     int nbx, nby, nbz, m, mz;
     int st = check_block(h, h->block, &nbx, &nby, &nbz, &m, &mz);
     if (st != LBM_OK) return st;
+    CHECK_PENDING("lbm_flag");
     CK(cudaSetDevice(h->device), "cudaSetDevice");
     const int nb = nbx * nby * nbz;
     int8_t *dst = host ? h->flags : out;
@@ -982,6 +995,7 @@ LBM_API int lbm_blocks_step(lbm_t *h, const lbm_level_batch *batch) {
         (long long)batch->nbz * batch->edge != h->nz)
         return fail(LBM_EINVAL, "block grid x edge must equal the handle's lattice (%d x %d x %d)",
                     h->nx, h->ny, h->nz);
+    CHECK_PENDING("lbm_blocks_step");
     CK(cudaSetDevice(h->device), "cudaSetDevice");
     if (h->mesh && !lbm::ml::same_layout(h->mesh, nb, batch->edge, batch->lmax, batch->leaf)) {
         CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");

@@ -13,6 +13,7 @@
 // contents survive from call to call; nothing in it has to start at zero, because each call writes
 // every tile maximum it later reads.
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 #include <math.h>
 #include <stdio.h>
 
@@ -26,23 +27,94 @@ namespace {
 // tile maxima (first half) and block maxima (second half), as doubles or floats
 static __device__ __align__(256) double g_noalloc_scratch[2 * LBM_NOALLOC_MAX_TILES];
 
-constexpr int kMaxDevices = 64;
+// The device address of the array is a property of the CUDA context the module is loaded in, not
+// of the device ordinal: after cudaDeviceReset, or under a caller's own (non-primary) context, the
+// same ordinal has a new context and a new address.  Addresses are therefore cached per context,
+// keyed by the driver's context ID, which is unique over the life of the process (a context created
+// after a reset never reuses the ID of the one it replaces).
+constexpr int kMaxContexts = 64;
+struct Entry {
+    unsigned long long ctx_id;
+    void *addr;
+};
 std::mutex g_mu;
-void *g_scratch_addr[kMaxDevices] = {};
+Entry g_cache[kMaxContexts] = {};
+int g_cache_used = 0;
+int g_cache_next = 0;  // next slot to overwrite once the table is full
 
-// Device address of the scratch array on the current device.  The host-side name of the array is
-// only a stand-in; its device address is looked up once per device, with that device current.
-int scratch_address(int dev, void **out) {
-    if (dev < 0 || dev >= kMaxDevices)
-        return lbm::report_error(LBM_EINVAL, "device ordinal out of range for lbm_step_noalloc");
+struct DriverFns {
+    PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+    PFN_cuCtxGetId_v12000 get_id = nullptr;
+};
+
+const DriverFns &driver_fns() {
+    static DriverFns fns;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fns.get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fns.get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(f);
+    });
+    return fns;
+}
+
+// ID of the calling thread's current context (0 if there is none yet).
+int current_context_id(unsigned long long *id) {
+    const DriverFns &fns = driver_fns();
+    if (!fns.get_current || !fns.get_id)
+        return lbm::report_error(LBM_ECUDA, "driver entry points cuCtxGetCurrent / cuCtxGetId "
+                                            "unavailable");
+    CUcontext ctx = nullptr;
+    if (fns.get_current(&ctx) != CUDA_SUCCESS)
+        return lbm::report_error(LBM_ECUDA, "cuCtxGetCurrent failed");
+    *id = 0;
+    if (ctx && fns.get_id(ctx, id) != CUDA_SUCCESS)
+        return lbm::report_error(LBM_ECUDA, "cuCtxGetId failed");
+    return LBM_OK;
+}
+
+// Device address of the scratch array in the calling thread's current context.  The host-side
+// name of the array is only a stand-in; its device address is looked up with cudaGetSymbolAddress
+// the first time a context calls, and cached under that context's ID.
+int scratch_address(void **out) {
+    unsigned long long id = 0;
+    int st = current_context_id(&id);
+    if (st != LBM_OK) return st;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) return lbm::report_cuda_error(e, "cudaGetSymbolAddress");
-        g_scratch_addr[dev] = p;
+    if (id != 0)
+        for (int k = 0; k < g_cache_used; ++k)
+            if (g_cache[k].ctx_id == id) {
+                *out = g_cache[k].addr;
+                return LBM_OK;
+            }
+    // first call in this context (or no context yet: the lookup makes the device's primary
+    // context current, and its ID is read afterwards)
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return lbm::report_cuda_error(e, "cudaGetSymbolAddress");
+    if (id == 0) {
+        st = current_context_id(&id);
+        if (st != LBM_OK) return st;
     }
-    *out = g_scratch_addr[dev];
+    if (id != 0) {
+        int slot;
+        if (g_cache_used < kMaxContexts) {
+            slot = g_cache_used++;
+        } else {  // full: replace the oldest entry
+            slot = g_cache_next;
+            g_cache_next = (g_cache_next + 1) % kMaxContexts;
+        }
+        g_cache[slot] = Entry{id, p};
+    }
+    *out = p;
     return LBM_OK;
 }
 
@@ -81,11 +153,12 @@ extern "C" LBM_API int lbm_step_noalloc(int lattice, int dtype, int nx, int ny, 
                  "(LBM_NOALLOC_MAX_TILES)", ntiles, LBM_NOALLOC_MAX_TILES);
         return lbm::report_error(LBM_EINVAL, msg);
     }
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return lbm::report_cuda_error(e, "cudaGetDevice");
+    // an error left pending by earlier work on this thread is reported as such, not as this
+    // call's launch failure
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) return lbm::report_cuda_error(e, "error pending before lbm_step_noalloc");
     void *scratch = nullptr;
-    int st = scratch_address(dev, &scratch);
+    int st = scratch_address(&scratch);
     if (st != LBM_OK) return st;
     double *tiles = static_cast<double *>(scratch);
     double *blocks = tiles + LBM_NOALLOC_MAX_TILES;

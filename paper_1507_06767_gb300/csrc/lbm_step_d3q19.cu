@@ -64,13 +64,20 @@ cudaError_t launch_tma_mode(const CUtensorMap &main_map, const CUtensorMap &halo
                             void *k_field, cudaStream_t s) {
     using T = typename Storage<DT>::T;
     using C = TmaCfg<DT>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(fused_step_tma_kernel<DT, MODE>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             C::SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        attr = true;
+    // the shared-memory opt-in is a per-device attribute of the kernel: set once per device
+    static std::mutex mu;
+    static bool attr[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (dev < 0 || dev >= 64 || !attr[dev]) {
+            e = cudaFuncSetAttribute(fused_step_tma_kernel<DT, MODE>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
+            if (e != cudaSuccess) return e;
+            if (dev >= 0 && dev < 64) attr[dev] = true;
+        }
     }
     const long long units = (long long)((p.nx + TMA_CHUNK - 1) / TMA_CHUNK) * p.ny *
                             ((p.nz + TMA_UNIT_Z - 1) / TMA_UNIT_Z);
