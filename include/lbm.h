@@ -489,6 +489,28 @@ LBM_API int lbm_net_log_targets(const double *kmax_dev, long long n, float offse
                                 float *t_dev, void *stream);
 LBM_API int lbm_net_to_maxima(const float *y_dev, long long n, float offset, double *kmax_dev,
                               void *stream);
+/*
+ * Intermediate buffers of the last lbm_net_forward / lbm_net_backward call, copied to host memory
+ * (synchronises): for inspection and for checking each layer on its own.  `which`:
+ *   LBM_NET_BUF_PARAMS_BF16  the BF16 parameters the kernels read (lbm_net_param_count values);
+ *   LBM_NET_BUF_X0           the normalised BF16 input, [batch][cin][h][w];
+ *   LBM_NET_BUF_A1 / _A2     the BF16 activations after the first / second ReLU, [batch][hidden][h][w];
+ *   LBM_NET_BUF_Y            the FP32 output of the last backward call, [batch][h][w];
+ *   LBM_NET_BUF_DY           dL/dY (FP32) of the last backward call, [batch][h][w];
+ *   LBM_NET_BUF_DZ2 / _DZ1   dL/dZ (FP32) of the second / first convolution's output, masked by
+ *                            its ReLU, [batch][hidden][h][w].
+ * bytes must equal the buffer's size for the shape of the last call (BF16: 2 bytes per value,
+ * FP32: 4); LBM_EINVAL otherwise, LBM_ESTATE before the first forward pass.
+ */
+#define LBM_NET_BUF_PARAMS_BF16 0
+#define LBM_NET_BUF_X0 1
+#define LBM_NET_BUF_A1 2
+#define LBM_NET_BUF_A2 3
+#define LBM_NET_BUF_Y 4
+#define LBM_NET_BUF_DY 5
+#define LBM_NET_BUF_DZ2 6
+#define LBM_NET_BUF_DZ1 7
+LBM_API int lbm_net_get_buffer(lbm_net *n, int which, void *out_host, size_t bytes);
 
 #ifdef __cplusplus
 }

@@ -315,6 +315,7 @@ struct lbm_net_s {
     __nv_bfloat16 *x0 = nullptr, *a1 = nullptr, *a2 = nullptr;
     float *y = nullptr, *dy = nullptr, *dz1 = nullptr, *dz2 = nullptr;
     double *loss_part = nullptr, *loss_dev = nullptr;
+    long long last_pos = 0;  // positions of the last forward / backward call (0: none yet)
 };
 
 namespace {
@@ -568,6 +569,7 @@ LBM_API int lbm_net_forward(lbm_net *n, const float *x_dev, int batch, int h, in
     st = ensure_acts(n, (long long)batch * h * w);
     if (st != LBM_OK) return st;
     NET_DISPATCH(n->cin, n->hid, (st = run_forward<CI, HD>(n, x_dev, batch, h, w, y_dev)));
+    if (st == LBM_OK) n->last_pos = (long long)batch * h * w;
     return st;
 }
 
@@ -581,12 +583,42 @@ LBM_API int lbm_net_backward(lbm_net *n, const float *x_dev, const float *target
     if (st != LBM_OK) return st;
     NET_DISPATCH(n->cin, n->hid, (st = run_backward<CI, HD>(n, x_dev, target_dev, batch, h, w)));
     if (st != LBM_OK) return st;
+    n->last_pos = (long long)batch * h * w;
     if (loss_host) {
         NETCK(cudaMemcpyAsync(loss_host, n->loss_dev, sizeof(double), cudaMemcpyDeviceToHost,
                               n->stream),
               "loss download");
         NETCK(cudaStreamSynchronize(n->stream), "lbm_net_backward");
     }
+    return LBM_OK;
+}
+
+LBM_API int lbm_net_get_buffer(lbm_net *n, int which, void *out_host, size_t bytes) {
+    CHECK_NET(n);
+    if (!out_host) return lbm::report_error(LBM_EINVAL, "NULL output");
+    const size_t P = (size_t)n->last_pos;
+    const void *src = nullptr;
+    size_t need = 0;
+    switch (which) {
+        case LBM_NET_BUF_PARAMS_BF16:
+            src = n->theta_b;
+            need = (size_t)n->nparam * sizeof(__nv_bfloat16);
+            break;
+        case LBM_NET_BUF_X0: src = n->x0; need = P * n->cin * sizeof(__nv_bfloat16); break;
+        case LBM_NET_BUF_A1: src = n->a1; need = P * n->hid * sizeof(__nv_bfloat16); break;
+        case LBM_NET_BUF_A2: src = n->a2; need = P * n->hid * sizeof(__nv_bfloat16); break;
+        case LBM_NET_BUF_Y: src = n->y; need = P * sizeof(float); break;
+        case LBM_NET_BUF_DY: src = n->dy; need = P * sizeof(float); break;
+        case LBM_NET_BUF_DZ2: src = n->dz2; need = P * n->hid * sizeof(float); break;
+        case LBM_NET_BUF_DZ1: src = n->dz1; need = P * n->hid * sizeof(float); break;
+        default: return lbm::report_error(LBM_EINVAL, "unknown network buffer");
+    }
+    if (which != LBM_NET_BUF_PARAMS_BF16 && n->last_pos == 0)
+        return lbm::report_error(LBM_ESTATE, "no forward or backward pass yet");
+    if (bytes != need) return lbm::report_error(LBM_EINVAL, "bytes must equal the buffer's size");
+    NETCK(cudaMemcpyAsync(out_host, src, need, cudaMemcpyDeviceToHost, n->stream),
+          "buffer download");
+    NETCK(cudaStreamSynchronize(n->stream), "lbm_net_get_buffer");
     return LBM_OK;
 }
 

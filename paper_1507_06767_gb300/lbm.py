@@ -113,6 +113,7 @@ _SIGS = {
     "lbm_net_train_step": (_i, [_vp, _vp, _vp, _i, _i, _i, ctypes.c_float, _dp]),
     "lbm_net_log_targets": (_i, [_vp, _ll, ctypes.c_float, ctypes.c_float, _vp, _vp]),
     "lbm_net_to_maxima": (_i, [_vp, _ll, ctypes.c_float, _vp, _vp]),
+    "lbm_net_get_buffer": (_i, [_vp, _i, _vp, _sz]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -429,6 +430,12 @@ def lbm_net_get_grads(n, host) -> int:
     return _ck(_lib.lbm_net_get_grads(n, _ptr(host)), "lbm_net_get_grads")
 
 
+def lbm_net_get_buffer(n, which: int, out) -> int:
+    """Copy an intermediate buffer of the last forward / backward pass into the numpy array `out`
+    (uint16 holding BF16 bits for the BF16 buffers, float32 otherwise)."""
+    return _ck(_lib.lbm_net_get_buffer(n, int(which), _ptr(out), out.nbytes), "lbm_net_get_buffer")
+
+
 def lbm_net_set_grads(n, host) -> int:
     return _ck(_lib.lbm_net_set_grads(n, _ptr(host)), "lbm_net_set_grads")
 
@@ -509,6 +516,15 @@ class Net:
 
     def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
         _ck(_lib.lbm_net_adam(self.n, lr, beta1, beta2, eps), "lbm_net_adam")
+
+    def buffer(self, which, shape):
+        """An intermediate buffer of the last pass (lbm_net_get_buffer): BF16 buffers come back
+        as uint16 arrays of their bits, FP32 ones as float32 arrays of the given shape."""
+        bf16 = which in (LBM_NET_BUF_PARAMS_BF16, LBM_NET_BUF_X0, LBM_NET_BUF_A1,
+                         LBM_NET_BUF_A2)
+        out = np.empty(shape, dtype=np.uint16 if bf16 else np.float32)
+        lbm_net_get_buffer(self.n, which, out)
+        return out
 
     def train_step(self, x, t, lr, sync=True):
         b, c, hh, ww = x.shape
