@@ -160,16 +160,21 @@ def nvtx_pop():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle samples of this process's GPU during the timed region."""
+    """nvidia-smi clock / throttle samples of this process's GPU.  Each sample carries nvidia-smi's
+    own timestamp, so samples can be assigned to the timed windows (``window``) even when the
+    pipe delivers them late; the statistics cover the samples inside a window ("under load"), or
+    every sample when no window was marked."""
 
-    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, uuid):
         self.uuid = uuid
         self.proc = None
         self.lines = []
+        self.windows = []
 
     def start(self):
         try:
@@ -185,6 +190,41 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def window(self, t0, t1):
+        """Mark [t0, t1] (time.time() seconds) as a timed window."""
+        self.windows.append((t0, t1))
+
+    @staticmethod
+    def _stamp(text):
+        import datetime
+
+        try:
+            return datetime.datetime.strptime(text, "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
+    def parse(self):
+        """Samples of this GPU as (time, sm MHz, max MHz, power W, set of active reasons)."""
+        out = []
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 10:
+                continue
+            if self.uuid and parts[1] != self.uuid:
+                continue
+            try:
+                sm, mx = float(parts[2]), float(parts[3])
+            except ValueError:
+                continue
+            try:
+                pw = float(parts[4])
+            except ValueError:
+                pw = None
+            reasons = {name for name, val in zip(self.REASONS, parts[6:10])
+                       if val.lower() == "active"}
+            out.append((self._stamp(parts[0]), sm, mx, pw, reasons))
+        return out
+
     def stop(self):
         if not self.proc:
             return None
@@ -194,25 +234,28 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.thread.join(timeout=2)
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
-                continue
-            if self.uuid and parts[0] != self.uuid:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
-            except ValueError:
-                continue
-            for name, val in zip(names, parts[5:9]):
-                if val.lower() == "active":
-                    reasons.add(name)
-        if not sm:
+        samples = self.parse()
+        if not samples:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+        if self.windows:
+            load = [sm for sm in samples if sm[0] is not None and
+                    any(t0 <= sm[0] <= t1 for t0, t1 in self.windows)]
+        else:
+            load = samples
+        use = load if load else samples
+        bins = {}
+        for sm in use:
+            key = str(int(round(sm[1])))
+            bins[key] = bins.get(key, 0) + 1
+        reasons = set()
+        for sm in use:
+            reasons |= sm[4]
+        powers = [sm[3] for sm in use if sm[3] is not None]
+        return {"sm_mhz": statistics.median(sm[1] for sm in use),
+                "sm_max_mhz": max(sm[2] for sm in samples), "samples": len(samples),
+                "samples_under_load": len(load),
+                "sm_mhz_bins": dict(sorted(bins.items(), key=lambda kv: -int(kv[0]))),
+                "power_w_max": max(powers) if powers else None,
                 "reasons": sorted(reasons)}
 
 
@@ -306,17 +349,9 @@ def run_blocks(args, w, ws, rank, local):
     sampler = ClockSampler(None)
     sampler.start()
     time.sleep(0.3)
-    barrier(ws)
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    mesh.step(args.steps)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    barrier(ws)
+    reps = timed_repeats(lambda: mesh.step(args.steps), stream, ws, sampler, args.min_time)
     clocks = sampler.stop()
-    ms = reduce_max(ev0.elapsed_time(ev1), ws)
+    ms = reduce_max(statistics.median(reps), ws)  # one repeat of args.steps cycles
     value = updates * args.steps * ws / (ms / 1e3) / 1e6
     # N_eff (Sec. 5.2): cells weighted by their update frequency, sum_l n_l / 2^(L - l) over the
     # leaf cells
@@ -344,6 +379,8 @@ def run_blocks(args, w, ws, rank, local):
                                               mesh.schedule(l))) for l in range(w["lmax"] + 1)],
                    "cell_updates_per_cycle": updates, "n_eff": n_eff,
                    "uniform_finest_cells": w["n"] ** 3, "step": "one level-0 cycle (graph)",
+                   "timing": (f"{len(reps)} repeats of {args.steps} cycles (>= {args.min_time} s of "
+                              "device time), median"),
                    "l2": "level buffers > 129 MB L2, no flush"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
@@ -353,7 +390,8 @@ def run_blocks(args, w, ws, rank, local):
                 "h2d_bytes_per_step": int(leaf.size), "d2h_bytes_per_step": int(8 * bm.size)},
         # per cycle: level l takes 2^l steps, each finer one a ghost fill before every step,
         # and 2^l restrictions onto level l from the level below it
-        "gpu_launches": args.steps * sum(
+        "repeats": len(reps),
+        "gpu_launches": len(reps) * args.steps * sum(
             (1 << l) * (1 + (l > 0)) + ((1 << l) if l < w["lmax"] and info[l + 1][2] > 0 else 0)
             for l in range(w["lmax"] + 1) if info[l][2] > 0),
         "clocks": clocks,
@@ -590,8 +628,178 @@ def run_learned(args, w, ws, rank, local):
 
 
 # ----------------------------------------------------------------------------------- our arm
-def run_ours(args, w, ws, rank, local):
+# Device time the timed region accumulates: the loop of --steps steps is repeated until at least
+# this much device time has passed, and the per-step time is the median over the repeats.
+MIN_TIMED_S = 1.5
+# mixed-precision row: the 512^3 cavity in each storage type, and the error check at 128^3
+MIXED_WORKLOADS = ("d3q19_512_fp32_re1000", "d3q19_512_f16s_re1000", "d3q19_512_bf16s_re1000")
+MIXED_ERROR = dict(n=128, steps=5000, re=1000.0, u=0.1, block=16)
+
+
+def timed_repeats(run_k, stream, ws, sampler, min_s=MIN_TIMED_S):
+    """Run ``run_k()`` (one repeat of the timed steps) until ``min_s`` seconds of device time have
+    accumulated.  The first repeat is timed alone to size the rest, which are queued back to back
+    (an event pair around each, one synchronisation at the end) so the GPU never idles between
+    them.  Returns the per-repeat milliseconds."""
+    import torch
+
+    barrier(ws)
+    torch.cuda.synchronize()
+    t_start = time.time()
+
+    def pair():
+        return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    e0, e1 = pair()
+    e0.record(stream)
+    run_k()
+    e1.record(stream)
+    e1.synchronize()
+    first = e0.elapsed_time(e1)
+    reps = max(0, math.ceil(min_s * 1e3 / max(first, 1e-3)) - 1)
+    evs = []
+    for _ in range(reps):
+        a, b = pair()
+        a.record(stream)
+        run_k()
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    sampler.window(t_start, time.time())
+    barrier(ws)
+    return [first] + [a.elapsed_time(b) for a, b in evs]
+
+
+def time_uniform(L, w, args, ws, sampler, kernel="auto", min_s=MIN_TIMED_S):
+    """Time the uniform-lattice workload ``w``: one bench step = one fused step (sensor on its
+    sensor steps) + the block-max / flag kernels.  Returns the open lattice, its flag closure and
+    the timing record."""
+    import torch
+
+    q, n = w["q"], w["n"]
+    nz = n if q == 19 else 1
+    tau = tau_of(w)
+    lat = L.Lattice(q, n, n, nz, tau, dtype=getattr(L, "LBM_" + w["dtype"]), lid=(w["u"], 0.0))
+    h = lat.h
+    L.lbm_set_kernel_variant(h, getattr(L, "LBM_KERNEL_" + kernel.upper()))
+    L.lbm_set_sensor_every(h, w["sensor_every"])
+    lat.block = w["block"]
+    nb = L.lbm_nblocks(h, w["block"])
+    flags_dev = torch.empty(nb, dtype=torch.int8, device="cuda")
+    param = w["param"] if w["rule"] == "top" else threshold_of(w)
+    flag_dev = L.lbm_flag_top_dev if w["rule"] == "top" else L.lbm_flag_dev
+
+    def one_step():
+        L.lbm_step(h, 1)
+        if w["sensor_every"] == 1 or L.lbm_steps_done(h) % w["sensor_every"] == 0:
+            flag_dev(h, param, flags_dev)
+
+    def run_k():
+        for _ in range(args.steps):
+            one_step()
+
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    L.lbm_set_profiling(h, 1)
+    reps = timed_repeats(run_k, stream, ws, sampler, min_s)
+    k_ms, k_n = L.lbm_kernel_time(h)
+    L.lbm_set_profiling(h, 0)
+    per_step = sorted(r / args.steps for r in reps)
+    ms_step = reduce_max(statistics.median(per_step), ws)
+    cells = cells_of(w)
+    peak, peak_kind = load_peaks()
+    per_launch_bytes = algorithmic_bytes_per_cell(w) * cells
+    avg_kernel_ms = k_ms / max(k_n, 1)
+    achieved = per_launch_bytes / (avg_kernel_ms / 1e3) / 1e9
+    rec = {
+        "value": cells * ws / (ms_step / 1e3) / 1e6, "ms_per_step": ms_step,
+        "repeats": len(reps), "timed_steps": len(reps) * args.steps,
+        "ms_per_step_min_max": [per_step[0], per_step[-1]],
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4),
+                     "traffic": recorded_traffic(w["name"], w, kernel),
+                     "peak_kind": peak_kind, "kernel": step_kernel_of(w, kernel)[0],
+                     "kernel_ms": round(avg_kernel_ms, 5),
+                     "algorithmic_bytes_per_launch": per_launch_bytes},
+        "nbytes": L.lbm_population_bytes(h), "nb": nb, "param": param, "tau": tau,
+        "n_sensor_per_repeat": args.steps // w["sensor_every"],
+    }
+    return lat, flag_dev, rec
+
+
+def mixed_error_block(L):
+    """Error of each storage type against the library's FP64 path (which the parity tests hold to
+    the FP64 oracle within 1e-12) on the 128^3 Re 1000 cavity after 5000 steps, sensor on the last
+    step: populations, density, velocity, per-cell sensor, 16^3 block maxima, flag agreement."""
     import numpy as np
+
+    e = MIXED_ERROR
+    n, u = e["n"], e["u"]
+    tau = 3.0 * u * n / e["re"] + 0.5
+    T = 4.0 * (4.0 / 3.0) * tau * u / n
+    res = {}
+    for name in ("F64", "F32", "F16S", "BF16S"):
+        lat = L.Lattice(19, n, n, n, tau, dtype=getattr(L, "LBM_" + name), lid=(u, 0.0))
+        L.lbm_set_sensor_field(lat.h, 1)
+        lat.step(e["steps"])
+        rho, uu = lat.moments()
+        res[name] = dict(f=lat.populations(), rho=rho, u=uu, K=lat.sensor_field(),
+                         bmax=lat.sensor(e["block"]), top=lat.flag_top(0.1, block=e["block"]),
+                         thr=lat.flag(T, block=e["block"]))
+        lat.close()
+    ref = res["F64"]
+    out = {"lattice": f"D3Q19 {n}^3 cavity", "re": e["re"], "tau": round(tau, 6),
+           "steps": e["steps"], "against": "the library's FP64 storage path",
+           "umax": float(np.abs(ref["u"]).max()), "Kmax": float(ref["K"].max())}
+    for name in ("F32", "F16S", "BF16S"):
+        g = res[name]
+        out[name.lower()] = {
+            "f_rel": float(np.abs(g["f"] - ref["f"]).max() / np.abs(ref["f"]).max()),
+            "rho_abs": float(np.abs(g["rho"] - ref["rho"]).max()),
+            "u_rel": float(np.abs(g["u"] - ref["u"]).max() / np.abs(ref["u"]).max()),
+            "K_rel": float(np.abs(g["K"] - ref["K"]).max() / ref["K"].max()),
+            "K_blockmax_rel": float(np.abs(g["bmax"] - ref["bmax"]).max() / ref["bmax"].max()),
+            "top10_flags_agree": float((g["top"] == ref["top"]).mean()),
+            "threshold_flags_agree": float((g["thr"] == ref["thr"]).mean()),
+        }
+    return out
+
+
+def run_mixed(args, ws, uuid):
+    """Mixed-precision half of the metric: the 512^3 D3Q19 Re 1000 cavity stored in FP32, FP16
+    (f - w_i) and BF16 (f - w_i), each timed like the headline workload, plus the live error
+    check of the storage types."""
+    import torch
+
+    import paper_1507_06767_gb300 as L
+
+    out = {"workload": "d3q19_512_re1000", "cells": 512 ** 3}
+    sampler = ClockSampler(uuid)
+    sampler.start()
+    time.sleep(0.3)
+    fp32 = None
+    for name in MIXED_WORKLOADS:
+        w = dict(WORKLOADS[name], name=name)
+        lat, _, rec = time_uniform(L, w, args, ws, sampler, min_s=min(1.0, args.min_time))
+        lat.close()
+        torch.cuda.synchronize()
+        key = w["dtype"].lower()
+        entry = {"value": round(rec["value"], 1), "unit": "MLUPS",
+                 "ms_per_step": round(rec["ms_per_step"], 5), "repeats": rec["repeats"],
+                 "dtype": DTYPE_NAME[w["dtype"]], "roofline": rec["roofline"]}
+        if fp32 is None:
+            fp32 = rec["value"]
+        else:
+            entry["ratio_to_fp32"] = round(rec["value"] / fp32, 4)
+        out[key] = entry
+    out["clocks"] = sampler.stop()
+    out["error_vs_f64"] = mixed_error_block(L)
+    return out
+
+
+def run_ours(args, w, ws, rank, local):
     import torch
 
     import paper_1507_06767_gb300 as L
@@ -600,68 +808,32 @@ def run_ours(args, w, ws, rank, local):
     dev_props = torch.cuda.get_device_properties(local)
     uuid = getattr(dev_props, "uuid", None)
     uuid = f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else uuid
+    w = dict(w, name=args.workload)
     q, n = w["q"], w["n"]
-    nz = n if q == 19 else 1
-    tau = tau_of(w)
-    dtype = getattr(L, "LBM_" + w["dtype"])
-    lat = L.Lattice(q, n, n, nz, tau, dtype=dtype, lid=(w["u"], 0.0))
-    h = lat.h
-    L.lbm_set_kernel_variant(h, getattr(L, "LBM_KERNEL_" + args.kernel.upper()))
-    L.lbm_set_sensor_every(h, w["sensor_every"])
-    lat.block = w["block"]
-    nb = L.lbm_nblocks(h, w["block"])
-    flags_dev = torch.empty(nb, dtype=torch.int8, device="cuda")
-    param = w["param"] if w["rule"] == "top" else threshold_of(w)
     cells = cells_of(w)
 
-    def one_step():
-        L.lbm_step(h, 1)
-        if w["sensor_every"] == 1 or L.lbm_steps_done(h) % w["sensor_every"] == 0:
-            if w["rule"] == "top":
-                L.lbm_flag_top_dev(h, param, flags_dev)
-            else:
-                L.lbm_flag_dev(h, param, flags_dev)
-
-    stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
-        one_step()
-    torch.cuda.synchronize()
-
-    # ---- device-resident timed region
-    L.lbm_set_profiling(h, 1)
+    # ---- device-resident timed region: repeats of --steps steps, >= MIN_TIMED_S of device time
     sampler = ClockSampler(uuid)
     sampler.start()
     time.sleep(0.3)
-    barrier(ws)
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        one_step()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    barrier(ws)
+    lat, flag_dev, rec = time_uniform(L, w, args, ws, sampler, kernel=args.kernel,
+                                      min_s=args.min_time)
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
-    k_ms, k_n = L.lbm_kernel_time(h)
-    L.lbm_set_profiling(h, 0)
-    ms_max = reduce_max(ms, ws)
-    value = cells * args.steps * ws / (ms_max / 1e3) / 1e6
+    h = lat.h
+    nb, param, nbytes = rec["nb"], rec["param"], rec["nbytes"]
+    stream = torch.cuda.current_stream()
 
-    # ---- end to end through the C ABI with host buffers: the job's initial state goes up from
-    # pinned host memory, every sensor step's flags come back to pinned host memory, the final
-    # state comes back.  The flags of a step are copied while the next step runs (two flag
-    # buffers); the host waits for step k's flags after launching step k + 1, as a driver that
-    # regrids from them would.
-    nbytes = L.lbm_population_bytes(h)
+    # ---- end to end through the C ABI with host buffers, one job of as many steps as the timed
+    # region ran: the job's initial state goes up from pinned host memory, every sensor step's
+    # flags come back to pinned host memory, the final state comes back.  The flags of a step are
+    # copied while the next step runs (two flag buffers); the host waits for step k's flags after
+    # launching step k + 1, as a driver that regrids from them would.
     host_state = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
     L.lbm_get_raw(h, host_state.data_ptr(), nbytes)
     host_flags = [torch.empty(nb, dtype=torch.int8, pin_memory=True) for _ in range(2)]
     dev_flags = [torch.empty(nb, dtype=torch.int8, device="cuda") for _ in range(2)]
     flag_ready = [torch.cuda.Event() for _ in range(2)]
-    flag_dev = L.lbm_flag_top_dev if w["rule"] == "top" else L.lbm_flag_dev
-    e2e_steps = args.steps
+    e2e_steps = rec["timed_steps"]
     barrier(ws)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -686,55 +858,53 @@ def run_ours(args, w, ws, rank, local):
     t_down = t2 - t1
     e2e_s = reduce_max(t2 - t0, ws)
     barrier(ws)
+    lat.close()
+    del host_state
+    torch.cuda.synchronize()
     n_flag_reads = e2e_steps // w["sensor_every"]
     e2e = {"value": round(cells * e2e_steps * ws / e2e_s / 1e6, 1), "unit": "MLUPS",
            "h2d_bytes_per_step": int(round(nbytes / e2e_steps)),
            "d2h_bytes_per_step": int(round((nbytes + n_flag_reads * nb) / e2e_steps)),
+           "job_steps": e2e_steps,
            # host link rates seen by the state copies of this run (they vary with the host)
            "state_h2d_gbs": round(nbytes / t_up / 1e9, 1),
            "state_d2h_gbs": round(nbytes / t_down / 1e9, 1)}
 
-    peak, peak_kind = load_peaks()
-    per_launch_bytes = algorithmic_bytes_per_cell(w) * cells
-    avg_kernel_ms = k_ms / max(k_n, 1)
-    achieved = per_launch_bytes / (avg_kernel_ms / 1e3) / 1e9
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4),
-                "traffic": recorded_traffic(args.workload, w, args.kernel),
-                "peak_kind": peak_kind, "kernel": step_kernel_of(w, args.kernel)[0],
-                "kernel_ms": round(avg_kernel_ms, 5),
-                "algorithmic_bytes_per_launch": per_launch_bytes}
     # launches of our kernels in the timed region: fused step every step, plus tile->block and
     # flag kernels on sensor steps
-    n_sensor = args.steps // w["sensor_every"]
-    gpu_launches = args.steps + 2 * n_sensor
-
+    gpu_launches = rec["timed_steps"] + 2 * rec["n_sensor_per_repeat"] * rec["repeats"]
     out = {
         "metric": "fused stream-collide+sensor MLUPS",
-        "value": round(value, 1),
+        "value": round(rec["value"], 1),
         "unit": "MLUPS",
         "n_gpus": ws,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": round(ms_max / args.steps, 5),
+        "ms_per_step": round(rec["ms_per_step"], 5),
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": DTYPE_NAME[w["dtype"]],
         "data": "synthetic (lid-driven cavity from rest)",
         "config": {"workload": args.workload, "lattice": f"D{3 if q == 19 else 2}Q{q}",
-                   "edge": n, "cells": cells, "re": w["re"], "tau": round(tau, 6), "lid_u": w["u"],
-                   "sensor_every": w["sensor_every"], "block": w["block"], "blocks": nb,
-                   "flag_rule": w["rule"], "flag_param": param,
+                   "edge": n, "cells": cells, "re": w["re"], "tau": round(rec["tau"], 6),
+                   "lid_u": w["u"], "sensor_every": w["sensor_every"], "block": w["block"],
+                   "blocks": nb, "flag_rule": w["rule"], "flag_param": param,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "timing": (f"{rec['repeats']} repeats of {args.steps} steps (>= {args.min_time} s "
+                              "of device time), CUDA events per repeat, median per-step time"),
                    "l2": (f"population buffers {2 * nbytes / 1e9:.2f} GB > 129 MB L2, no flush"
                           if 2 * nbytes > 129e6 else "working set fits L2 (launch-bound case)")},
-        "roofline": roofline,
+        "repeats": rec["repeats"],
+        "ms_per_step_min_max": [round(x, 5) for x in rec["ms_per_step_min_max"]],
+        "roofline": rec["roofline"],
         "e2e": e2e,
         "gpu_launches": gpu_launches,
         "clocks": clocks,
     }
-    lat.close()
+    if (ws == 1 and not args.no_mixed and args.workload == DEFAULT_WORKLOAD
+            and args.edge is None and args.kernel == "auto"):
+        out["mixed"] = run_mixed(args, ws, uuid)
     return out
 
 
@@ -837,6 +1007,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--min-time", type=float, default=MIN_TIMED_S,
+                    help="device seconds the timed loop accumulates (repeats of --steps steps); "
+                         "a shorter time is for profiling captures only")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the mixed-precision row (512^3 FP32 / FP16 / BF16 storage and the "
+                         "error check) that the default workload's line carries")
     ap.add_argument("--kernel", default="auto", choices=["auto", "cell", "pair", "tma"],
                     help="fused step kernel (default: the library's automatic choice)")
     ap.add_argument("--fusion", default="auto", choices=["auto", "separate", "fused"],

@@ -84,20 +84,38 @@ class _Thread:
         pass
 
 
+def _stamp(sec):
+    import datetime
+
+    return datetime.datetime.fromtimestamp(sec).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+
+
 def test_clock_sampler_parses_and_filters_samples():
     s = bench.ClockSampler("GPU-a")
     s.proc, s.thread = _Proc(), _Thread()
+    t = 1_800_000_000.0
     s.lines = [
-        "GPU-a, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
-        "GPU-a, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
-        "GPU-b, 900, 2070, 100.0, 0x8, Active, Not Active, Not Active, Not Active",  # other GPU
-        "GPU-a, 2070, 2070, 1100.0, 0x0, Not Active, Not Active, Not Active, Not Active",
-        "GPU-a, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        f"{_stamp(t)}, GPU-a, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+        f"{_stamp(t + 1)}, GPU-a, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+        # another GPU
+        f"{_stamp(t + 1)}, GPU-b, 900, 2070, 100.0, 0x8, Active, Not Active, Not Active, Not Active",
+        f"{_stamp(t + 2)}, GPU-a, 2070, 2070, 1100.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        f"{_stamp(t + 3)}, GPU-a, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active",
         "garbage",
     ]
+    c = s.stop()  # no timed window marked: every sample counts
+    assert c["sm_mhz"] == 2070.0 and c["sm_max_mhz"] == 2070.0
+    assert c["samples"] == 3 and c["samples_under_load"] == 3
+    assert c["reasons"] == ["sw_power_cap"]
+    assert c["sm_mhz_bins"] == {"2070": 2, "1980": 1}
+    assert c["power_w_max"] == 1390.0
+
+    # only the samples inside a timed window count as under load
+    s.window(t + 0.5, t + 1.5)
     c = s.stop()
-    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "samples": 3,
-                 "reasons": ["sw_power_cap"]}
+    assert c["samples"] == 3 and c["samples_under_load"] == 1
+    assert c["sm_mhz"] == 1980.0 and c["reasons"] == ["sw_power_cap"]
+    assert c["sm_mhz_bins"] == {"1980": 1}
 
 
 def test_clock_sampler_without_samples():
