@@ -100,8 +100,9 @@ def _load():
             lib.ml_set_block.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, dp]
             lib.ml_level_info.argtypes = [ctypes.c_void_p, ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_int), dp]
+            lib.ml_set_time_interp.argtypes = [ctypes.c_void_p, ctypes.c_int]
             for name in ("ml_cycles", "ml_block_max", "ml_get_block", "ml_set_block",
-                         "ml_level_info"):
+                         "ml_level_info", "ml_set_time_interp"):
                 getattr(lib, name).restype = ctypes.c_int
             for name in ("orc_threads", "orc_set_threads", "orc_step_cells", "orc_lattice", "orc_step", "orc_run", "orc_collide", "orc_stream_push",
                          "orc_sensor", "orc_equilibrium", "orc_block_max", "orc_conservation"):
@@ -425,6 +426,12 @@ class MultiLevel:
         tau = ctypes.c_double()
         _check(_load().ml_level_info(self._h, l, ctypes.byref(n), ctypes.byref(tau)), "info")
         return n.value, tau.value
+
+    def set_time_interp(self, mode):
+        """Test hook: 0 (default) interpolates a fine level's ghosts linearly in time (theta = 0
+        and 1/2 on its two sub-steps); 1 plants the mistake theta = 0 on both (the coarse level
+        frozen over its step), for the pin that shows the test can tell them apart."""
+        _check(_load().ml_set_time_interp(self._h, int(mode)), "set_time_interp")
 
     def cycles(self, c):
         _check(_load().ml_cycles(self._h, int(c)), "cycles")

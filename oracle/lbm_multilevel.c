@@ -84,6 +84,7 @@ typedef struct {
     double *prev[ML_MAXL];      /* state before the level's last step (time interpolation) */
     double *K[ML_MAXL];         /* sensor per cell of the last step, per slot, n^3 */
     long long steps[ML_MAXL];
+    int frozen_time;            /* test hook: 1 = theta 0 on both sub-steps (a planted mistake) */
 } ml_mesh;
 
 #define ML_OK 0
@@ -412,11 +413,22 @@ static int advance(ml_mesh *m, int l, double theta) {
     if (st != ML_OK) return st;
     step_level(m, l);
     if (l < m->d.lmax) {
+        /* the fine level's two sub-steps start at the coarse step's start and half-way through
+         * it: its ghosts are interpolated linearly in time at theta = 0 and 1/2 */
         st = advance(m, l + 1, 0.0);
-        if (st == ML_OK) st = advance(m, l + 1, 0.5);
+        if (st == ML_OK) st = advance(m, l + 1, m->frozen_time ? 0.0 : 0.5);
         if (st != ML_OK) return st;
         restrict_level(m, l);
     }
+    return ML_OK;
+}
+
+/* Test hook for the pin of the temporal interpolation: mode 1 plants a mistake, filling the
+ * ghosts of every second fine sub-step from the coarse state before the coarse step (theta = 0 on
+ * both sub-steps, a coarse level frozen in time); mode 0 (the default) is the linear reading. */
+int ml_set_time_interp(ml_mesh *m, int mode) {
+    if (mode != 0 && mode != 1) return ML_EINVAL;
+    m->frozen_time = mode;
     return ML_OK;
 }
 

@@ -87,6 +87,15 @@ def conv3_weight_grad(dO, A):
     return out
 
 
+def bf16_round(x):
+    """Round to the nearest BF16 value (8 significant bits, the exponent range of FP32), ties to
+    the even significand: the storage rounding of the network's weights and activations.  Written
+    for finite values in the normal range, which is all the network produces (zeros stay zero)."""
+    x = np.asarray(x, dtype=np.float64)
+    m, e = np.frexp(x)                 # x = m 2^e, 0.5 <= |m| < 1
+    return np.ldexp(np.rint(m * 256.0) / 256.0, e)   # np.rint rounds halves to even
+
+
 def normalise(X, shift, scale):
     X = np.asarray(X, dtype=np.float64)
     return (X - np.asarray(shift)[None, :, None, None]) * np.asarray(scale)[None, :, None, None]

@@ -160,6 +160,45 @@ def test_cavity_d3q19_256_full_size_sampled(L):
     lat.close()
 
 
+def test_cavity_d3q19_256_full_field_150_steps(L):
+    """The 256^3 D3Q19 FP32 workload in the benchmark's launch configuration (automatic kernel,
+    sensor every step), 150 steps from a seeded perturbed state, against the FP64 oracle stepping
+    the whole lattice: every population of every cell (<= 1e-5 relative), every 16^3 block maximum
+    of the last step (<= 1e-4), and the top-10 % and fixed-threshold flags of the lattice against
+    the oracle's flag rules on the oracle's own maxima (identical outside the 1e-4 band)."""
+    n, q, steps = 256, 19, 150
+    tau = O.tau_from_re(0.1, n, 1000.0)
+    lat = L.Lattice(q, n, n, n, tau, dtype=L.LBM_F32, lid=(0.1, 0.0))
+    o = O.Oracle(q, n, n, n, tau, lid=(0.1, 0.0, 0.0))
+    L.lbm_set_sensor_every(lat.h, 1)
+    f0 = perturbed(o, seed=1507, amp=0.01).astype(np.float32)
+    lat.set_raw(f0.view(np.uint8).reshape(-1))
+    f0 = f0.astype(np.float64)  # the oracle starts from the same (FP32-rounded) state
+    lat.step(steps)
+    gmax = lat.sensor(16)
+    top = lat.flag_top(0.1, block=16)
+    T = 4.0 * (4.0 / 3.0) * tau * 0.1 / n
+    thr = lat.flag(T, block=16)
+    f_gpu = lat.raw().view(np.float32).reshape(q, n, n, n)
+    lat.close()
+    f_ref, K = o.run(f0, steps, sensor_last=True)
+    del f0
+    scale = np.abs(f_ref).max()
+    worst = 0.0
+    for i in range(q):  # one direction at a time keeps the host memory in check
+        worst = max(worst, float(np.abs(f_gpu[i].astype(np.float64) - f_ref[i]).max()))
+    assert worst / scale <= 1e-5, f"populations differ by {worst / scale:.3e} of max|f|"
+    ref_max = O.block_max(K, 16)
+    assert gmax.shape == (4096,)
+    assert rel(gmax, ref_max) <= 1e-4
+    ok, ncmp, _ = O.flags_agree(top, ref_max, "top", 0.1, 1e-4)
+    assert ok and ncmp >= 4000
+    ok, ncmp, _ = O.flags_agree(thr, ref_max, "threshold", T, 1e-4)
+    assert ok and ncmp >= 4000
+    # the top-10 % rule refines exactly ceil(0.1 * 4096) = 410 blocks
+    assert int((top == 1).sum()) == 410 and int((top == 0).sum()) == 4096 - 410
+
+
 # ----------------------------------------------------------------------------- edge cases
 EDGE_CASES = [
     (9, (1, 1, 1), 0), (9, (2, 3, 1), 0), (9, (5, 7, 1), O.PERIODIC_X), (9, (33, 17, 1), 0),

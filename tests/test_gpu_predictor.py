@@ -2,10 +2,14 @@
 (oracle/predictor.py) and with the plain definition of the block means.
 
 Tolerances: the network stores weights and activations in BF16 (8 significant bits, relative
-rounding 2^-9) and accumulates in FP32, while the oracle is FP64 throughout.  Each layer adds a
-few such roundings to every value, partly averaging out over its 9 * C terms, so the outputs are
-compared norm-wise at 1e-2 relative and the gradients (three layers of products) at 3e-2; a wrong
-index or a dropped term gives O(1) errors.  Adam is FP32 against FP64 on the same gradients: 1e-5.
+rounding 2^-9) and accumulates in FP32.  The parity proper is element-wise and layer by layer
+(test_each_layer_matches_oracle_elementwise): the oracle evaluates each layer in FP64 on the exact
+BF16 operands the kernels read, which leaves only FP32 accumulation, bounded per element.  The
+chained network is also compared with the oracle evaluated in FP64 throughout on the unrounded
+parameters (test_forward_and_gradients_match_oracle): there the BF16 roundings of three layers
+accumulate and some rounding decisions fall differently, so that end-to-end check is norm-wise,
+at 1e-2 for the outputs and 3e-2 for the gradients.  Adam is FP32 against FP64 on the same
+gradients: 1e-5.
 """
 import numpy as np
 import pytest
@@ -117,6 +121,106 @@ def test_forward_and_gradients_match_oracle(L, case):
     g1 = net.grads()
     net.backward(dev(Xraw), dev(T))
     assert np.array_equal(g1, net.grads())
+    net.close()
+
+
+U32 = 2.0 ** -24  # unit roundoff of FP32
+
+
+def bf16_bits_to_f64(bits):
+    return (np.asarray(bits, dtype=np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+def check_rounded(gpu, z, tol, what):
+    """gpu = BF16 rounding of the FP32 value of z (a sum computed within tol of the exact z):
+    equal to bf16_round(z) wherever z's rounding cannot change inside [z - tol, z + tol], else one
+    of the two neighbours.  The ambiguous elements must be rare."""
+    ref = P.bf16_round(z)
+    lo, hi = P.bf16_round(z - tol), P.bf16_round(z + tol)
+    amb = lo != hi
+    assert np.array_equal(gpu[~amb], ref[~amb]), (what, int((gpu[~amb] != ref[~amb]).sum()))
+    assert np.all((gpu[amb] == lo[amb]) | (gpu[amb] == hi[amb])), what
+    assert amb.mean() < 0.01, (what, amb.mean())
+
+
+def check_sum(gpu, ref, mag, nterms, what):
+    """gpu = an FP32 sum of nterms products whose exact value is ref and whose absolute terms add
+    up to mag: |gpu - ref| <= (nterms + 1) u mag element by element."""
+    err = np.abs(np.asarray(gpu, np.float64) - ref)
+    bound = (nterms + 1) * U32 * mag + 1e-30
+    assert np.all(err <= bound), (what, float((err / bound).max()))
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_each_layer_matches_oracle_elementwise(L, case):
+    """Element-wise parity of every layer of the forward and backward pass.  Each layer is
+    evaluated by the oracle in FP64 on the exact BF16 operands the kernels read (the BF16 rounding
+    of the parameters, and the kernels' own BF16 activations of the previous layer), so what is
+    left is FP32 accumulation, bounded per element by (terms + 1) u sum|terms|; the BF16 rounding of
+    an activation must equal the rounding of the oracle's value wherever the accumulation bound
+    cannot move it across a rounding midpoint.  Weight gradients are reduced by 256 threads, each
+    summing a strided share of the positions before a fixed tree over the threads, which bounds
+    their terms per element by ceil(positions / 256) + 8."""
+    cin, hid, B, H, W = CASES[case]
+    p32 = P.flatten(params(960 + case, cin, hid)).astype(np.float32)
+    g = seeded.rng(970 + case)
+    shift = g.uniform(-0.5, 0.5, cin).astype(np.float32)
+    scale = g.uniform(0.5, 2.0, cin).astype(np.float32)
+    Xraw = (g.normal(size=(B, cin, H, W)) / scale[None, :, None, None]
+            + shift[None, :, None, None]).astype(np.float32)
+    T = g.normal(size=(B, 1, H, W)).astype(np.float32)
+    net = L.Net(cin, hid)
+    net.set_normalisation(shift, scale)
+    net.set_params(p32)
+    net.backward(dev(Xraw), dev(T))
+    buf = lambda which, shape: net.buffer(which, shape)  # noqa: E731
+    # parameters: BF16 rounding of the FP32 master copy, exactly
+    pb = bf16_bits_to_f64(buf(L.LBM_NET_BUF_PARAMS_BF16, p32.size))
+    assert np.array_equal(pb, P.bf16_round(p32.astype(np.float64)))
+    p = P.unflatten(pb, cin, hid)
+    pa = {k: np.abs(v) for k, v in p.items()}
+    # normalised input: (x - shift) * scale in FP32 (the kernels' precision decides the rounding)
+    x0 = bf16_bits_to_f64(buf(L.LBM_NET_BUF_X0, (B, cin, H, W)))
+    xn = ((Xraw - shift[None, :, None, None]) * scale[None, :, None, None]).astype(np.float32)
+    assert np.array_equal(x0, P.bf16_round(xn.astype(np.float64)))
+    # layer 1 and 2: pre-activation in FP64 on the kernels' operands, ReLU, BF16 rounding
+    a_in = x0
+    acts = []
+    for k, (Wk, bk, nt) in enumerate((("W1", "b1", 9 * cin), ("W2", "b2", 9 * hid))):
+        z = P.conv3(a_in, p[Wk], p[bk])
+        mag = P.conv3(np.abs(a_in), pa[Wk], pa[bk])
+        a_gpu = bf16_bits_to_f64(buf((L.LBM_NET_BUF_A1, L.LBM_NET_BUF_A2)[k], (B, hid, H, W)))
+        check_rounded(a_gpu, np.maximum(z, 0.0), (nt + 1) * U32 * mag, f"A{k + 1}")
+        acts.append(a_gpu)
+        a_in = a_gpu
+    A1, A2 = acts
+    # output layer (FP32 output, no rounding to BF16)
+    y = buf(L.LBM_NET_BUF_Y, (B, 1, H, W))
+    check_sum(y, P.conv3(A2, p["W3"], p["b3"]), P.conv3(A2, pa["W3"], pa["b3"]), 9 * hid + 4, "Y")
+    # a planted mistake in the oracle (the kernel taps mirrored) is caught by the same bound
+    ybad = P.conv3(A2, p["W3"][:, :, ::-1, ::-1], p["b3"])
+    err = np.abs(y - ybad) / ((9 * hid + 5) * U32 * P.conv3(A2, pa["W3"], pa["b3"]))
+    assert (err > 1).mean() > 0.5
+    # loss gradient dY = (2 / n)(Y - T): two FP32 roundings
+    n = B * H * W
+    dy = buf(L.LBM_NET_BUF_DY, (B, 1, H, W))
+    dref = (2.0 / n) * (y.astype(np.float64) - T)
+    assert np.all(np.abs(dy - dref) <= 3 * U32 * np.abs(dref) + 1e-45)
+    dy = dy.astype(np.float64)
+    grads = P.unflatten(net.grads().astype(np.float64), cin, hid)
+    red = -(-n // 256) + 8  # terms of the weight-gradient reductions, per element
+    # backward through layer 3, 2, 1 on the kernels' own upstream gradients
+    dz2 = buf(L.LBM_NET_BUF_DZ2, (B, hid, H, W)).astype(np.float64)
+    dz1 = buf(L.LBM_NET_BUF_DZ1, (B, hid, H, W)).astype(np.float64)
+    for Wk, bk, d_out, a_low in (("W3", "b3", dy, A2), ("W2", "b2", dz2, A1), ("W1", "b1", dz1, x0)):
+        check_sum(grads[Wk], P.conv3_weight_grad(d_out, a_low),
+                  P.conv3_weight_grad(np.abs(d_out), np.abs(a_low)), red, "g" + Wk)
+        check_sum(grads[bk], d_out.sum(axis=(0, 2, 3)), np.abs(d_out).sum(axis=(0, 2, 3)), red,
+                  "g" + bk)
+    for Wk, d_out, d_in, a_low in (("W3", dy, dz2, A2), ("W2", dz2, dz1, A1)):
+        ref = P.conv3_input_grad(d_out, p[Wk]) * (a_low > 0)
+        mag = P.conv3_input_grad(np.abs(d_out), pa[Wk])
+        check_sum(d_in, ref, mag, 9 * p[Wk].shape[0], "d" + Wk)
     net.close()
 
 

@@ -91,3 +91,23 @@ def test_training_fits_a_teacher_network():
         theta = opt.step(theta, P.flatten(grads))
     L, _ = P.gradients(P.unflatten(theta, cin, hidden), X, T)
     assert L < 0.05 * first and L < 0.1 * np.var(T)
+
+
+def test_bf16_round_hand_cases_and_library_conversion():
+    # 8 significant bits: spacing 2^-7 on [1, 2); halves go to the even significand
+    r = P.bf16_round
+    assert r(1.0 + 2.0 ** -8) == 1.0                      # tie -> even (1.0000000)
+    assert r(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6      # tie -> even (1.0000010)
+    assert r(1.0 + 2.0 ** -8 + 2.0 ** -30) == 1.0 + 2.0 ** -7  # above the tie
+    assert r(-3.0 - 2.0 ** -7) == -3.0                    # tie at spacing 2^-6, negative
+    assert r(0.0) == 0.0 and r(2.0 ** -126) == 2.0 ** -126
+    assert r(255.5) == 256.0 and r(254.5) == 254.0        # spacing 1 on [128, 256)
+    # against the library's round-to-nearest-even FP32 -> BF16 conversion on FP32 values
+    torch = pytest.importorskip("torch")
+    g = seeded.rng(77)
+    x = (g.normal(size=20000) * 10.0 ** g.uniform(-6, 4, size=20000)).astype(np.float32)
+    # add exact ties: FP32 values whose low 16 bits are 0x8000
+    ties = (g.integers(0x3f000000, 0x41000000, size=2000, dtype=np.int64) & ~0xffff) | 0x8000
+    x = np.concatenate([x, ties.astype(np.uint32).view(np.float32)])
+    lib = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(r(x.astype(np.float64)), lib)
