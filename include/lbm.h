@@ -96,6 +96,7 @@ extern "C" {
 #define LBM_ETIMEOUT (-5) /* a bounded device wait ran out */
 #define LBM_ENOTSUP (-6)  /* not supported in this build */
 #define LBM_ESTATE (-7)   /* call not allowed in the handle's current state */
+#define LBM_EIO (-8)      /* a checkpoint file could not be written, read or verified */
 
 /* Periodic axis mask bits. */
 #define LBM_PERIODIC_X 1
@@ -267,6 +268,35 @@ LBM_API int lbm_get_sensor_field(lbm_t *h, double *out_host);
  * LBM_ENUMERIC (with the sums still written) if a population is NaN or Inf.
  */
 LBM_API int lbm_conservation(lbm_t *h, double *mass, double *mom3);
+
+/*
+ * Checkpoint files (no counterpart in the paper; resuming a long run).  lbm_checkpoint_save writes
+ * an 88-byte header -- magic "LBMCKPT\0", version 1, lattice, nx, ny, nz, storage type, periodic
+ * mask, tau, lid (x, z), step counter, payload size and the 64-bit FNV-1a checksum of the payload,
+ * native byte order -- followed by the populations in the layout of lbm_get_raw (synchronises).
+ * lbm_checkpoint_load checks the header and the checksum (LBM_EIO on an unreadable, truncated or
+ * corrupted file), requires the handle's lattice, dimensions and storage type (LBM_EINVAL
+ * otherwise), then restores tau, the lid, the periodic mask, the populations and the step counter,
+ * so that the run continues bit for bit where it was saved.  Sensor results of earlier steps are
+ * not part of a checkpoint.
+ */
+LBM_API int lbm_checkpoint_save(lbm_t *h, const char *path);
+LBM_API int lbm_checkpoint_load(lbm_t *h, const char *path);
+
+/*
+ * Failure injection for tests (no counterpart in the paper).  lbm_debug_fail_alloc(after): of the
+ * library's next device allocations (any handle, process-wide), the first `after` succeed and the
+ * one after them fails with cudaErrorMemoryAllocation (reported as LBM_ENOMEM) without calling
+ * cudaMalloc; the hook then disarms itself.  A negative value disarms it.  A call that fails this
+ * way keeps what it had allocated (lbm_destroy frees it) and can be retried.
+ * lbm_debug_set_wait_limit(h, ns) sets the limit of the bounded waits between the warps of the
+ * handle's kernels that have them (the TMA-staged step); 0 restores the default of one second.  A
+ * wait that runs out makes the kernel stop, wait (with the full default limit) for its own copies
+ * in flight and return; the next synchronising call reports LBM_ETIMEOUT and the state is invalid
+ * until lbm_reset.
+ */
+LBM_API int lbm_debug_fail_alloc(int after);
+LBM_API int lbm_debug_set_wait_limit(lbm_t *h, long long ns);
 
 /* Total time (ms) and count of the fused step kernels timed since profiling was turned on.
  * Synchronises. */

@@ -8,6 +8,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 #include <vector>
 
@@ -106,6 +107,7 @@ struct lbm_s {
 
     // profiling
     int profiling = 0;
+    unsigned long long wait_ns = 0;  // lbm_debug_set_wait_limit (0: the kernels' default)
     std::vector<cudaEvent_t> events;
     size_t events_used = 0;
 
@@ -153,25 +155,32 @@ StepParams params_of(const lbm_t *h) {
     lbm::finish_params(p);
     p.err = h->err_dev;
     p.tile_zero = nullptr;
+    p.wait_ns = h->wait_ns;
     return p;
 }
 
 int ensure_scratch(lbm_t *h) {
     if (h->scratch_ready) return LBM_OK;
     CK(cudaSetDevice(h->device), "cudaSetDevice");
-    CK(cudaMalloc(&h->tilebuf[0], h->ntiles * h->rsize()), "cudaMalloc(tiles)");
-    CK(cudaMalloc(&h->tilebuf[1], h->ntiles * h->rsize()), "cudaMalloc(tiles)");
+    // each buffer is allocated only if it does not exist yet: after a failed allocation the
+    // handle keeps what it got (lbm_destroy frees it) and the next call continues from there
+    if (!h->tilebuf[0]) CK(lbm::dev_alloc(&h->tilebuf[0], h->ntiles * h->rsize()), "cudaMalloc(tiles)");
+    if (!h->tilebuf[1]) CK(lbm::dev_alloc(&h->tilebuf[1], h->ntiles * h->rsize()), "cudaMalloc(tiles)");
     CK(cudaMemset(h->tilebuf[0], 0, h->ntiles * h->rsize()), "cudaMemset(tiles)");
     CK(cudaMemset(h->tilebuf[1], 0, h->ntiles * h->rsize()), "cudaMemset(tiles)");
     h->tiles = h->tilebuf[0];
     h->tile_next = 0;
-    CK(cudaMalloc(&h->blocks, h->ntiles * h->rsize()), "cudaMalloc(blocks)");
-    CK(cudaMalloc((void **)&h->blocks_f64, h->ntiles * sizeof(double)), "cudaMalloc(blocks_f64)");
-    CK(cudaMalloc((void **)&h->flags, h->ntiles), "cudaMalloc(flags)");
-    CK(cudaMalloc((void **)&h->cons_partial, lbm::CONS_PARTS * 5 * sizeof(double)),
-       "cudaMalloc(partial)");
-    CK(cudaMalloc((void **)&h->cons_result, 8 * sizeof(double)), "cudaMalloc(result)");
-    CK(cudaHostAlloc((void **)&h->err_host, sizeof(int), cudaHostAllocMapped), "cudaHostAlloc(err)");
+    if (!h->blocks) CK(lbm::dev_alloc(&h->blocks, h->ntiles * h->rsize()), "cudaMalloc(blocks)");
+    if (!h->blocks_f64)
+        CK(lbm::dev_alloc(&h->blocks_f64, h->ntiles * sizeof(double)), "cudaMalloc(blocks_f64)");
+    if (!h->flags) CK(lbm::dev_alloc(&h->flags, h->ntiles), "cudaMalloc(flags)");
+    if (!h->cons_partial)
+        CK(lbm::dev_alloc(&h->cons_partial, lbm::CONS_PARTS * 5 * sizeof(double)),
+           "cudaMalloc(partial)");
+    if (!h->cons_result) CK(lbm::dev_alloc(&h->cons_result, 8 * sizeof(double)), "cudaMalloc(result)");
+    if (!h->err_host)
+        CK(cudaHostAlloc((void **)&h->err_host, sizeof(int), cudaHostAllocMapped),
+           "cudaHostAlloc(err)");
     *h->err_host = 0;
     CK(cudaHostGetDevicePointer((void **)&h->err_dev, h->err_host, 0), "cudaHostGetDevicePointer");
     h->scratch_ready = true;
@@ -184,12 +193,12 @@ int ensure_buffers(lbm_t *h) {
     if (h->buf[0]) return LBM_OK;
     CK(cudaSetDevice(h->device), "cudaSetDevice");
     const size_t bytes = h->pop_bytes();
-    cudaError_t e = cudaMalloc(&h->buf[0], bytes);
+    cudaError_t e = lbm::dev_alloc(&h->buf[0], bytes);
     if (e != cudaSuccess) {
         h->buf[0] = nullptr;
         return cuda_fail(e, "cudaMalloc(populations A)");
     }
-    e = cudaMalloc(&h->buf[1], bytes);
+    e = lbm::dev_alloc(&h->buf[1], bytes);
     if (e != cudaSuccess) {
         cudaFree(h->buf[0]);
         h->buf[0] = nullptr;
@@ -207,14 +216,14 @@ int ensure_buffers(lbm_t *h) {
 int ensure_staging(lbm_t *h) {
     if (h->staging) return LBM_OK;
     const size_t cap = h->N > 64 ? h->N : 64;
-    CK(cudaMalloc((void **)&h->staging, cap * sizeof(double)), "cudaMalloc(staging)");
+    CK(lbm::dev_alloc((void **)&h->staging, cap * sizeof(double)), "cudaMalloc(staging)");
     h->staging_cap = cap;
     return LBM_OK;
 }
 
 int ensure_kfield(lbm_t *h) {
     if (h->kfield) return LBM_OK;
-    CK(cudaMalloc(&h->kfield, h->N * h->rsize()), "cudaMalloc(k field)");
+    CK(lbm::dev_alloc(&h->kfield, h->N * h->rsize()), "cudaMalloc(k field)");
     return LBM_OK;
 }
 
@@ -364,6 +373,24 @@ int sync(lbm_t *h) {
 }  // namespace
 
 namespace lbm {
+// Failure injection of lbm_debug_fail_alloc: the number of further allocations that succeed before
+// one fails (-1: disarmed).
+std::atomic<long long> g_fail_alloc_after{-1};
+
+cudaError_t dev_alloc(void **p, size_t bytes) {
+    long long c = g_fail_alloc_after.load();
+    while (c >= 0) {
+        if (g_fail_alloc_after.compare_exchange_weak(c, c - 1)) {
+            if (c == 0) {  // this is the allocation that fails; the hook is disarmed now
+                *p = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+            break;
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
+
 // Error reporting for the other C-ABI translation units (same thread-local state as this file).
 int report_error(int code, const char *msg) { return fail(code, "%s", msg); }
 int report_cuda_error(cudaError_t e, const char *what) { return cuda_fail(e, what); }
@@ -386,6 +413,7 @@ LBM_API const char *lbm_strerror(int status) {
         case LBM_ETIMEOUT: return "device wait timed out";
         case LBM_ENOTSUP: return "not supported";
         case LBM_ESTATE: return "not allowed in the current state";
+        case LBM_EIO: return "checkpoint file error";
         default: return "unknown status";
     }
 }
@@ -902,8 +930,8 @@ LBM_API int lbm_set_sensor_average(lbm_t *h, int on) {
     if (st != LBM_OK) return st;
     if (on) {
         if (!h->tile_sum) {
-            CK(cudaMalloc((void **)&h->tile_sum, h->ntiles * sizeof(double)), "cudaMalloc(sum)");
-            CK(cudaMalloc((void **)&h->tile_avg, h->ntiles * sizeof(double)), "cudaMalloc(avg)");
+            CK(lbm::dev_alloc((void **)&h->tile_sum, h->ntiles * sizeof(double)), "cudaMalloc(sum)");
+            CK(lbm::dev_alloc((void **)&h->tile_avg, h->ntiles * sizeof(double)), "cudaMalloc(avg)");
         }
         CK(cudaMemsetAsync(h->tile_sum, 0, h->ntiles * sizeof(double), h->stream), "memset");
         h->avg_count = 0;
@@ -1130,3 +1158,130 @@ LBM_API int lbm_regrid(lbm_t *h, const double *field_dev, const lbm_regrid_param
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------ failure injection
+LBM_API int lbm_debug_fail_alloc(int after) {
+    g_err = LBM_OK;
+    lbm::g_fail_alloc_after.store(after < 0 ? -1 : (long long)after);
+    return LBM_OK;
+}
+
+LBM_API int lbm_debug_set_wait_limit(lbm_t *h, long long ns) {
+    CHECK_H(h);
+    if (ns < 0) return fail(LBM_EINVAL, "wait limit must be >= 0 (0: the default)");
+    h->wait_ns = (unsigned long long)ns;
+    drop_graphs(h);  // captured launches carry the old limit
+    return LBM_OK;
+}
+
+// ------------------------------------------------------------------------------ checkpoints
+namespace {
+
+struct CkptHeader {
+    char magic[8];          // "LBMCKPT\0"
+    int32_t version;        // 1
+    int32_t lattice;        // LBM_D2Q9 / LBM_D3Q19
+    int32_t nx, ny, nz;
+    int32_t dtype;          // storage type of the payload
+    int32_t periodic;
+    int32_t reserved;
+    double tau, lid_x, lid_z;
+    int64_t step;           // steps taken since the last reset
+    uint64_t payload_bytes; // q * N * element size, the layout of lbm_get_raw
+    uint64_t checksum;      // FNV-1a (64-bit) of the payload
+};
+static_assert(sizeof(CkptHeader) == 88, "checkpoint header layout");
+const char kCkptMagic[8] = {'L', 'B', 'M', 'C', 'K', 'P', 'T', '\0'};
+
+uint64_t fnv1a(const unsigned char *p, size_t n, uint64_t h = 1469598103934665603ull) {
+    for (size_t k = 0; k < n; ++k) {
+        h ^= p[k];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+}  // namespace
+
+LBM_API int lbm_checkpoint_save(lbm_t *h, const char *path) {
+    CHECK_H(h);
+    if (!path) return fail(LBM_EINVAL, "NULL path");
+    const size_t bytes = h->pop_bytes();
+    std::vector<unsigned char> buf;
+    try {
+        buf.resize(bytes);
+    } catch (...) {
+        return fail(LBM_ENOMEM, "host buffer of %zu bytes for the checkpoint", bytes);
+    }
+    int st = lbm_get_raw(h, buf.data(), bytes);
+    if (st != LBM_OK) return st;
+    CkptHeader hd;
+    memset(&hd, 0, sizeof(hd));
+    memcpy(hd.magic, kCkptMagic, 8);
+    hd.version = 1;
+    hd.lattice = h->q;
+    hd.nx = h->nx;
+    hd.ny = h->ny;
+    hd.nz = h->nz;
+    hd.dtype = h->dtype;
+    hd.periodic = h->periodic;
+    hd.tau = h->tau;
+    hd.lid_x = h->lid_x;
+    hd.lid_z = h->lid_z;
+    hd.step = h->t;
+    hd.payload_bytes = bytes;
+    hd.checksum = fnv1a(buf.data(), bytes);
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(LBM_EIO, "cannot open %s for writing", path);
+    const bool ok = fwrite(&hd, sizeof(hd), 1, f) == 1 && fwrite(buf.data(), 1, bytes, f) == bytes;
+    const bool closed = fclose(f) == 0;
+    if (!ok || !closed) return fail(LBM_EIO, "writing %s failed", path);
+    return LBM_OK;
+}
+
+LBM_API int lbm_checkpoint_load(lbm_t *h, const char *path) {
+    CHECK_H(h);
+    if (!path) return fail(LBM_EINVAL, "NULL path");
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(LBM_EIO, "cannot open %s", path);
+    CkptHeader hd;
+    if (fread(&hd, sizeof(hd), 1, f) != 1 || memcmp(hd.magic, kCkptMagic, 8) != 0 ||
+        hd.version != 1) {
+        fclose(f);
+        return fail(LBM_EIO, "%s is not a checkpoint of this library (bad header)", path);
+    }
+    if (hd.lattice != h->q || hd.nx != h->nx || hd.ny != h->ny || hd.nz != h->nz ||
+        hd.dtype != h->dtype || hd.payload_bytes != h->pop_bytes()) {
+        fclose(f);
+        return fail(LBM_EINVAL, "checkpoint %s holds a %d-velocity %d x %d x %d lattice of storage "
+                                "type %d; the handle is %d-velocity %d x %d x %d of type %d",
+                    path, hd.lattice, hd.nx, hd.ny, hd.nz, hd.dtype, h->q, h->nx, h->ny, h->nz,
+                    h->dtype);
+    }
+    if (!(hd.tau > 0.5) || !isfinite(hd.tau) || !isfinite(hd.lid_x) || !isfinite(hd.lid_z) ||
+        (hd.periodic & ~7) || hd.step < 0) {
+        fclose(f);
+        return fail(LBM_EIO, "checkpoint %s has invalid parameters", path);
+    }
+    std::vector<unsigned char> buf;
+    try {
+        buf.resize(hd.payload_bytes);
+    } catch (...) {
+        fclose(f);
+        return fail(LBM_ENOMEM, "host buffer of %llu bytes for the checkpoint",
+                    (unsigned long long)hd.payload_bytes);
+    }
+    const bool ok = fread(buf.data(), 1, buf.size(), f) == buf.size();
+    fclose(f);
+    if (!ok) return fail(LBM_EIO, "checkpoint %s is truncated", path);
+    if (fnv1a(buf.data(), buf.size()) != hd.checksum)
+        return fail(LBM_EIO, "checkpoint %s fails its checksum", path);
+    // parameters first (they validate), then the state; the step counter last
+    int st = lbm_set_tau(h, hd.tau);
+    if (st == LBM_OK) st = lbm_set_lid(h, hd.lid_x, hd.lid_z);
+    if (st == LBM_OK) st = lbm_set_periodic(h, hd.periodic);
+    if (st == LBM_OK) st = lbm_set_raw(h, buf.data(), buf.size());
+    if (st != LBM_OK) return st;
+    h->t = hd.step;
+    return LBM_OK;
+}

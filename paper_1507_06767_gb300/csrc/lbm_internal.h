@@ -106,6 +106,15 @@ int regrid(const void *field, int field_type, int nx, int ny, int nz, int period
            long long *ntagged, uint8_t *tags_out, cudaStream_t s);
 }  // namespace rg
 
+// Every device allocation of the library goes through dev_alloc (lbm_api.cu): cudaMalloc, except
+// that the failure injection of lbm_debug_fail_alloc can make one call report
+// cudaErrorMemoryAllocation without allocating.
+cudaError_t dev_alloc(void **p, size_t bytes);
+template <class T>
+inline cudaError_t dev_alloc(T **p, size_t bytes) {
+    return dev_alloc(reinterpret_cast<void **>(p), bytes);
+}
+
 // Error state shared by the C-ABI translation units (lbm_api.cu).
 int report_error(int code, const char *msg);
 int report_cuda_error(cudaError_t e, const char *what);

@@ -602,7 +602,7 @@ template <class T>
 int upload(T **dev, const std::vector<T> &v) {
     *dev = nullptr;
     if (v.empty()) return LBM_OK;
-    MLCK(cudaMalloc((void **)dev, v.size() * sizeof(T)), "cudaMalloc(tasks)");
+    MLCK(lbm::dev_alloc((void **)dev, v.size() * sizeof(T)), "cudaMalloc(tasks)");
     MLCK(cudaMemcpy(*dev, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), "cudaMemcpy");
     return LBM_OK;
 }
@@ -1118,10 +1118,10 @@ int build(Mesh **out, const int nb[3], int edge, int lmax, const int8_t *leaf, d
             break;
         }
         const size_t bytes = (size_t)L.nslot * Q * L.G * sizeof(float);
-        cudaError_t e = cudaMalloc((void **)&L.buf[0], bytes);
-        if (e == cudaSuccess) e = cudaMalloc((void **)&L.buf[1], bytes);
+        cudaError_t e = lbm::dev_alloc((void **)&L.buf[0], bytes);
+        if (e == cudaSuccess) e = lbm::dev_alloc((void **)&L.buf[1], bytes);
         if (e == cudaSuccess)
-            e = cudaMalloc((void **)&L.kmax, sizeof(float) * std::max(L.nslot, 1));
+            e = lbm::dev_alloc((void **)&L.kmax, sizeof(float) * std::max(L.nslot, 1));
         if (e != cudaSuccess) {
             st = report_cuda_error(e, "cudaMalloc(level)");
             break;
@@ -1182,7 +1182,7 @@ int block_max(Mesh *m, double *out_host, cudaStream_t s) {
     double *dout = nullptr;
     int st = upload(&dls, ls);
     if (st == LBM_OK) st = upload(&dll, ll);
-    if (st == LBM_OK && cudaMalloc((void **)&dout, sizeof(double) * m->nblk) != cudaSuccess)
+    if (st == LBM_OK && lbm::dev_alloc((void **)&dout, sizeof(double) * m->nblk) != cudaSuccess)
         st = report_error(LBM_ENOMEM, "cudaMalloc(block max)");
     if (st == LBM_OK) {
         const float *k1 = m->lmax >= 1 ? m->lv[1].kmax : m->lv[0].kmax;

@@ -339,13 +339,13 @@ int ensure_acts(lbm_net *n, long long pos) {
     if (pos <= n->cap) return LBM_OK;
     free_acts(n);
     const size_t P = (size_t)pos;
-    cudaError_t e = cudaMalloc(&n->x0, P * n->cin * sizeof(__nv_bfloat16));
-    if (e == cudaSuccess) e = cudaMalloc(&n->a1, P * n->hid * sizeof(__nv_bfloat16));
-    if (e == cudaSuccess) e = cudaMalloc(&n->a2, P * n->hid * sizeof(__nv_bfloat16));
-    if (e == cudaSuccess) e = cudaMalloc(&n->y, P * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&n->dy, P * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&n->dz1, P * n->hid * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&n->dz2, P * n->hid * sizeof(float));
+    cudaError_t e = lbm::dev_alloc(&n->x0, P * n->cin * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = lbm::dev_alloc(&n->a1, P * n->hid * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = lbm::dev_alloc(&n->a2, P * n->hid * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = lbm::dev_alloc(&n->y, P * sizeof(float));
+    if (e == cudaSuccess) e = lbm::dev_alloc(&n->dy, P * sizeof(float));
+    if (e == cudaSuccess) e = lbm::dev_alloc(&n->dz1, P * n->hid * sizeof(float));
+    if (e == cudaSuccess) e = lbm::dev_alloc(&n->dz2, P * n->hid * sizeof(float));
     if (e != cudaSuccess) {
         free_acts(n);
         return lbm::report_cuda_error(e, "cudaMalloc(network activations)");
@@ -462,13 +462,13 @@ LBM_API lbm_net *lbm_net_create(int cin, int hidden) {
         n->norm.shift[c] = 0.f;
         n->norm.scale[c] = 1.f;
     }
-    cudaError_t e = cudaMalloc(&n->theta, sizeof(float) * o);
-    if (e == cudaSuccess) e = cudaMalloc(&n->grad, sizeof(float) * o);
-    if (e == cudaSuccess) e = cudaMalloc(&n->m, sizeof(float) * o);
-    if (e == cudaSuccess) e = cudaMalloc(&n->v, sizeof(float) * o);
-    if (e == cudaSuccess) e = cudaMalloc(&n->theta_b, sizeof(__nv_bfloat16) * o);
-    if (e == cudaSuccess) e = cudaMalloc(&n->loss_part, sizeof(double) * LOSS_PARTS);
-    if (e == cudaSuccess) e = cudaMalloc(&n->loss_dev, sizeof(double));
+    cudaError_t e = lbm::dev_alloc(&n->theta, sizeof(float) * o);
+    if (e == cudaSuccess) e = lbm::dev_alloc(&n->grad, sizeof(float) * o);
+    if (e == cudaSuccess) e = lbm::dev_alloc(&n->m, sizeof(float) * o);
+    if (e == cudaSuccess) e = lbm::dev_alloc(&n->v, sizeof(float) * o);
+    if (e == cudaSuccess) e = lbm::dev_alloc(&n->theta_b, sizeof(__nv_bfloat16) * o);
+    if (e == cudaSuccess) e = lbm::dev_alloc(&n->loss_part, sizeof(double) * LOSS_PARTS);
+    if (e == cudaSuccess) e = lbm::dev_alloc(&n->loss_dev, sizeof(double));
     if (e == cudaSuccess) e = cudaMemset(n->theta, 0, sizeof(float) * o);
     if (e == cudaSuccess) e = cudaMemset(n->grad, 0, sizeof(float) * o);
     if (e == cudaSuccess) e = cudaMemset(n->m, 0, sizeof(float) * o);

@@ -268,7 +268,7 @@ struct DevBuf {
         cudaFree(p);
         p = nullptr;
         cap = 0;
-        cudaError_t e = cudaMalloc(&p, bytes);
+        cudaError_t e = lbm::dev_alloc(&p, bytes);
         if (e == cudaSuccess) cap = bytes;
         return e;
     }

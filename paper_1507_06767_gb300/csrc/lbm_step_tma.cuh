@@ -110,12 +110,13 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // Wait for the phase of parity `parity` to complete.  Returns 1 when it did, 0 when the wait ran out
 // of time, -1 when the CTA's abort flag was raised meanwhile.
 __device__ __forceinline__ int mbar_wait_bounded(uint32_t bar, uint32_t parity,
-                                                 const volatile int *abort_flag) {
+                                                 const volatile int *abort_flag,
+                                                 unsigned long long limit_ns = TMA_WAIT_NS) {
     if (mbar_try_wait(bar, parity)) return 1;
     const unsigned long long t0 = global_ns();
     while (!mbar_try_wait(bar, parity)) {
         if (abort_flag && *abort_flag) return -1;
-        if (global_ns() - t0 > TMA_WAIT_NS) return 0;
+        if (global_ns() - t0 > limit_ns) return 0;
     }
     return 1;
 }
@@ -173,6 +174,9 @@ __global__ void __launch_bounds__(TMA_THREADS, TMA_CTAS_PER_SM)
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const size_t N = (size_t)nx * ny * nz;
     const int uxc = (nx + TMA_CHUNK - 1) / TMA_CHUNK;
+    // limit of the waits between the producer and the consumers; the producer's final wait for its
+    // copies in flight keeps the full default, so no CTA exits while a copy into it is pending
+    const unsigned long long wait_ns = p.wait_ns ? p.wait_ns : TMA_WAIT_NS;
     const int U = uxc * ny * ((nz + TMA_UNIT_Z - 1) / TMA_UNIT_Z);
 
     // clear the other tile buffer for the next sensor step
@@ -206,7 +210,8 @@ __global__ void __launch_bounds__(TMA_THREADS, TMA_CTAS_PER_SM)
             for (int j = 0; j < w.nzu; ++j, ++g) {
                 const int s = g % NS;
                 if (g >= NS) {
-                    const int r = mbar_wait_bounded(empty0 + 8 * s, ((g / NS) - 1) & 1, abort_flag);
+                    const int r =
+                        mbar_wait_bounded(empty0 + 8 * s, ((g / NS) - 1) & 1, abort_flag, wait_ns);
                     if (r != 1) {
                         if (r == 0) {
                             *abort_flag = 1;
@@ -234,7 +239,7 @@ __global__ void __launch_bounds__(TMA_THREADS, TMA_CTAS_PER_SM)
         // wait (bounded) for the copies still in flight: the last NS issued stages
         for (int g2 = max(0, g - NS); g2 < g; ++g2) {
             const int s = g2 % NS;
-            mbar_wait_bounded(full0 + 8 * s, (g2 / NS) & 1, nullptr);
+            mbar_wait_bounded(full0 + 8 * s, (g2 / NS) & 1, nullptr, TMA_WAIT_NS);
         }
         return;
     }
@@ -250,7 +255,7 @@ __global__ void __launch_bounds__(TMA_THREADS, TMA_CTAS_PER_SM)
         bool quit = false;
         for (int j = 0; j < w.nzu; ++j, ++g) {
             const int s = g % NS;
-            const int r = mbar_wait_bounded(full0 + 8 * s, (g / NS) & 1, abort_flag);
+            const int r = mbar_wait_bounded(full0 + 8 * s, (g / NS) & 1, abort_flag, wait_ns);
             if (r != 1) {
                 if (r == 0) {
                     *abort_flag = 1;

@@ -131,6 +131,9 @@ struct StepParams {
     float omega_f, lid_x_f, lid_z_f;  // the same in float (no FP64 conversion in FP32 kernels)
     int *err;          // device-visible error word for bounded waits (may be null)
     void *tile_zero;   // tile-maxima buffer a sensor step clears for the next one (may be null)
+    // limit (ns) of the bounded waits between a kernel's own warps; 0 = the kernel's default.  A
+    // kernel waiting for its copies in flight before it exits always uses its default.
+    unsigned long long wait_ns = 0;
 };
 
 // The relaxation rate and lid velocity in the kernel's arithmetic type.

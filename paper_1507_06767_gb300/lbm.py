@@ -114,6 +114,10 @@ _SIGS = {
     "lbm_net_log_targets": (_i, [_vp, _ll, ctypes.c_float, ctypes.c_float, _vp, _vp]),
     "lbm_net_to_maxima": (_i, [_vp, _ll, ctypes.c_float, _vp, _vp]),
     "lbm_net_get_buffer": (_i, [_vp, _i, _vp, _sz]),
+    "lbm_checkpoint_save": (_i, [_h, ctypes.c_char_p]),
+    "lbm_checkpoint_load": (_i, [_h, ctypes.c_char_p]),
+    "lbm_debug_fail_alloc": (_i, [_i]),
+    "lbm_debug_set_wait_limit": (_i, [_h, _ll]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -198,6 +202,16 @@ lbm_set_graphs = _wrap("lbm_set_graphs")
 lbm_set_kernel_variant = _wrap("lbm_set_kernel_variant")
 lbm_reset = _wrap("lbm_reset")
 lbm_step = _wrap("lbm_step")
+lbm_debug_fail_alloc = _wrap("lbm_debug_fail_alloc")
+lbm_debug_set_wait_limit = _wrap("lbm_debug_set_wait_limit")
+
+
+def lbm_checkpoint_save(h, path) -> int:
+    return _ck(_lib.lbm_checkpoint_save(h, os.fsencode(path)), "lbm_checkpoint_save")
+
+
+def lbm_checkpoint_load(h, path) -> int:
+    return _ck(_lib.lbm_checkpoint_load(h, os.fsencode(path)), "lbm_checkpoint_load")
 
 
 def lbm_set_stream(h, stream) -> int:
