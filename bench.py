@@ -107,6 +107,9 @@ def step_kernel_of(w, variant="auto"):
         return pair
     if variant == "tma":
         return "fused_step_tma_kernel", ("lbm_step_tma.cuh", "lbm_step.cuh", "lbm_traits.cuh")
+    if variant == "tma_pair":
+        return "fused_step_tma_pair_kernel", ("lbm_step_tma_pair.cuh", "lbm_step_tma.cuh",
+                                              "lbm_step_pair.cuh", "lbm_step.cuh", "lbm_traits.cuh")
     applicable = w["n"] % 2 == 0 and (w["q"] + 1) * cells < 1 << 32
     if variant == "auto" and applicable and (
             w["dtype"] in ("F16S", "BF16S") or (w["dtype"] == "F32" and w["q"] == 9
@@ -1013,7 +1016,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the mixed-precision row (512^3 FP32 / FP16 / BF16 storage and the "
                          "error check) that the default workload's line carries")
-    ap.add_argument("--kernel", default="auto", choices=["auto", "cell", "pair", "tma"],
+    ap.add_argument("--kernel", default="auto", choices=["auto", "cell", "pair", "tma", "tma_pair"],
                     help="fused step kernel (default: the library's automatic choice)")
     ap.add_argument("--fusion", default="auto", choices=["auto", "separate", "fused"],
                     help="multi-level workload: the finest level's restriction as a separate "

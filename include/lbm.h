@@ -162,14 +162,17 @@ LBM_API int lbm_set_profiling(lbm_t *h, int on);
  * packed FP32 arithmetic (storage other than LBM_F64, an even nx and (q + 1) * cells < 2^32),
  * LBM_KERNEL_TMA the kernel that
  * stages the populations through shared memory with TMA copies (D3Q19, storage other than LBM_F64,
- * nx times the element size a multiple of 16 bytes); LBM_EINVAL where a variant does not apply.
- * All compute the same step; they differ in rounding order only.  The TMA kernel's waits are
+ * nx times the element size a multiple of 16 bytes), LBM_KERNEL_TMA_PAIR the two-cell kernel that
+ * stages the populations of a 64 x 8-cell tile through shared memory with TMA copies (D3Q19, 16-bit
+ * storage, nx a multiple of 8, 20 * cells < 2^32); LBM_EINVAL where a variant does not apply.
+ * All compute the same step; they differ in rounding order only.  The TMA kernels' waits are
  * bounded: if one runs out (it should not), the next synchronising call returns LBM_ETIMEOUT until
  * lbm_reset. */
 #define LBM_KERNEL_AUTO 0
 #define LBM_KERNEL_CELL 1
 #define LBM_KERNEL_PAIR 2
 #define LBM_KERNEL_TMA 3
+#define LBM_KERNEL_TMA_PAIR 4
 LBM_API int lbm_set_kernel_variant(lbm_t *h, int variant);
 /* on != 0: lbm_step replays captured CUDA graphs for runs of steps (default on). */
 LBM_API int lbm_set_graphs(lbm_t *h, int on);
@@ -293,10 +296,14 @@ LBM_API int lbm_checkpoint_load(lbm_t *h, const char *path);
  * handle's kernels that have them (the TMA-staged step); 0 restores the default of one second.  A
  * wait that runs out makes the kernel stop, wait (with the full default limit) for its own copies
  * in flight and return; the next synchronising call reports LBM_ETIMEOUT and the state is invalid
- * until lbm_reset.
+ * until lbm_reset.  lbm_debug_hold_copies(h, on): the producer warps of the handle's TMA-staged
+ * kernels issue no copies, so their consumers' first wait can only run out -- a wait on something
+ * that never comes, with nothing in flight when the kernel gives up (tests of the timeout path;
+ * off by default).
  */
 LBM_API int lbm_debug_fail_alloc(int after);
 LBM_API int lbm_debug_set_wait_limit(lbm_t *h, long long ns);
+LBM_API int lbm_debug_hold_copies(lbm_t *h, int on);
 
 /* Total time (ms) and count of the fused step kernels timed since profiling was turned on.
  * Synchronises. */

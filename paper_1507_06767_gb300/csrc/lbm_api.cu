@@ -108,6 +108,7 @@ struct lbm_s {
     // profiling
     int profiling = 0;
     unsigned long long wait_ns = 0;  // lbm_debug_set_wait_limit (0: the kernels' default)
+    int hold_copies = 0;             // lbm_debug_hold_copies
     std::vector<cudaEvent_t> events;
     size_t events_used = 0;
 
@@ -156,6 +157,7 @@ StepParams params_of(const lbm_t *h) {
     p.err = h->err_dev;
     p.tile_zero = nullptr;
     p.wait_ns = h->wait_ns;
+    p.hold_copies = h->hold_copies;
     return p;
 }
 
@@ -561,8 +563,14 @@ LBM_API int lbm_set_profiling(lbm_t *h, int on) {
 
 LBM_API int lbm_set_kernel_variant(lbm_t *h, int variant) {
     CHECK_H(h);
-    if (variant < LBM_KERNEL_AUTO || variant > LBM_KERNEL_TMA)
+    if (variant < LBM_KERNEL_AUTO || variant > LBM_KERNEL_TMA_PAIR)
         return fail(LBM_EINVAL, "unknown kernel variant %d", variant);
+    if (variant == LBM_KERNEL_TMA_PAIR &&
+        (h->q != LBM_D3Q19 || (h->dtype != LBM_F16S && h->dtype != LBM_BF16S) || h->nx % 8 != 0 ||
+         20ULL * ((unsigned long long)h->nx * h->ny * h->nz) >= (1ULL << 32)))
+        return fail(LBM_EINVAL,
+                    "the TMA two-cell kernel needs D3Q19, 16-bit storage, nx a multiple of 8 and "
+                    "20 * cells < 2^32");
     if (variant == LBM_KERNEL_PAIR &&
         (h->dtype == LBM_F64 || h->nx % 2 != 0 ||
          (unsigned long long)(h->q + 1) * ((unsigned long long)h->nx * h->ny * h->nz) >=
@@ -1171,6 +1179,13 @@ LBM_API int lbm_debug_set_wait_limit(lbm_t *h, long long ns) {
     if (ns < 0) return fail(LBM_EINVAL, "wait limit must be >= 0 (0: the default)");
     h->wait_ns = (unsigned long long)ns;
     drop_graphs(h);  // captured launches carry the old limit
+    return LBM_OK;
+}
+
+LBM_API int lbm_debug_hold_copies(lbm_t *h, int on) {
+    CHECK_H(h);
+    h->hold_copies = on ? 1 : 0;
+    drop_graphs(h);
     return LBM_OK;
 }
 

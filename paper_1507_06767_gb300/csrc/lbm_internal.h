@@ -13,7 +13,8 @@ namespace lbm {
 
 // Fused step (lbm_step_d2q9.cu / lbm_step_d3q19.cu).  mode: 0 no sensor, 1 tile max, 2 + field.
 // variant: KERNEL_CELL: the one-cell kernel; KERNEL_PAIR: the two-cell packed one; KERNEL_TMA: the
-// TMA-staged one (D3Q19 only); the last two are errors where they do not apply.  KERNEL_AUTO picks
+// TMA-staged one (D3Q19 only); KERNEL_TMA_PAIR: the TMA-staged two-cell one (D3Q19, 16-bit
+// storage); the last three are errors where they do not apply.  KERNEL_AUTO picks
 // the two-cell kernel where it applies (even nx, (q + 1) * cells < 2^32) for 16-bit storage and
 // for FP32 storage on D2Q9 lattices of at least AUTO_PAIR_MIN_CELLS_D2Q9_F32 cells, else the
 // one-cell kernel (FP64, FP32 D3Q19, small FP32 D2Q9).  It never picks the TMA kernel, whose tile
@@ -23,6 +24,7 @@ constexpr int KERNEL_AUTO = 0;
 constexpr int KERNEL_CELL = 1;
 constexpr int KERNEL_PAIR = 2;
 constexpr int KERNEL_TMA = 3;
+constexpr int KERNEL_TMA_PAIR = 4;
 cudaError_t step_d2q9(int dtype, const void *fin, void *fout, const StepParams &p, int mode,
                       void *tile_max, void *k_field, cudaStream_t s, int variant = KERNEL_AUTO);
 cudaError_t step_d3q19(int dtype, const void *fin, void *fout, const StepParams &p, int mode,

@@ -1,5 +1,6 @@
 // D3Q19 instantiations of the fused step: the TMA-staged kernel (lbm_step_tma.cuh), the one-cell
-// kernel (lbm_step.cuh) and the two-cell packed kernel (lbm_step_pair.cuh), chosen by `variant`.
+// kernel (lbm_step.cuh), the two-cell packed kernel (lbm_step_pair.cuh) and the TMA-staged
+// two-cell kernel for 16-bit storage (lbm_step_tma_pair.cuh), chosen by `variant`.
 #include <cudaTypedefs.h>
 
 #include <mutex>
@@ -7,6 +8,7 @@
 #include "lbm_internal.h"
 #include "lbm_step_pair.cuh"
 #include "lbm_step_tma.cuh"
+#include "lbm_step_tma_pair.cuh"
 
 namespace lbm {
 namespace {
@@ -103,6 +105,66 @@ cudaError_t launch_fused_step_tma(const void *fin, void *fout, const StepParams 
     return launch_tma_mode<DT, 2>(main_map, halo_map, fin, fout, p, tile_max, k_field, s);
 }
 
+// Tensor map of a 16-bit population buffer as a 4-D tensor (x, y, z, direction) with box
+// (bx, by, 1, 1); out-of-range elements read as zero.
+bool encode_u16(CUtensorMap *map, const void *base, const StepParams &p, int bx, int by) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)p.nx, (cuuint64_t)p.ny, (cuuint64_t)p.nz, 19};
+    const cuuint64_t strides[3] = {(cuuint64_t)p.nx * 2, (cuuint64_t)p.nx * p.ny * 2,
+                                   (cuuint64_t)p.nx * p.ny * p.nz * 2};
+    const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, const_cast<void *>(base), dims, strides, box,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               (CUtensorMapL2promotion)LBM_TMA_L2_PROMO, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+template <int DT, int MODE>
+cudaError_t launch_tma_pair_mode(const TpMaps &maps, const void *fin, void *fout,
+                                 const StepParams &p, void *tile_max, void *k_field,
+                                 cudaStream_t s) {
+    using T = typename Storage<DT>::T;
+    static std::mutex mu;
+    static bool attr[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (dev < 0 || dev >= 64 || !attr[dev]) {
+            e = cudaFuncSetAttribute(fused_step_tma_pair_kernel<DT, MODE>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     TpLayout::SMEM_BYTES);
+            if (e != cudaSuccess) return e;
+            if (dev >= 0 && dev < 64) attr[dev] = true;
+        }
+    }
+    const long long units = (long long)((p.nx + TP_TX - 1) / TP_TX) *
+                            ((p.ny + TP_TY - 1) / TP_TY) * ((p.nz + TP_TZ - 1) / TP_TZ);
+    const int nsm = sm_count();
+    long long grid = (long long)TP_CTAS_PER_SM * (nsm > 0 ? nsm : 1);
+    if (grid > units) grid = units;
+    fused_step_tma_pair_kernel<DT, MODE><<<(unsigned)grid, TP_THREADS, TpLayout::SMEM_BYTES, s>>>(
+        maps, static_cast<const T *>(fin), static_cast<T *>(fout), p,
+        static_cast<float *>(tile_max), static_cast<float *>(k_field));
+    return cudaGetLastError();
+}
+
+template <int DT>
+cudaError_t launch_fused_step_tma_pair(const void *fin, void *fout, const StepParams &p, int mode,
+                                       void *tile_max, void *k_field, cudaStream_t s) {
+    if (!tma_pair_applicable(DT, p)) return cudaErrorInvalidValue;
+    TpMaps maps;
+    if (!encode_u16(&maps.narrow, fin, p, TP_TX, TP_TY) ||
+        !encode_u16(&maps.wide, fin, p, TP_WIDE, TP_TY) || !encode_u16(&maps.face, fin, p, 8, 8))
+        return cudaErrorInvalidValue;
+    if (mode == 0) return launch_tma_pair_mode<DT, 0>(maps, fin, fout, p, tile_max, k_field, s);
+    if (mode == 1) return launch_tma_pair_mode<DT, 1>(maps, fin, fout, p, tile_max, k_field, s);
+    return launch_tma_pair_mode<DT, 2>(maps, fin, fout, p, tile_max, k_field, s);
+}
+
 }  // namespace
 
 cudaError_t step_d3q19(int dtype, const void *fin, void *fout, const StepParams &p, int mode,
@@ -117,8 +179,14 @@ cudaError_t step_d3q19(int dtype, const void *fin, void *fout, const StepParams 
     const bool pair_ok = dtype != 0 && pair_applicable<D3Q19>(p);
     const bool pair = pair_ok && (variant == KERNEL_PAIR || (variant == KERNEL_AUTO && dtype >= 2));
     const bool tma = tma_applicable(dtype, p.nx) && variant == KERNEL_TMA;
-    if ((variant == KERNEL_PAIR && !pair_ok) || (variant == KERNEL_TMA && !tma))
+    const bool tma_pair = variant == KERNEL_TMA_PAIR && tma_pair_applicable(dtype, p);
+    if ((variant == KERNEL_PAIR && !pair_ok) || (variant == KERNEL_TMA && !tma) ||
+        (variant == KERNEL_TMA_PAIR && !tma_pair))
         return cudaErrorInvalidValue;
+    if (tma_pair) {
+        if (dtype == 2) return launch_fused_step_tma_pair<2>(fin, fout, p, mode, tile_max, k_field, s);
+        return launch_fused_step_tma_pair<3>(fin, fout, p, mode, tile_max, k_field, s);
+    }
     switch (dtype) {
         case 0: return launch_fused_step<D3Q19, 0>(fin, fout, p, mode, tile_max, k_field, s);
         case 1:

@@ -29,6 +29,7 @@ namespace lbm {
 
 constexpr int PAIR_CTA_CELLS_X = 2 * CTA_X;  // 64 cells along x per CTA
 
+
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
 // The populations of the two cells of one direction as held in registers between the gather and

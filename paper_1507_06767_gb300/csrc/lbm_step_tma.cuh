@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(TMA_THREADS, TMA_CTAS_PER_SM)
 
     if (warp == TMA_CONSUMER_WARPS) {
         // ---------------------------------------------------------------- producer warp
-        if (lane != 0) return;
+        if (lane != 0 || p.hold_copies) return;
         int g = 0;
         bool stop = false;
         for (int u = blockIdx.x; u < U && !stop; u += gridDim.x) {
@@ -256,11 +256,12 @@ __global__ void __launch_bounds__(TMA_THREADS, TMA_CTAS_PER_SM)
         for (int j = 0; j < w.nzu; ++j, ++g) {
             const int s = g % NS;
             const int r = mbar_wait_bounded(full0 + 8 * s, (g / NS) & 1, abort_flag, wait_ns);
-            if (r != 1) {
-                if (r == 0) {
-                    *abort_flag = 1;
-                    if (p.err) atomicOr(p.err, 1);
-                }
+            if (r == 0) {
+                *abort_flag = 1;
+                if (p.err) atomicOr(p.err, 1);
+            }
+            // the lanes poll on their own: the warp stops as one if any of them stopped
+            if (__any_sync(0xffffffffu, r != 1)) {
                 quit = true;
                 break;
             }

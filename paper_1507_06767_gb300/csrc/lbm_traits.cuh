@@ -134,6 +134,9 @@ struct StepParams {
     // limit (ns) of the bounded waits between a kernel's own warps; 0 = the kernel's default.  A
     // kernel waiting for its copies in flight before it exits always uses its default.
     unsigned long long wait_ns = 0;
+    // test hook: the producer warps of the TMA-staged kernels issue no copies, so the consumers'
+    // first wait can only run out (no copy is in flight when they give up)
+    int hold_copies = 0;
 };
 
 // The relaxation rate and lid velocity in the kernel's arithmetic type.

@@ -118,6 +118,7 @@ _SIGS = {
     "lbm_checkpoint_load": (_i, [_h, ctypes.c_char_p]),
     "lbm_debug_fail_alloc": (_i, [_i]),
     "lbm_debug_set_wait_limit": (_i, [_h, _ll]),
+    "lbm_debug_hold_copies": (_i, [_h, _i]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -204,6 +205,7 @@ lbm_reset = _wrap("lbm_reset")
 lbm_step = _wrap("lbm_step")
 lbm_debug_fail_alloc = _wrap("lbm_debug_fail_alloc")
 lbm_debug_set_wait_limit = _wrap("lbm_debug_set_wait_limit")
+lbm_debug_hold_copies = _wrap("lbm_debug_hold_copies")
 
 
 def lbm_checkpoint_save(h, path) -> int:

@@ -4,9 +4,10 @@ or by a shortened wait limit (no GPU fault is ever provoked).
 * an allocation that fails (lbm_debug_fail_alloc makes the library's k-th next device allocation
   report cudaErrorMemoryAllocation without allocating) gives LBM_ENOMEM, leaks no device memory,
   and the call succeeds when retried, with the same results as an undisturbed handle;
-* a bounded wait that runs out (lbm_debug_set_wait_limit shortens the limit of the TMA-staged
-  step's producer/consumer waits to 1 ns) makes the next synchronising call return LBM_ETIMEOUT;
-  the kernel drains its own copies in flight and returns, so the context stays usable: after
+* a bounded wait that runs out (lbm_debug_hold_copies stops the TMA-staged kernels' producers
+  from issuing copies, so the consumers wait for something that never comes, and
+  lbm_debug_set_wait_limit shortens their limit to 1 ms) makes the next synchronising call return
+  LBM_ETIMEOUT; the kernel returns with nothing in flight, so the context stays usable: after
   lbm_reset the handle runs bit for bit like a fresh one;
 * a checkpoint file written by lbm_checkpoint_save resumes the run bit for bit; a corrupted,
   truncated or foreign file is refused.
@@ -95,24 +96,30 @@ def test_network_allocation_failure(L):
     assert abs(free_bytes() - free0) < 8 << 20
 
 
-def test_bounded_wait_runs_out_and_the_context_survives(L):
+@pytest.mark.parametrize("variant,dtype", [("TMA", "F32"), ("TMA_PAIR", "F16S")])
+def test_bounded_wait_runs_out_and_the_context_survives(L, variant, dtype):
     dims = (64, 64, 64)
-    lat = L.Lattice(L.LBM_D3Q19, *dims, 0.6, dtype=L.LBM_F32, lid=(0.1, 0.0))
-    L.lbm_set_kernel_variant(lat.h, L.LBM_KERNEL_TMA)
-    L.lbm_debug_set_wait_limit(lat.h, 1)  # 1 ns: the first wait for a copy in flight runs out
-    L.lbm_step(lat.h, 4)
+    dt = getattr(L, "LBM_" + dtype)
+    kv = getattr(L, "LBM_KERNEL_" + variant)
+    lat = L.Lattice(L.LBM_D3Q19, *dims, 0.6, dtype=dt, lid=(0.1, 0.0))
+    L.lbm_set_kernel_variant(lat.h, kv)
+    # the producers issue nothing: the consumers' first wait runs out after 1 ms
+    L.lbm_debug_hold_copies(lat.h, 1)
+    L.lbm_debug_set_wait_limit(lat.h, 1_000_000)
+    L.lbm_step(lat.h, 2)
     with pytest.raises(L.LbmError) as ei:
         lat.sensor(16)  # synchronises and reads the kernels' error word
     assert ei.value.status == L.LBM_ETIMEOUT
-    # the default limit again; lbm_reset clears the error and restarts from rest
+    # the default again; lbm_reset clears the error and restarts from rest
+    L.lbm_debug_hold_copies(lat.h, 0)
     L.lbm_debug_set_wait_limit(lat.h, 0)
     L.lbm_reset(lat.h)
     L.lbm_step(lat.h, 10)
     got = lat.populations()
     k_got = lat.sensor(16)
     lat.close()
-    fresh = L.Lattice(L.LBM_D3Q19, *dims, 0.6, dtype=L.LBM_F32, lid=(0.1, 0.0))
-    L.lbm_set_kernel_variant(fresh.h, L.LBM_KERNEL_TMA)
+    fresh = L.Lattice(L.LBM_D3Q19, *dims, 0.6, dtype=dt, lid=(0.1, 0.0))
+    L.lbm_set_kernel_variant(fresh.h, kv)
     L.lbm_step(fresh.h, 10)
     assert np.array_equal(got, fresh.populations())
     assert np.array_equal(k_got, fresh.sensor(16))

@@ -364,10 +364,11 @@ STORAGE_TOL = {  # populations (max|df|/max|f| after 3 steps), sensor field (rel
                                              (19, (288, 9, 11), 0),
                                              (9, (66, 30, 1), 0)])
 def test_kernel_variants_match_oracle(L, dtype, q, dims, periodic):
-    """The one-cell kernel, the two-cell packed kernel and the TMA-staged kernel compute the same
-    step: each matches the oracle from the same storage-rounded input within the storage type's
-    tolerance, and they agree with each other to a few FP32 roundings.  The lattices are ragged
-    against the TMA work unit (32 x 8 x 8 cells) in every direction.  Shifted FP16 / BF16 storage
+    """The one-cell kernel, the two-cell packed kernel, the TMA-staged kernel and (16-bit storage)
+    the TMA-staged two-cell kernel compute the same step: each matches the oracle from the same
+    storage-rounded input within the storage type's tolerance, and they agree with each other to a
+    few FP32 roundings.  The lattices are ragged against the TMA work units (256 x 1 x 8 and
+    64 x 8 x 8 cells) in every direction.  Shifted FP16 / BF16 storage
     (f - w_i) rounds the deviation from rest to 11 / 8 significant bits per step; the tolerances
     above are those roundings over 3 steps."""
     dt = getattr(L, "LBM_" + dtype)
@@ -375,6 +376,8 @@ def test_kernel_variants_match_oracle(L, dtype, q, dims, periodic):
     o = O.Oracle(q, *dims, tau=0.6, lid=lid, periodic=periodic)
     f0 = perturbed(o, seed=77 + q + dims[0], amp=0.02)
     variants = [L.LBM_KERNEL_CELL, L.LBM_KERNEL_PAIR] + ([L.LBM_KERNEL_TMA] if q == 19 else [])
+    if q == 19 and dtype != "F32" and dims[0] % 8 == 0:
+        variants.append(L.LBM_KERNEL_TMA_PAIR)
     res = {}
     for variant in variants:
         lat = L.Lattice(q, *dims, 0.6, dtype=dt, lid=(lid[0], lid[2]), periodic=periodic)
@@ -433,12 +436,44 @@ def test_two_cell_kernel_tiny_lattices(L, dtype, q, dims, periodic):
     assert rel(res[L.LBM_KERNEL_PAIR][1], res[L.LBM_KERNEL_CELL][1]) < tol_f
 
 
+@pytest.mark.parametrize("dtype", ["F16S", "BF16S"])
+@pytest.mark.parametrize("dims,periodic", [((8, 8, 8), 0), ((16, 5, 3), O.PERIODIC_X),
+                                           ((72, 20, 19), O.PERIODIC_X | O.PERIODIC_Z),
+                                           ((136, 17, 23), 0), ((64, 64, 64), 7),
+                                           ((200, 12, 9), O.PERIODIC_Y)])
+def test_tma_pair_kernel_bitwise_equals_two_cell_kernel(L, dtype, dims, periodic):
+    """The TMA-staged two-cell kernel evaluates the same floating-point operations as the two-cell
+    kernel on the same stored inputs (the same rows take the packed relaxation, the same rows the
+    per-cell gather), so over 50 steps -- mixed sensor and plain steps, graph replay, a lid with x
+    and z components -- the stored populations and the sensor maxima are identical bit for bit.
+    The lattices cover one tile holding both x faces (nx = 8), x-periodic wrap at both faces,
+    partial units in every direction, and fewer rows or planes than a unit."""
+    dt = getattr(L, "LBM_" + dtype)
+    o = O.Oracle(19, *dims, tau=0.58, lid=(0.09, 0.0, 0.03), periodic=periodic)
+    f0 = perturbed(o, seed=311 + sum(dims), amp=0.02)
+    out = {}
+    for variant in (L.LBM_KERNEL_PAIR, L.LBM_KERNEL_TMA_PAIR):
+        lat = L.Lattice(19, *dims, 0.58, dtype=dt, lid=(0.09, 0.03), periodic=periodic)
+        L.lbm_set_kernel_variant(lat.h, variant)
+        L.lbm_set_sensor_every(lat.h, 7)
+        lat.set_populations(f0)
+        lat.step(50)
+        out[variant] = (lat.raw(), lat.sensor(8))
+        lat.close()
+    a, b = out[L.LBM_KERNEL_PAIR], out[L.LBM_KERNEL_TMA_PAIR]
+    assert np.array_equal(a[0], b[0])
+    assert np.array_equal(a[1], b[1])
+
+
 def test_kernel_variant_applicability(L):
     """A variant that does not apply is refused when it is set (LBM_EINVAL), before any buffer is
     allocated: the two-cell kernel with FP64 storage, an odd nx, or (q + 1) * cells >= 2^32 (its
-    32-bit offsets); the TMA kernel on D2Q9."""
+    32-bit offsets); the TMA kernel on D2Q9; the TMA two-cell kernel with FP32 storage, nx not a
+    multiple of 8, 20 * cells >= 2^32, or D2Q9."""
     cases = [(19, (33, 8, 8), "F32", "PAIR"), (19, (32, 8, 8), "F64", "PAIR"),
-             (19, (1024, 1024, 208), "F16S", "PAIR"), (9, (64, 64, 1), "F32", "TMA")]
+             (19, (1024, 1024, 208), "F16S", "PAIR"), (9, (64, 64, 1), "F32", "TMA"),
+             (19, (64, 8, 8), "F32", "TMA_PAIR"), (19, (36, 8, 8), "F16S", "TMA_PAIR"),
+             (19, (1024, 1024, 208), "BF16S", "TMA_PAIR"), (9, (64, 64, 1), "F16S", "TMA_PAIR")]
     for q, (nx, ny, nz), dt, variant in cases:
         h = L.lbm_create(q, nx, ny, nz, 0.6)
         try:

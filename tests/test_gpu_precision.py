@@ -18,8 +18,9 @@ of that error at (1 - 1/tau) per step while the moments keep it, so the error se
 few times the one-step rounding instead of growing like the step count.  The asserted values are
 about three times the errors measured on GB300 for this run and well inside the random-walk
 ceiling sqrt(steps) * 2^-p * max|f - w| / max|f|.  Flags must agree except on blocks whose oracle
-maximum lies within the storage type's K bound of a decision value (T, T/2, the k-th largest
-maximum): outside that band no admissible error can move the decision.
+maximum lies within twice the storage type's block-maximum bound (times the largest maximum) of a
+decision value (T, T/2, the k-th largest maximum): outside that band no admissible error can move
+the decision.
 """
 import numpy as np
 import pytest
@@ -88,15 +89,21 @@ def test_storage_error_budget_5000_steps(L, reference, dtype):
     bound = BOUNDS[dtype]
     for key, val in err.items():
         assert val <= bound[key], f"{dtype} {key} error {val:.3e} above its bound {bound[key]:.1e}"
-    # flags: identical outside the band the storage type's sensor error allows
-    band = max(bound["Kb"], 1e-4)
-    ok, ncmp, nex = O.flags_agree(lat.flag_top(0.1, block=BLOCK), reference["bmax"], "top", 0.1,
-                                  band)
-    assert ok, f"{dtype} top-10 % flags differ outside the {band:.0e} band ({nex} excluded)"
-    assert ncmp >= 0.9 * len(reference["bmax"])
-    ok, ncmp, nex = O.flags_agree(lat.flag(T_FIXED, block=BLOCK), reference["bmax"], "threshold",
-                                  T_FIXED, band)
-    assert ok, f"{dtype} threshold flags differ outside the {band:.0e} band ({nex} excluded)"
+    # flags: identical outside the band the storage type's sensor error allows.  Every block maximum
+    # is within Kb times the largest maximum of the oracle's, so a block can cross a decision
+    # value (T, T/2, the k-th largest maximum) only if its oracle value lies within twice that
+    # absolute error of it.  With BF16 storage the band is wide and covers most blocks near T.
+    bmax = reference["bmax"]
+    band = 2.0 * bound["Kb"] * bmax.max()
+    kth = np.sort(bmax)[::-1][O.top_count(0.1, len(bmax)) - 1]
+    ok, ncmp, nex = O.flags_agree(lat.flag_top(0.1, block=BLOCK), bmax, "top", 0.1,
+                                  max(band / kth, 1e-4))
+    assert ok, f"{dtype} top-10 % flags differ outside the band ({nex} excluded)"
+    assert ncmp >= 0.5 * len(bmax)
+    ok, ncmp, nex = O.flags_agree(lat.flag(T_FIXED, block=BLOCK), bmax, "threshold", T_FIXED,
+                                  max(band / (T_FIXED / 2.0), 1e-4))
+    assert ok, f"{dtype} threshold flags differ outside the band ({nex} excluded)"
+    assert ncmp >= 0.05 * len(bmax)
     # mass of the closed cavity: exact in the oracle; the FP64 sums of the stored state keep it to
     # the storage rounding of the whole lattice
     m, _ = lat.conservation()

@@ -132,15 +132,18 @@ def bf16_bits_to_f64(bits):
 
 
 def check_rounded(gpu, z, tol, what):
-    """gpu = BF16 rounding of the FP32 value of z (a sum computed within tol of the exact z):
-    equal to bf16_round(z) wherever z's rounding cannot change inside [z - tol, z + tol], else one
-    of the two neighbours.  The ambiguous elements must be rare."""
-    ref = P.bf16_round(z)
-    lo, hi = P.bf16_round(z - tol), P.bf16_round(z + tol)
+    """gpu = BF16 rounding of ReLU of the FP32 value of z (a sum computed within tol of the exact
+    pre-activation z): equal to bf16_round(max(z, 0)) wherever that cannot change inside
+    [z - tol, z + tol]; elsewhere (ReLU and rounding are monotone) between the roundings of the two
+    ends.  The ambiguous elements must be a small share (the bound is the worst case of a sum of
+    up to 145 terms, some ten times the typical rounding error, so a few per cent are ambiguous)."""
+    relu = lambda v: np.maximum(v, 0.0)  # noqa: E731
+    ref = P.bf16_round(relu(z))
+    lo, hi = P.bf16_round(relu(z - tol)), P.bf16_round(relu(z + tol))
     amb = lo != hi
     assert np.array_equal(gpu[~amb], ref[~amb]), (what, int((gpu[~amb] != ref[~amb]).sum()))
-    assert np.all((gpu[amb] == lo[amb]) | (gpu[amb] == hi[amb])), what
-    assert amb.mean() < 0.01, (what, amb.mean())
+    assert np.all((gpu[amb] >= lo[amb]) & (gpu[amb] <= hi[amb])), what
+    assert amb.mean() < 0.1, (what, amb.mean())
 
 
 def check_sum(gpu, ref, mag, nterms, what):
@@ -190,7 +193,7 @@ def test_each_layer_matches_oracle_elementwise(L, case):
         z = P.conv3(a_in, p[Wk], p[bk])
         mag = P.conv3(np.abs(a_in), pa[Wk], pa[bk])
         a_gpu = bf16_bits_to_f64(buf((L.LBM_NET_BUF_A1, L.LBM_NET_BUF_A2)[k], (B, hid, H, W)))
-        check_rounded(a_gpu, np.maximum(z, 0.0), (nt + 1) * U32 * mag, f"A{k + 1}")
+        check_rounded(a_gpu, z, (nt + 1) * U32 * mag, f"A{k + 1}")
         acts.append(a_gpu)
         a_in = a_gpu
     A1, A2 = acts
