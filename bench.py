@@ -1018,7 +1018,7 @@ def main():
                          "error check) that the default workload's line carries")
     ap.add_argument("--kernel", default="auto", choices=["auto", "cell", "pair", "tma", "tma_pair"],
                     help="fused step kernel (default: the library's automatic choice)")
-    ap.add_argument("--fusion", default="auto", choices=["auto", "separate", "fused"],
+    ap.add_argument("--fusion", default="auto", choices=["auto", "separate", "fused", "brick"],
                     help="multi-level workload: the finest level's restriction as a separate "
                          "kernel or fused into its second sub-step (default: the library's)")
     ap.add_argument("--step-form", default="auto",

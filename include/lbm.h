@@ -393,13 +393,17 @@ LBM_API int lbm_blocks_set(lbm_t *h, int level, int block, const double *in_host
 LBM_API int lbm_blocks_info(lbm_t *h, int level, int *n, double *tau, int *nblocks, int *threads,
                             int *cells_per_thread, long long *cell_updates_per_cycle);
 /* Restriction onto the next coarser level after the finest level's two sub-steps: a separate
- * kernel (LBM_FUSION_SEPARATE, and LBM_FUSION_AUTO, the default: the fused form measured slower on
- * the benchmark mesh) or fused into the finest level's second sub-step (LBM_FUSION_FUSED, where
- * that level's blocks have 16, 32 or 64 cells per edge; the same average and f^neq rescaling,
- * summed in another order).  Applies from the next mesh build: an existing mesh is discarded. */
+ * kernel (LBM_FUSION_SEPARATE) or fused into the finest level's second sub-step -- the tiled form
+ * (LBM_FUSION_FUSED, blocks of 16, 32 or 64 cells per edge), or the brick form (LBM_FUSION_BRICK,
+ * 8, 16, 32 or 64 cells per edge: one thread steps a 2 x 2 x 2 brick of fine cells and writes the
+ * coarse cell under it).  All give the same average and f^neq rescaling, summed in other orders.
+ * LBM_FUSION_AUTO (default) times the separate step + restriction against the brick form when the
+ * mesh is built and keeps the faster.  Applies from the next mesh build: an existing mesh is
+ * discarded. */
 #define LBM_FUSION_AUTO 0
 #define LBM_FUSION_SEPARATE 1
 #define LBM_FUSION_FUSED 2
+#define LBM_FUSION_BRICK 3
 LBM_API int lbm_blocks_set_fusion(lbm_t *h, int mode);
 /* Form of every level's step kernel: LBM_STEP_FORM_AUTO (default) times the candidate forms and
  * launch shapes of each level when the mesh is built and keeps the fastest; the others force one
@@ -418,8 +422,8 @@ LBM_API int lbm_blocks_set_fusion(lbm_t *h, int mode);
 LBM_API int lbm_blocks_set_step_form(lbm_t *h, int form);
 /* The schedule picked for a level: the step kernel's form (0 flat, 1 tiled, 2 flat with the
  * address-select gather, 3 two cells per thread: LBM_STEP_FORM_* minus one), the planes a tiled
- * CTA walks (0 otherwise) and, for the finest level, the planes of the fused step + restriction
- * kernel (0: not fused).  Any pointer may be NULL; LBM_ESTATE without a mesh. */
+ * CTA walks (0 otherwise) and, for the finest level, how its second sub-step restricts: 0 a
+ * separate kernel, 1 the brick form, >= 2 the planes of the tiled fused kernel.  Any pointer may be NULL; LBM_ESTATE without a mesh. */
 LBM_API int lbm_blocks_schedule(lbm_t *h, int level, int *form, int *planes, int *fused);
 
 /*

@@ -1089,8 +1089,8 @@ LBM_API int lbm_block_features(lbm_t *h, int block, float *out_dev) {
 
 LBM_API int lbm_blocks_set_fusion(lbm_t *h, int mode) {
     CHECK_H(h);
-    if (mode < LBM_FUSION_AUTO || mode > LBM_FUSION_FUSED)
-        return fail(LBM_EINVAL, "fusion mode must be LBM_FUSION_AUTO, _SEPARATE or _FUSED");
+    if (mode < LBM_FUSION_AUTO || mode > LBM_FUSION_BRICK)
+        return fail(LBM_EINVAL, "fusion mode must be LBM_FUSION_AUTO, _SEPARATE, _FUSED or _BRICK");
     if (h->mesh) {  // applies to the next build
         CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
         lbm::ml::destroy(h->mesh);

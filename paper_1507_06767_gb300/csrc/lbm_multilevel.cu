@@ -104,6 +104,9 @@ struct Level {
     // brick kernel walking fuse_zc planes); the coarser level then skips k_restrict
     bool fuse = false;
     int fuse_zc = 2;
+    // or the two-cell brick form (k_step_pair_restrict) with its own launch shape
+    bool fuse_brick = false;
+    int brick_threads = 256, brick_cpt = 1;
     int *cslot = nullptr;  // device: per slot, the slot of the same block one level coarser
 };
 
@@ -113,7 +116,7 @@ struct Mesh {
     double lid[3] = {0, 0, 0};
     int periodic = 0;
     Level lv[MAXL];
-    int fusion = 0;  // 0, 1: separate restriction, 2: fused where possible
+    int fusion = 0;  // 0 timed, 1 separate restriction, 2 tiled fused form, 3 brick fused form
     int step_form = -1;  // FORM_* forced on every level where it applies, -1: autotuned
     // a cycle runs level l's work on stream ss[l] (level 0 on the caller's stream, the finer
     // levels on the mesh's own streams), ordered by events: ev_pre[l] before level l's step,
@@ -396,23 +399,73 @@ __global__ void __launch_bounds__(256, 4) k_step_tiled(const float *__restrict__
 // thread, x fastest; the rows of a block are ordered interior rows first ((n - 2)^2 rows, y
 // fastest), then the rows on a y or z face, so that a warp holds rows of one kind only (except one
 // warp for n = 8) and does not run both the select gather and the per-cell one.
+// One row pair-step of k_step_pair: cells (x0, y, z) and (x0 + 1, y, z) of the block, their
+// post-collision populations stored and shown to also(i, float2) (the per-cell gather of a face
+// row shows each cell's value as (v, 0)); returns both sensors.
+struct NoVisit2 {
+    __device__ __forceinline__ void operator()(int, float2) const {}
+};
+template <int NT, class Also = NoVisit2>
+__device__ __forceinline__ float2 pair_row_step(const float *__restrict__ in, const float *src,
+                                                float *dst, const int *snb, bool top,
+                                                const StepArgs &a, int x0, int y, int z,
+                                                Also &&also = NoVisit2()) {
+    using L = D3Q19;
+    constexpr int n = NT, row = n, plane = n * (n + 2);
+    const int G = a.G;
+    const int nbm = snb[12], nbp = snb[14];  // the x - 1 and x + 1 neighbours
+    const int g = (z + 1) * plane + (y + 1) * row + x0;
+    const bool lo = x0 == 0, hi = x0 + 2 == n;
+    if (y == 0 || y == n - 1 || z == 0 || z == n - 1) {
+        const float K0 = step_cell<NT>(in, src, dst, snb, top, a, x0, y, z,
+                                       [&](int i, float v) { also(i, make_float2(v, 0.f)); });
+        const float K1 = step_cell<NT>(in, src, dst, snb, top, a, x0 + 1, y, z,
+                                       [&](int i, float v) { also(i, make_float2(v, 0.f)); });
+        return make_float2(K0, K1);
+    }
+    // the pull of direction i for a row whose y and z sources lie in this block (or its ghost
+    // rows): the x-face lanes select their x neighbour
+    const auto inner = [&](int i) -> float2 {
+        const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+        const int off = cz * plane + cy * row;
+        const float *base = src + (i * G + g - off);
+        if (cx == 0) return *reinterpret_cast<const float2 *>(base);
+        const int ghost = (z - cz + 1) * (n + 2) + (y - cy + 1);
+        if (cx == 1) {  // cell x0 pulls from x0 - 1, cell x0 + 1 from x0
+            const float *alt = nbm >= 0 ? in + ((size_t)nbm * Q * G + (i * G + g - off - 1 + n))
+                               : nbm == NB_GHOST ? src + (i * G + side_base(n, 0) + ghost)
+                                                 : src + (L::opp(i) * G + g);
+            return make_float2(*(lo ? alt : base - 1), *base);
+        }
+        // cell x0 pulls from x0 + 1, cell x0 + 1 from x0 + 2
+        const float *alt = nbp >= 0 ? in + ((size_t)nbp * Q * G + (i * G + g - off + 2 - n))
+                           : nbp == NB_GHOST ? src + (i * G + side_base(n, 1) + ghost)
+                                             : src + (L::opp(i) * G + g + 1);
+        return make_float2(base[1], *(hi ? alt : base + 2));
+    };
+    float2 df[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) df[i] = __fadd2_rn(inner(i), f2(-weight<L, float>(i)));
+    return relax_pair<L, 1, 1>([&](int i) { return df[i]; }, [&](int i) { return df[i]; },
+                               a.omega, [&](int i, float2 v) {
+                                   *reinterpret_cast<float2 *>(dst + (i * G + g)) = v;
+                                   also(i, v);
+                               });
+}
+
 template <int NT>
 __global__ void __launch_bounds__(256, 3) k_step_pair(const float *__restrict__ in,
                                                    float *__restrict__ out,
                                                    const int *__restrict__ nbr, const StepArgs a,
                                                    int cpt, float *kmax) {
-    using L = D3Q19;
     __shared__ int snb[27];
     const int slot = blockIdx.x;
     if (threadIdx.x < 27) snb[threadIdx.x] = nbr[27 * slot + threadIdx.x];
     __syncthreads();
     constexpr int n = NT, half = NT / 2, npair = NT * NT * NT / 2;
-    constexpr int row = n, plane = n * (n + 2);
     const bool top = snb[NB_TOP] == NB_WALL;
-    const int G = a.G;
-    const float *src = in + (size_t)slot * Q * G;
-    float *dst = out + (size_t)slot * Q * G;
-    const int nbm = snb[12], nbp = snb[14];  // the x - 1 and x + 1 neighbours
+    const float *src = in + (size_t)slot * Q * a.G;
+    float *dst = out + (size_t)slot * Q * a.G;
     int km = 0;
     for (int r = 0; r < cpt; ++r) {
         const int pidx = (blockIdx.y * cpt + r) * blockDim.x + threadIdx.x;
@@ -420,46 +473,12 @@ __global__ void __launch_bounds__(256, 3) k_step_pair(const float *__restrict__ 
         const int x0 = 2 * (pidx % half);
         int y, z;
         face_row_order<n>(pidx / half, y, z);
-        const int g = (z + 1) * plane + (y + 1) * row + x0;
-        const bool lo = x0 == 0, hi = x0 + 2 == n;
-        if (y == 0 || y == n - 1 || z == 0 || z == n - 1) {
-            const float K0 = step_cell<NT>(in, src, dst, snb, top, a, x0, y, z);
-            const float K1 = step_cell<NT>(in, src, dst, snb, top, a, x0 + 1, y, z);
-            km = max(km, max(__float_as_int(K0), __float_as_int(K1)));
-            continue;
-        }
-        // the pull of direction i for a row whose y and z sources lie in this block (or its
-        // ghost rows): the x-face lanes select their x neighbour
-        const auto inner = [&](int i) -> float2 {
-            const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-            const int off = cz * plane + cy * row;
-            const float *base = src + (i * G + g - off);
-            if (cx == 0) return *reinterpret_cast<const float2 *>(base);
-            const int ghost = (z - cz + 1) * (n + 2) + (y - cy + 1);
-            if (cx == 1) {  // cell x0 pulls from x0 - 1, cell x0 + 1 from x0
-                const float *alt = nbm >= 0 ? in + ((size_t)nbm * Q * G + (i * G + g - off - 1 + n))
-                                   : nbm == NB_GHOST ? src + (i * G + side_base(n, 0) + ghost)
-                                                     : src + (L::opp(i) * G + g);
-                return make_float2(*(lo ? alt : base - 1), *base);
-            }
-            // cell x0 pulls from x0 + 1, cell x0 + 1 from x0 + 2
-            const float *alt = nbp >= 0 ? in + ((size_t)nbp * Q * G + (i * G + g - off + 2 - n))
-                               : nbp == NB_GHOST ? src + (i * G + side_base(n, 1) + ghost)
-                                                 : src + (L::opp(i) * G + g + 1);
-            return make_float2(base[1], *(hi ? alt : base + 2));
-        };
-        float2 df[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) df[i] = __fadd2_rn(inner(i), f2(-weight<L, float>(i)));
-        const float2 K = relax_pair<L, 1, 1>([&](int i) { return df[i]; },
-                                             [&](int i) { return df[i]; }, a.omega,
-                                             [&](int i, float2 v) {
-                                                 *reinterpret_cast<float2 *>(dst + (i * G + g)) = v;
-                                             });
+        const float2 K = pair_row_step<NT>(in, src, dst, snb, top, a, x0, y, z);
         km = max(km, max(__float_as_int(K.x), __float_as_int(K.y)));
     }
     block_max_flush(km, kmax, slot, threadIdx.x & 31);
 }
+
 
 // Where the fused restriction writes: the coarser level's current buffer, the coarse slot of every
 // fine block, and the rescaling of the non-equilibrium part 2 (tau_c - 1) / (tau_f - 1).
@@ -469,6 +488,58 @@ struct RestrictArgs {
     int Gc;
     float scale;
 };
+
+// The finest level's second sub-step with the restriction onto the next coarser level fused, for
+// NT = 8, 16, 32, 64: one thread owns a 2 x 2 x 2 brick of fine cells (an x pair in two rows and
+// two planes), steps its four row pairs as k_step_pair does and sums each population's
+// post-collision values in registers; the coarse cell under the brick becomes their average with
+// f^neq rescaled, as in k_restrict (summed in another order), so the restriction's second pass
+// over the fine level is not needed and no thread waits for another.  Bricks come in the coarse
+// block's interior-rows-first order, so that most warps take one kind of gather.
+template <int NT>
+__global__ void __launch_bounds__(256, 2)
+    k_step_pair_restrict(const float *__restrict__ in, float *__restrict__ out,
+                         const int *__restrict__ nbr, const StepArgs a, int cpt, float *kmax,
+                         const RestrictArgs r) {
+    __shared__ int snb[27];
+    const int slot = blockIdx.x;
+    if (threadIdx.x < 27) snb[threadIdx.x] = nbr[27 * slot + threadIdx.x];
+    __syncthreads();
+    constexpr int NC = NT / 2, nbrick = NC * NC * NC;
+    const bool top = snb[NB_TOP] == NB_WALL;
+    const float *src = in + (size_t)slot * Q * a.G;
+    float *dst = out + (size_t)slot * Q * a.G;
+    float *coarse = r.coarse + (size_t)r.cslot[slot] * Q * r.Gc;
+    int km = 0;
+    for (int k = 0; k < cpt; ++k) {
+        const int b = (blockIdx.y * cpt + k) * blockDim.x + threadIdx.x;
+        if (b >= nbrick) break;
+        const int xc = b % NC;
+        int yc, zc;
+        face_row_order<NC>(b / NC, yc, zc);
+        float acc[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) acc[i] = 0.f;
+#pragma unroll 1
+        for (int q4 = 0; q4 < 4; ++q4) {
+            const float2 K = pair_row_step<NT>(in, src, dst, snb, top, a, 2 * xc, 2 * yc + (q4 & 1),
+                                               2 * zc + (q4 >> 1),
+                                               [&](int i, float2 v) { acc[i] += v.x + v.y; });
+            km = max(km, max(__float_as_int(K.x), __float_as_int(K.y)));
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) acc[i] *= 0.125f;
+        float rho, ux, uy, uz;
+        moments19(acc, rho, ux, uy, uz);
+        const int gc = ((zc + 1) * (NC + 2) + (yc + 1)) * NC + xc;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const float fe = feq19(i, rho, ux, uy, uz);
+            coarse[i * r.Gc + gc] = fe + r.scale * (acc[i] - fe);
+        }
+    }
+    block_max_flush(km, kmax, slot, threadIdx.x & 31);
+}
 
 // The tiled step of the finest level's second sub-step fused with the restriction onto the next
 // coarser level (NT = 16, 32, 64: bricks one plane deep; zc even).  Each 2 x 2 x 2 group of fine
@@ -844,6 +915,37 @@ cudaError_t launch_step_restrict(const Mesh &m, int l, int zc, cudaStream_t s, i
     }
 }
 
+template <int NT>
+cudaError_t launch_brick(const Mesh &m, int l, int threads, int cpt, cudaStream_t s, int src) {
+    const Level &L = m.lv[l], &C = m.lv[l - 1];
+    RestrictArgs r;
+    r.coarse = C.buf[C.cur];
+    r.cslot = L.cslot;
+    r.Gc = C.G;
+    r.scale = (float)(2.0 * (C.tau - 1.0) / (L.tau - 1.0));
+    const int nbrick = (NT / 2) * (NT / 2) * (NT / 2);
+    const dim3 grid(L.nslot, (nbrick + threads * cpt - 1) / (threads * cpt));
+    k_step_pair_restrict<NT><<<grid, threads, 0, s>>>(L.buf[src], L.buf[src ^ 1], L.nbr,
+                                                       step_args(m, l), cpt, L.kmax, r);
+    return cudaGetLastError();
+}
+
+// The brick form of the fused step + restriction of level l onto l - 1 (n = 8, 16, 32, 64).
+cudaError_t launch_step_restrict_brick(const Mesh &m, int l, int threads, int cpt, cudaStream_t s,
+                                       int src) {
+    switch (m.lv[l].n) {
+        case 8: return launch_brick<8>(m, l, threads, cpt, s, src);
+        case 16: return launch_brick<16>(m, l, threads, cpt, s, src);
+        case 32: return launch_brick<32>(m, l, threads, cpt, s, src);
+        case 64: return launch_brick<64>(m, l, threads, cpt, s, src);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+bool can_fuse_brick(const Mesh &m, int l) {
+    return l == m.lmax && l > 0 && has_tiled(m.lv[l].n) && m.lv[l - 1].nrestrict > 0;
+}
+
 bool can_fuse(const Mesh &m, int l) {
     const int n = m.lv[l].n;
     return l == m.lmax && l > 0 && (n == 16 || n == 32 || n == 64) && m.lv[l - 1].nrestrict > 0;
@@ -891,7 +993,10 @@ int advance(Mesh &m, int l, float theta, cudaStream_t *ss) {
     MLCK(cudaGetLastError(), "ghost fill");
     MLCK(cudaMemsetAsync(L.kmax, 0, sizeof(float) * L.nslot, s), "memset(kmax)");
     MLCK(cudaEventRecord(m.ev_pre[l], s), "cudaEventRecord");
-    if (L.fuse && theta > 0.f)  // the second sub-step of the finest level restricts as it steps
+    if (L.fuse_brick && theta > 0.f)  // the finest level's second sub-step restricts as it steps
+        MLCK(launch_step_restrict_brick(m, l, L.brick_threads, L.brick_cpt, s, L.cur),
+             "level step + restriction");
+    else if (L.fuse && theta > 0.f)
         MLCK(launch_step_restrict(m, l, L.fuse_zc, s, L.cur), "level step + restriction");
     else
         MLCK(launch_step(m, l, L.form, L.threads, L.cpt, L.zc, s, L.cur), "level step");
@@ -903,7 +1008,7 @@ int advance(Mesh &m, int l, float theta, cudaStream_t *ss) {
         if (st != LBM_OK) return st;
         const Level &F = m.lv[l + 1];
         if (F.nslot > 0) MLCK(cudaStreamWaitEvent(s, m.ev_done[l + 1], 0), "cudaStreamWaitEvent");
-        if (L.nrestrict && !F.fuse) {
+        if (L.nrestrict && !F.fuse && !F.fuse_brick) {
             const float scale = (float)(2.0 * (L.tau - 1.0) / (F.tau - 1.0));
             k_restrict<<<blocks_for(L.nrestrict, 128), 128, 0, s>>>(
                 L.restricts, L.nrestrict, L.buf[L.cur], L.G, F.buf[F.cur], F.P, F.plane, F.G,
@@ -989,13 +1094,54 @@ int autotune(Mesh &m, int l, cudaStream_t s) {
             L.zc = c.zc;
         }
     }
-    // finest level: the restriction stays a separate kernel unless the mesh's fusion setting
-    // forces the fused step + restriction (measured slower on the benchmark mesh: 3.45 against
-    // 2.65 ms per cycle)
+    // finest level: the restriction onto the next coarser level as a separate kernel after the
+    // second sub-step, or fused into that sub-step -- the tiled form (forced only: measured slower
+    // on the benchmark mesh, 3.45 against 2.65 ms per cycle) or the brick form, timed against the
+    // separate step + restriction unless a setting forces one
     L.fuse = false;
+    L.fuse_brick = false;
     if (can_fuse(m, l) && m.fusion == 2) {
         L.fuse = true;
         L.fuse_zc = 4;
+    }
+    if (can_fuse_brick(m, l) && (m.fusion == 0 || m.fusion == 3)) {
+        const Level &C = m.lv[l - 1];
+        const float scale = (float)(2.0 * (C.tau - 1.0) / (L.tau - 1.0));
+        const auto time_it = [&](auto &&launch, float *ms) -> int {
+            for (int k = 0; k < 2; ++k) MLCK(launch(), "autotune");
+            MLCK(cudaEventRecord(e0, s), "cudaEventRecord");
+            for (int k = 0; k < 3; ++k) MLCK(launch(), "autotune");
+            MLCK(cudaEventRecord(e1, s), "cudaEventRecord");
+            MLCK(cudaEventSynchronize(e1), "cudaEventSynchronize");
+            MLCK(cudaEventElapsedTime(ms, e0, e1), "cudaEventElapsedTime");
+            return LBM_OK;
+        };
+        float sep = 0.f;
+        int st = time_it([&]() -> cudaError_t {
+            cudaError_t e = launch_step(m, l, L.form, L.threads, L.cpt, L.zc, s, L.cur);
+            if (e != cudaSuccess) return e;
+            k_restrict<<<blocks_for(C.nrestrict, 128), 128, 0, s>>>(
+                C.restricts, C.nrestrict, C.buf[C.cur], C.G, L.buf[L.cur ^ 1], L.P, L.plane, L.G,
+                scale);
+            return cudaGetLastError();
+        }, &sep);
+        if (st != LBM_OK) return st;
+        float bestb = 1e30f;
+        const int nbrick = (L.n / 2) * (L.n / 2) * (L.n / 2);
+        const int shapes[][2] = {{128, 1}, {128, 2}, {256, 1}, {256, 2}};
+        for (const auto &c : shapes) {
+            if (c[0] * c[1] > 2 * nbrick && !(c[0] == 128 && c[1] == 1)) continue;
+            float ms = 0.f;
+            st = time_it([&]() { return launch_step_restrict_brick(m, l, c[0], c[1], s, L.cur); },
+                         &ms);
+            if (st != LBM_OK) return st;
+            if (ms < bestb) {
+                bestb = ms;
+                L.brick_threads = c[0];
+                L.brick_cpt = c[1];
+            }
+        }
+        L.fuse_brick = m.fusion == 3 || bestb < sep;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1258,7 +1404,7 @@ int schedule(const Mesh *m, int l, int *form, int *planes, int *fused) {
     const Level &L = m->lv[l];
     if (form) *form = L.form;
     if (planes) *planes = L.form == FORM_TILED ? L.zc : 0;
-    if (fused) *fused = L.fuse ? L.fuse_zc : 0;
+    if (fused) *fused = L.fuse ? L.fuse_zc : (L.fuse_brick ? 1 : 0);
     return LBM_OK;
 }
 

@@ -196,19 +196,38 @@ def test_bench_mesh_full_size_one_cycle(L):
     g.close()
 
 
-@pytest.mark.parametrize("fusion", ["SEPARATE", "FUSED"])
+@pytest.mark.parametrize("fusion", ["SEPARATE", "FUSED", "BRICK"])
 def test_fused_restriction_matches_oracle(L, fusion):
     """A 2-level mesh whose finest blocks have 16 cells per edge, with the restriction onto level 0
-    as a separate kernel and fused into the finest level's second sub-step: both against the FP64
-    oracle after 10 cycles (the fused form sums the 8 fine cells in another order)."""
+    as a separate kernel and fused into the finest level's second sub-step (tiled form, brick
+    form): each against the FP64 oracle after 10 cycles (the fused forms sum the 8 fine cells in
+    other orders)."""
     leaf = np.zeros((3, 3, 4), np.int8)
     leaf[1, 2, 1:3] = 1
     leaf[2, 2, 2] = 1
     edge, lmax, tau, cycles = 16, 1, 0.6, 10
     g = L.BlockMesh(leaf, edge, lmax, tau, lid=(0.1, 0.02),
                     fusion=getattr(L, "LBM_FUSION_" + fusion))
-    assert g.schedule(1)[2] == (4 if fusion == "FUSED" else 0)
+    assert g.schedule(1)[2] == {"SEPARATE": 0, "FUSED": 4, "BRICK": 1}[fusion]
     o = O.MultiLevel(leaf, edge, lmax, tau, lid=(0.1, 0.0, 0.02))
+    bm = g.step(cycles, block_max=True)
+    o.cycles(cycles)
+    for level in range(lmax + 1):
+        assert rel(g.leaf_field(level), o.leaf_field(level)) < 2e-6, level
+    assert rel(bm, o.block_max()) < 1e-4
+    g.close()
+
+
+@pytest.mark.parametrize("edge", [16, 32])
+def test_brick_restriction_three_levels(L, edge):
+    """The brick form of the fused restriction on the 3-level lid-driven mesh (finest blocks of 8
+    and 16 cells per edge: with 8, every brick touches a block face; the x-face lanes select their
+    neighbour), with graph replay, against the FP64 oracle after 8 cycles."""
+    leaf = three_level_leaf()
+    lmax, tau, cycles = 2, 0.6, 8
+    g = L.BlockMesh(leaf, edge // 2, lmax, tau, lid=(0.1, 0.02), fusion=L.LBM_FUSION_BRICK)
+    assert g.schedule(2)[2] == 1
+    o = O.MultiLevel(leaf, edge // 2, lmax, tau, lid=(0.1, 0.0, 0.02))
     bm = g.step(cycles, block_max=True)
     o.cycles(cycles)
     for level in range(lmax + 1):
