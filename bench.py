@@ -341,8 +341,10 @@ def run_blocks(args, w, ws, rank, local):
     tau = tau_of(w)
     form = getattr(L, "LBM_STEP_FORM_" + args.step_form.upper())
     fusion = getattr(L, "LBM_FUSION_" + args.fusion.upper())
+    schedule = getattr(L, "LBM_SCHEDULE_" + args.schedule.upper())
     mesh = L.BlockMesh(leaf, w["block"], w["lmax"], tau, lid=(w["u"], 0.0), step_form=form,
-                       fusion=fusion)
+                       fusion=fusion, schedule=schedule)
+    persistent = mesh.cycle_form() == L.LBM_SCHEDULE_PERSISTENT
     info = [mesh.info(l) for l in range(w["lmax"] + 1)]
     updates = info[0][5]  # cell updates per cycle over all levels
     for _ in range(args.warmup):
@@ -381,7 +383,9 @@ def run_blocks(args, w, ws, rank, local):
                    "step_schedule": [dict(zip(("form", "planes", "fused_planes"),
                                               mesh.schedule(l))) for l in range(w["lmax"] + 1)],
                    "cell_updates_per_cycle": updates, "n_eff": n_eff,
-                   "uniform_finest_cells": w["n"] ** 3, "step": "one level-0 cycle (graph)",
+                   "uniform_finest_cells": w["n"] ** 3,
+                   "step": ("one level-0 cycle (one persistent launch, replayed as a graph)"
+                            if persistent else "one level-0 cycle (graph of separate launches)"),
                    "timing": (f"{len(reps)} repeats of {args.steps} cycles (>= {args.min_time} s of "
                               "device time), median"),
                    "l2": "level buffers > 129 MB L2, no flush"},
@@ -394,8 +398,12 @@ def run_blocks(args, w, ws, rank, local):
         # per cycle: level l takes 2^l steps, each finer one a ghost fill before every step,
         # and 2^l restrictions onto level l from the level below it
         "repeats": len(reps),
-        "gpu_launches": len(reps) * args.steps * sum(
-            (1 << l) * (1 + (l > 0)) + ((1 << l) if l < w["lmax"] and info[l + 1][2] > 0 else 0)
+        # per cycle, graph form: level l takes 2^l steps, a finer one a ghost fill before every
+        # step, and 2^l restrictions onto level l unless the finer level's second sub-step does
+        # them (brick or tiled fused form); persistent form: one launch per cycle
+        "gpu_launches": len(reps) * args.steps if persistent else len(reps) * args.steps * sum(
+            (1 << l) * (1 + (l > 0)) + ((1 << l) if l < w["lmax"] and info[l + 1][2] > 0
+                                        and mesh.schedule(l + 1)[2] == 0 else 0)
             for l in range(w["lmax"] + 1) if info[l][2] > 0),
         "clocks": clocks,
     }
@@ -1021,6 +1029,9 @@ def main():
     ap.add_argument("--fusion", default="auto", choices=["auto", "separate", "fused", "brick"],
                     help="multi-level workload: the finest level's restriction as a separate "
                          "kernel or fused into its second sub-step (default: the library's)")
+    ap.add_argument("--schedule", default="auto", choices=["auto", "graph", "persistent"],
+                    help="multi-level workload: a cycle as a graph of separate launches or one "
+                         "persistent launch (default: timed at mesh build)")
     ap.add_argument("--step-form", default="auto",
                     choices=["auto", "flat", "tiled", "select", "pair"],
                     help="multi-level workload: force one form of the level step kernel on the "

@@ -405,6 +405,23 @@ LBM_API int lbm_blocks_info(lbm_t *h, int level, int *n, double *tau, int *nbloc
 #define LBM_FUSION_FUSED 2
 #define LBM_FUSION_BRICK 3
 LBM_API int lbm_blocks_set_fusion(lbm_t *h, int mode);
+/* How a cycle runs: a captured graph of the separate launches (LBM_SCHEDULE_GRAPH; the levels on
+ * streams of their own, ordered by events), or one persistent launch (LBM_SCHEDULE_PERSISTENT):
+ * persistent CTAs claim the cycle's tasks -- ghost fills, level steps, restrictions -- in the order
+ * the graph enqueues them and wait, device-side and bounded, for the phases each task depends on
+ * (replayed from a captured graph of that launch when graphs are on).  LBM_SCHEDULE_AUTO (default)
+ * times both when the mesh is built and keeps the faster; the persistent form is not available
+ * with LBM_FUSION_FUSED.  A wait that runs out (limit: lbm_debug_set_wait_limit, default one
+ * second; lbm_debug_hold_copies makes every wait run out) stops the launch; the next call that
+ * synchronises (lbm_blocks_step with block maxima, lbm_blocks_get) returns LBM_ETIMEOUT and the
+ * mesh must be rebuilt.  Applies from the next mesh build: an existing mesh is discarded.
+ * lbm_blocks_cycle_form returns the form the current mesh uses (LBM_SCHEDULE_GRAPH or
+ * LBM_SCHEDULE_PERSISTENT), LBM_ESTATE without a mesh. */
+#define LBM_SCHEDULE_AUTO 0
+#define LBM_SCHEDULE_GRAPH 1
+#define LBM_SCHEDULE_PERSISTENT 2
+LBM_API int lbm_blocks_set_schedule(lbm_t *h, int mode);
+LBM_API int lbm_blocks_cycle_form(lbm_t *h);
 /* Form of every level's step kernel: LBM_STEP_FORM_AUTO (default) times the candidate forms and
  * launch shapes of each level when the mesh is built and keeps the fastest; the others force one
  * form on every level whose block edge it applies to (the remaining levels stay timed):

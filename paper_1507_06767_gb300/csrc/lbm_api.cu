@@ -116,6 +116,7 @@ struct lbm_s {
     lbm::ml::Mesh *mesh = nullptr;
     int blocks_fusion = 0;  // LBM_FUSION_* for the next mesh build
     int blocks_step_form = 0;  // LBM_STEP_FORM_* for the next mesh build
+    int blocks_schedule = 0;   // LBM_SCHEDULE_* for the next mesh build
 
     // graph cache: runs of RUN_LEN[k] plain steps (k = 0: 2 steps, 1: 16 steps), by starting
     // buffer
@@ -1038,27 +1039,57 @@ LBM_API int lbm_blocks_step(lbm_t *h, const lbm_level_batch *batch) {
         lbm::ml::destroy(h->mesh);
         h->mesh = nullptr;
     }
+    // the error word of the persistent cycle's bounded waits
+    int st = ensure_scratch(h);
+    if (st != LBM_OK) return st;
     if (!h->mesh) {
         const double lid[3] = {h->lid_x, 0.0, h->lid_z};
-        int st = lbm::ml::build(&h->mesh, nb, batch->edge, batch->lmax, batch->leaf, h->tau, lid,
-                                h->periodic, h->blocks_fusion, h->blocks_step_form - 1,
-                                h->stream);
+        st = lbm::ml::build(&h->mesh, nb, batch->edge, batch->lmax, batch->leaf, h->tau, lid,
+                            h->periodic, h->blocks_fusion, h->blocks_step_form - 1,
+                            h->blocks_schedule, h->stream);
         if (st != LBM_OK) return st;
     }
-    int st = lbm::ml::run_cycles(h->mesh, batch->cycles, h->stream, h->graphs != 0);
+    st = lbm::ml::run_cycles(h->mesh, batch->cycles, h->stream, h->graphs != 0, h->err_dev,
+                             h->wait_ns, h->hold_copies);
     if (st != LBM_OK) return st;
     if (batch->block_max) {
-        st = lbm::ml::block_max(h->mesh, batch->block_max, h->stream);
+        st = lbm::ml::block_max(h->mesh, batch->block_max, h->stream);  // synchronises
         if (st != LBM_OK) return st;
+        if (*(volatile int *)h->err_host)
+            return fail(LBM_ETIMEOUT, "a bounded wait of the persistent cycle ran out; the mesh "
+                                      "state is not valid (rebuild it)");
     }
     return LBM_OK;
+}
+
+LBM_API int lbm_blocks_set_schedule(lbm_t *h, int mode) {
+    CHECK_H(h);
+    if (mode < LBM_SCHEDULE_AUTO || mode > LBM_SCHEDULE_PERSISTENT)
+        return fail(LBM_EINVAL, "schedule must be LBM_SCHEDULE_AUTO, _GRAPH or _PERSISTENT");
+    if (h->mesh) {  // applies to the next build
+        CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+        lbm::ml::destroy(h->mesh);
+        h->mesh = nullptr;
+    }
+    h->blocks_schedule = mode;
+    return LBM_OK;
+}
+
+LBM_API int lbm_blocks_cycle_form(lbm_t *h) {
+    CHECK_H(h);
+    if (!h->mesh) return fail(LBM_ESTATE, "no multi-level mesh (call lbm_blocks_step first)");
+    return lbm::ml::uses_persistent(h->mesh) ? LBM_SCHEDULE_PERSISTENT : LBM_SCHEDULE_GRAPH;
 }
 
 LBM_API int lbm_blocks_get(lbm_t *h, int level, int block, double *out_host) {
     CHECK_H(h);
     if (!h->mesh) return fail(LBM_ESTATE, "no multi-level mesh (call lbm_blocks_step first)");
     if (!out_host) return fail(LBM_EINVAL, "NULL output");
-    return lbm::ml::get_block(h->mesh, level, block, out_host, h->stream);
+    const int st = lbm::ml::get_block(h->mesh, level, block, out_host, h->stream);  // synchronises
+    if (st == LBM_OK && h->err_host && *(volatile int *)h->err_host)
+        return fail(LBM_ETIMEOUT, "a bounded wait of the persistent cycle ran out; the mesh state "
+                                  "is not valid (rebuild it)");
+    return st;
 }
 
 LBM_API int lbm_blocks_set(lbm_t *h, int level, int block, const double *in_host) {

@@ -79,11 +79,17 @@ struct Mesh;
 // fusion: 0 automatic (separate), 1 separate restriction, 2 fused into the finest level's step;
 // step_form: -1 autotuned, else the step kernel form forced where it applies (LBM_STEP_FORM_*
 // minus one)
+// schedule: 0 timed, 1 graph of separate launches, 2 one persistent launch per cycle
 int build(Mesh **out, const int nb[3], int edge, int lmax, const int8_t *leaf, double tau_fine,
-          const double lid[3], int periodic, int fusion, int step_form, cudaStream_t s);
+          const double lid[3], int periodic, int fusion, int step_form, int schedule,
+          cudaStream_t s);
 void destroy(Mesh *m);
 bool same_layout(const Mesh *m, const int nb[3], int edge, int lmax, const int8_t *leaf);
-int run_cycles(Mesh *m, int cycles, cudaStream_t s, bool graphs);
+// err: device-visible error word set when a bounded wait of the persistent kernel runs out (may
+// be null); wait_ns: that wait's limit (0: one second); hold: test hook (every wait runs out)
+int run_cycles(Mesh *m, int cycles, cudaStream_t s, bool graphs, int *err, unsigned long long wait_ns,
+               int hold);
+bool uses_persistent(const Mesh *m);
 int block_max(Mesh *m, double *out_host, cudaStream_t s);
 int get_block(Mesh *m, int l, int b, double *out, cudaStream_t s);
 int set_block(Mesh *m, int l, int b, const double *in, cudaStream_t s);

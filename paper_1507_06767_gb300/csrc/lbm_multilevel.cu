@@ -126,6 +126,22 @@ struct Mesh {
     cudaEvent_t ev_fork = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // by level-0 buffer parity
     long long cycles = 0;
+    // persistent form of a cycle (one k_cycle launch): phase table and dependency lists per
+    // level-0 buffer parity, the counters, the launch width, and whether cycles use it
+    struct Plan {
+        void *phases = nullptr;  // device PPhase[nph]
+        int *deps = nullptr;
+        int nph = 0, ntask = 0;
+    } plan[2];
+    int *pctr = nullptr;  // device: 2 + phases counters
+    int pctr_len = 0;
+    int pk_grid = 0;
+    bool persistent = false;
+    int schedule = 0;  // LBM_SCHEDULE_* of the build
+    // error word and wait settings the persistent graphs were captured with
+    int *err = nullptr;
+    unsigned long long wait_ns = 0;
+    int hold = 0;
 };
 
 // ---------------------------------------------------------------------------------- kernels
@@ -152,15 +168,32 @@ __device__ __forceinline__ float feq19(int i, float rho, float ux, float uy, flo
     return weight<D3Q19, float>(i) * rho * (1.f + 3.f * cu + 4.5f * cu * cu - 1.5f * uu);
 }
 
+// How the level kernels read populations.  LdPlain leaves the load form to the compiler: in the
+// graph form of a cycle each launch only reads buffers that no CTA of the same launch writes.  LdL2
+// reads through L2 (ld.global.cg), the point of coherence: the persistent cycle kernel reads
+// buffers that other CTAs of the same launch wrote, which neither the read-only path nor an L1
+// line filled earlier in the launch may serve.
+struct LdPlain {
+    __device__ __forceinline__ float operator()(const float *p) const { return *p; }
+    __device__ __forceinline__ float2 pair(const float *p) const {
+        return *reinterpret_cast<const float2 *>(p);
+    }
+};
+struct LdL2 {
+    __device__ __forceinline__ float operator()(const float *p) const { return __ldcg(p); }
+    __device__ __forceinline__ float2 pair(const float *p) const {
+        return __ldcg(reinterpret_cast<const float2 *>(p));
+    }
+};
+
 // coarse -> fine ghost: interpolate in space and time, rescale the non-equilibrium part.  BLEND:
 // theta > 0 (the coarse states before and after its step are mixed); without it only the state
 // before the coarse step is read.
-template <bool BLEND>
-__global__ void k_interp(const InterpTask *t, int n, float *fine, int Gf, const float *cprev,
-                         const float *ccur, int Gc, float theta, float scale) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const InterpTask it = t[k];
+template <bool BLEND, class LD = LdPlain>
+__device__ __forceinline__ void interp_one(const InterpTask &it, float *fine, int Gf,
+                                           const float *cprev, const float *ccur, int Gc,
+                                           float theta, float scale) {
+    const LD ld;
     float acc[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -169,9 +202,9 @@ __global__ void k_interp(const InterpTask *t, int n, float *fine, int Gf, const 
         for (int s = 0; s < 8; ++s) {
             const int o = it.src[s] + i * Gc;
             if (BLEND)
-                a += it.w[s] * ((1.f - theta) * cprev[o] + theta * ccur[o]);
+                a += it.w[s] * ((1.f - theta) * ld(cprev + o) + theta * ld(ccur + o));
             else
-                a += it.w[s] * cprev[o];
+                a += it.w[s] * ld(cprev + o);
         }
         acc[i] = a;
     }
@@ -184,19 +217,27 @@ __global__ void k_interp(const InterpTask *t, int n, float *fine, int Gf, const 
     }
 }
 
-// level cells under the finer level: average of 8 fine cells, non-equilibrium part rescaled
-__global__ void k_restrict(const RestrictTask *t, int n, float *coarse, int Gc, const float *fine,
-                           int pf, int planef, int Gf, float scale) {
+template <bool BLEND>
+__global__ void k_interp(const InterpTask *t, int n, float *fine, int Gf, const float *cprev,
+                         const float *ccur, int Gc, float theta, float scale) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    const RestrictTask r = t[k];
+    interp_one<BLEND>(t[k], fine, Gf, cprev, ccur, Gc, theta, scale);
+}
+
+// level cells under the finer level: average of 8 fine cells, non-equilibrium part rescaled
+template <class LD = LdPlain>
+__device__ __forceinline__ void restrict_one(const RestrictTask &r, float *coarse, int Gc,
+                                             const float *fine, int pf, int planef, int Gf,
+                                             float scale) {
+    const LD ld;
     const int row = pf, plane = planef;
     float avg[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const float *f = fine + r.fine + i * Gf;
-        avg[i] = 0.125f * (f[0] + f[1] + f[row] + f[row + 1] + f[plane] + f[plane + 1] +
-                           f[plane + row] + f[plane + row + 1]);
+        avg[i] = 0.125f * (ld(f) + ld(f + 1) + ld(f + row) + ld(f + row + 1) + ld(f + plane) +
+                           ld(f + plane + 1) + ld(f + plane + row) + ld(f + plane + row + 1));
     }
     float rho, ux, uy, uz;
     moments19(avg, rho, ux, uy, uz);
@@ -205,6 +246,13 @@ __global__ void k_restrict(const RestrictTask *t, int n, float *coarse, int Gc, 
         const float fe = feq19(i, rho, ux, uy, uz);
         coarse[r.dst + i * Gc] = fe + scale * (avg[i] - fe);
     }
+}
+
+__global__ void k_restrict(const RestrictTask *t, int n, float *coarse, int Gc, const float *fine,
+                           int pf, int planef, int Gf, float scale) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    restrict_one(t[k], coarse, Gc, fine, pf, planef, Gf, scale);
 }
 
 struct StepArgs {
@@ -223,7 +271,7 @@ struct NoVisit {
 // the branch is warp-uniform) take a gather where a pull along x that leaves the block selects its
 // address (x-neighbour block, interpolated x-ghost column or the wall's bounce-back) instead of
 // branching on it, so the two face lanes of a row do not split the warp.
-template <int NT, bool XSEL = false, class Also = NoVisit>
+template <int NT, bool XSEL = false, class LD = LdPlain, class Also = NoVisit>
 __device__ __forceinline__ float step_cell(const float *__restrict__ in, const float *src,
                                            float *dst, const int *snb, bool top,
                                            const StepArgs &a, int x, int y, int z,
@@ -253,7 +301,7 @@ __device__ __forceinline__ float step_cell(const float *__restrict__ in, const f
                         : src + (size_t)L::opp(i) * G + g;
                 p = (cx == 1 ? xl : xh) ? q : p;
             }
-            df[i] = *p - weight<L, float>(i);
+            df[i] = LD()(p) - weight<L, float>(i);
         }
         return relax_cell<L, 1, 1>(df, a.omega, [&](int i, float d) {
             const float v = d + weight<L, float>(i);
@@ -269,18 +317,19 @@ __device__ __forceinline__ float step_cell(const float *__restrict__ in, const f
         const int dz = (cz == 1 && zl) ? -1 : ((cz == -1 && zh) ? 1 : 0);
         float v;
         if ((dx | dy | dz) == 0) {
-            v = src[i * G + g - (cz * plane + cy * row + cx)];
+            v = LD()(src + (i * G + g - (cz * plane + cy * row + cx)));
         } else {
             const int nb = snb[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)];
             if (nb >= 0) {
-                v = in[(size_t)nb * Q * G + i * G + (z - cz - dz * n + 1) * plane +
-                       (y - cy - dy * n + 1) * row + (x - cx - dx * n)];
+                v = LD()(in + ((size_t)nb * Q * G + i * G + (z - cz - dz * n + 1) * plane +
+                               (y - cy - dy * n + 1) * row + (x - cx - dx * n)));
             } else if (nb == NB_GHOST) {
                 // interpolated ghost: an x-ghost column, or a ghost row / plane of the block
-                v = src[i * G + (dx != 0 ? side_base(n, dx > 0) + (z - cz + 1) * (n + 2) + (y - cy + 1)
-                                         : g - (cz * plane + cy * row + cx))];
+                v = LD()(src + (i * G + (dx != 0 ? side_base(n, dx > 0) + (z - cz + 1) * (n + 2) +
+                                                       (y - cy + 1)
+                                                 : g - (cz * plane + cy * row + cx))));
             } else {
-                v = src[L::opp(i) * G + g];
+                v = LD()(src + (L::opp(i) * G + g));
                 if (dy == 1 && top)
                     v += 6.f * weight<L, float>(i) * ((float)cx * a.lid_x + (float)cz * a.lid_z);
             }
@@ -405,7 +454,7 @@ __global__ void __launch_bounds__(256, 4) k_step_tiled(const float *__restrict__
 struct NoVisit2 {
     __device__ __forceinline__ void operator()(int, float2) const {}
 };
-template <int NT, class Also = NoVisit2>
+template <int NT, class LD = LdPlain, class Also = NoVisit2>
 __device__ __forceinline__ float2 pair_row_step(const float *__restrict__ in, const float *src,
                                                 float *dst, const int *snb, bool top,
                                                 const StepArgs &a, int x0, int y, int z,
@@ -417,10 +466,10 @@ __device__ __forceinline__ float2 pair_row_step(const float *__restrict__ in, co
     const int g = (z + 1) * plane + (y + 1) * row + x0;
     const bool lo = x0 == 0, hi = x0 + 2 == n;
     if (y == 0 || y == n - 1 || z == 0 || z == n - 1) {
-        const float K0 = step_cell<NT>(in, src, dst, snb, top, a, x0, y, z,
-                                       [&](int i, float v) { also(i, make_float2(v, 0.f)); });
-        const float K1 = step_cell<NT>(in, src, dst, snb, top, a, x0 + 1, y, z,
-                                       [&](int i, float v) { also(i, make_float2(v, 0.f)); });
+        const float K0 = step_cell<NT, false, LD>(in, src, dst, snb, top, a, x0, y, z,
+                                                  [&](int i, float v) { also(i, make_float2(v, 0.f)); });
+        const float K1 = step_cell<NT, false, LD>(in, src, dst, snb, top, a, x0 + 1, y, z,
+                                                  [&](int i, float v) { also(i, make_float2(v, 0.f)); });
         return make_float2(K0, K1);
     }
     // the pull of direction i for a row whose y and z sources lie in this block (or its ghost
@@ -429,19 +478,19 @@ __device__ __forceinline__ float2 pair_row_step(const float *__restrict__ in, co
         const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
         const int off = cz * plane + cy * row;
         const float *base = src + (i * G + g - off);
-        if (cx == 0) return *reinterpret_cast<const float2 *>(base);
+        if (cx == 0) return LD().pair(base);
         const int ghost = (z - cz + 1) * (n + 2) + (y - cy + 1);
         if (cx == 1) {  // cell x0 pulls from x0 - 1, cell x0 + 1 from x0
             const float *alt = nbm >= 0 ? in + ((size_t)nbm * Q * G + (i * G + g - off - 1 + n))
                                : nbm == NB_GHOST ? src + (i * G + side_base(n, 0) + ghost)
                                                  : src + (L::opp(i) * G + g);
-            return make_float2(*(lo ? alt : base - 1), *base);
+            return make_float2(LD()(lo ? alt : base - 1), LD()(base));
         }
         // cell x0 pulls from x0 + 1, cell x0 + 1 from x0 + 2
         const float *alt = nbp >= 0 ? in + ((size_t)nbp * Q * G + (i * G + g - off + 2 - n))
                            : nbp == NB_GHOST ? src + (i * G + side_base(n, 1) + ghost)
                                              : src + (L::opp(i) * G + g + 1);
-        return make_float2(base[1], *(hi ? alt : base + 2));
+        return make_float2(LD()(base + 1), LD()(hi ? alt : base + 2));
     };
     float2 df[Q];
 #pragma unroll
@@ -496,6 +545,41 @@ struct RestrictArgs {
 // f^neq rescaled, as in k_restrict (summed in another order), so the restriction's second pass
 // over the fine level is not needed and no thread waits for another.  Bricks come in the coarse
 // block's interior-rows-first order, so that most warps take one kind of gather.
+// One brick of k_step_pair_restrict: brick b (coarse-block order) of the fine block whose source
+// and destination are src / dst, its coarse cell written to `coarse` (the coarse block); returns
+// the largest sensor bits of its 8 cells.
+template <int NT, class LD = LdPlain>
+__device__ __forceinline__ int brick_one(const float *__restrict__ in, const float *src, float *dst,
+                                         const int *snb, bool top, const StepArgs &a, int b,
+                                         float *coarse, int Gc, float scale) {
+    constexpr int NC = NT / 2;
+    const int xc = b % NC;
+    int yc, zc;
+    face_row_order<NC>(b / NC, yc, zc);
+    float acc[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) acc[i] = 0.f;
+    int km = 0;
+#pragma unroll 1
+    for (int q4 = 0; q4 < 4; ++q4) {
+        const float2 K = pair_row_step<NT, LD>(in, src, dst, snb, top, a, 2 * xc, 2 * yc + (q4 & 1),
+                                               2 * zc + (q4 >> 1),
+                                               [&](int i, float2 v) { acc[i] += v.x + v.y; });
+        km = max(km, max(__float_as_int(K.x), __float_as_int(K.y)));
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) acc[i] *= 0.125f;
+    float rho, ux, uy, uz;
+    moments19(acc, rho, ux, uy, uz);
+    const int gc = ((zc + 1) * (NC + 2) + (yc + 1)) * NC + xc;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float fe = feq19(i, rho, ux, uy, uz);
+        coarse[i * Gc + gc] = fe + scale * (acc[i] - fe);
+    }
+    return km;
+}
+
 template <int NT>
 __global__ void __launch_bounds__(256, 2)
     k_step_pair_restrict(const float *__restrict__ in, float *__restrict__ out,
@@ -514,29 +598,7 @@ __global__ void __launch_bounds__(256, 2)
     for (int k = 0; k < cpt; ++k) {
         const int b = (blockIdx.y * cpt + k) * blockDim.x + threadIdx.x;
         if (b >= nbrick) break;
-        const int xc = b % NC;
-        int yc, zc;
-        face_row_order<NC>(b / NC, yc, zc);
-        float acc[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) acc[i] = 0.f;
-#pragma unroll 1
-        for (int q4 = 0; q4 < 4; ++q4) {
-            const float2 K = pair_row_step<NT>(in, src, dst, snb, top, a, 2 * xc, 2 * yc + (q4 & 1),
-                                               2 * zc + (q4 >> 1),
-                                               [&](int i, float2 v) { acc[i] += v.x + v.y; });
-            km = max(km, max(__float_as_int(K.x), __float_as_int(K.y)));
-        }
-#pragma unroll
-        for (int i = 0; i < Q; ++i) acc[i] *= 0.125f;
-        float rho, ux, uy, uz;
-        moments19(acc, rho, ux, uy, uz);
-        const int gc = ((zc + 1) * (NC + 2) + (yc + 1)) * NC + xc;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const float fe = feq19(i, rho, ux, uy, uz);
-            coarse[i * r.Gc + gc] = fe + r.scale * (acc[i] - fe);
-        }
+        km = max(km, brick_one<NT>(in, src, dst, snb, top, a, b, coarse, r.Gc, r.scale));
     }
     block_max_flush(km, kmax, slot, threadIdx.x & 31);
 }
@@ -603,6 +665,197 @@ __global__ void __launch_bounds__(256, 4)
         }
     }
     block_max_flush(km, kmax, slot, tid & 31);
+}
+
+// ------------------------------------------------------------------ persistent cycle kernel
+// One launch runs a whole cycle: the work of the graph form (ghost fills, level steps, restrictions,
+// the zeroing of each level's sensor maxima) as a list of phases in the order the graph enqueues
+// them, each split into tasks of 256 threads.  Persistent CTAs claim tasks in index order with an
+// atomic counter; a task first waits until every phase it depends on has completed all its tasks
+// (per-phase counters, read with acquire), then runs, then counts itself complete (fence, atomic
+// add).  The dependencies are those of the graph form: each level's phases in order (its stream)
+// and the cross-level waits on a coarser level's state before or after its step and on the
+// restriction onto a finer level.  Every dependency points to an earlier phase, so when a CTA
+// claims task t every task before t is held by a running CTA and finishes: no co-residency is
+// needed.  Populations are read through L2 (LdL2), as buffers written by other CTAs of the same
+// launch are read.  Every wait is bounded: one that runs out raises the abort flag and the error
+// word, and every CTA then stops claiming tasks.
+constexpr int PH_ZERO = 0;      // zero the level's per-slot sensor maxima
+constexpr int PH_INTERP0 = 1;   // ghost fill from the coarser level before its step (theta 0)
+constexpr int PH_INTERPB = 2;   // ghost fill blended in time (theta 1/2)
+constexpr int PH_STEP = 3;      // level step
+constexpr int PH_BRICK = 4;     // finest level's second sub-step with the restriction fused
+constexpr int PH_RESTRICT = 5;  // restriction onto the level from the next finer one
+constexpr int PK_THREADS = 256;
+constexpr unsigned long long PK_WAIT_NS = 1000000000ull;
+
+struct PPhase {
+    int kind, level, ntask, task0, dep0, ndep;
+    int chunks;          // step / brick: tasks per slot
+    int nslot;           // zero: slots
+    const float *in;     // step / brick: source buffer; ghost fill: coarse state before its step;
+                         // restriction: the finer level's state
+    float *out;          // step / brick: destination; ghost fill: the fine level's buffer;
+                         // restriction: the level's current buffer
+    const float *aux;    // ghost fill: the coarse state after its step
+    const int *nbr;      // step / brick: neighbour table
+    float *kmax;         // step / brick / zero: per-slot sensor maxima
+    const void *items;   // ghost fill / restriction: task list
+    int nitems;
+    int G2, P2, plane2;  // ghost fill: coarse G; restriction: finer G, row pitch, plane size
+    float theta, scale;
+    StepArgs a;          // the level's step arguments (a.G: the level's G)
+    float *coarse;       // brick: the coarser level's current buffer, its slots and G
+    const int *cslot;
+    int Gc;
+};
+
+__device__ __forceinline__ int ld_acquire_gpu(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long pk_now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <int NT>
+__device__ __forceinline__ void pk_step(const PPhase &P, int slot, int chunk, const int *snb) {
+    const bool top = snb[NB_TOP] == NB_WALL;
+    const float *src = P.in + (size_t)slot * Q * P.a.G;
+    float *dst = P.out + (size_t)slot * Q * P.a.G;
+    int km = 0;
+    if constexpr (NT == 0) {
+        const int n = P.a.n, c = chunk * PK_THREADS + threadIdx.x;
+        if (c < n * n * n) {
+            const float K = step_cell<0, false, LdL2>(P.in, src, dst, snb, top, P.a, c % n,
+                                                      (c / n) % n, c / (n * n));
+            km = __float_as_int(K);
+        }
+    } else {
+        constexpr int half = NT / 2, npair = NT * NT * NT / 2;
+        const int pidx = chunk * PK_THREADS + threadIdx.x;
+        if (pidx < npair) {
+            int y, z;
+            face_row_order<NT>(pidx / half, y, z);
+            const float2 K =
+                pair_row_step<NT, LdL2>(P.in, src, dst, snb, top, P.a, 2 * (pidx % half), y, z);
+            km = max(__float_as_int(K.x), __float_as_int(K.y));
+        }
+    }
+    block_max_flush(km, P.kmax, slot, threadIdx.x & 31);
+}
+
+template <int NT>
+__device__ __forceinline__ void pk_brick(const PPhase &P, int slot, int chunk, const int *snb) {
+    const bool top = snb[NB_TOP] == NB_WALL;
+    const float *src = P.in + (size_t)slot * Q * P.a.G;
+    float *dst = P.out + (size_t)slot * Q * P.a.G;
+    float *coarse = P.coarse + (size_t)P.cslot[slot] * Q * P.Gc;
+    const int b = chunk * PK_THREADS + threadIdx.x;
+    int km = 0;
+    if (b < (NT / 2) * (NT / 2) * (NT / 2))
+        km = brick_one<NT, LdL2>(P.in, src, dst, snb, top, P.a, b, coarse, P.Gc, P.scale);
+    block_max_flush(km, P.kmax, slot, threadIdx.x & 31);
+}
+
+__device__ __forceinline__ void pk_run(const PPhase &P, int k, int *snb) {
+    const int tid = threadIdx.x;
+    if (P.kind == PH_ZERO) {
+        for (int i = tid; i < P.nslot; i += PK_THREADS) P.kmax[i] = 0.f;
+        return;
+    }
+    if (P.kind == PH_INTERP0 || P.kind == PH_INTERPB) {
+        const int j = k * PK_THREADS + tid;
+        if (j >= P.nitems) return;
+        const InterpTask &it = static_cast<const InterpTask *>(P.items)[j];
+        if (P.kind == PH_INTERPB)
+            interp_one<true, LdL2>(it, P.out, P.a.G, P.in, P.aux, P.G2, P.theta, P.scale);
+        else
+            interp_one<false, LdL2>(it, P.out, P.a.G, P.in, P.aux, P.G2, P.theta, P.scale);
+        return;
+    }
+    if (P.kind == PH_RESTRICT) {
+        const int j = k * PK_THREADS + tid;
+        if (j >= P.nitems) return;
+        restrict_one<LdL2>(static_cast<const RestrictTask *>(P.items)[j], P.out, P.a.G, P.in, P.P2,
+                           P.plane2, P.G2, P.scale);
+        return;
+    }
+    // step or brick: the block's neighbour table in shared memory
+    const int slot = k / P.chunks, chunk = k % P.chunks;
+    if (tid < 27) snb[tid] = P.nbr[27 * slot + tid];
+    __syncthreads();
+    if (P.kind == PH_STEP) {
+        switch (P.a.n) {
+            case 8: pk_step<8>(P, slot, chunk, snb); break;
+            case 16: pk_step<16>(P, slot, chunk, snb); break;
+            case 32: pk_step<32>(P, slot, chunk, snb); break;
+            case 64: pk_step<64>(P, slot, chunk, snb); break;
+            default: pk_step<0>(P, slot, chunk, snb); break;
+        }
+    } else {
+        switch (P.a.n) {
+            case 8: pk_brick<8>(P, slot, chunk, snb); break;
+            case 16: pk_brick<16>(P, slot, chunk, snb); break;
+            case 32: pk_brick<32>(P, slot, chunk, snb); break;
+            default: pk_brick<64>(P, slot, chunk, snb); break;
+        }
+    }
+}
+
+// ctr: [0] next task, [1] abort flag, [2 + p] completed tasks of phase p (zeroed before a launch).
+// hold != 0 (a test hook) makes every dependency unreachable, so the first wait runs out.
+__global__ void __launch_bounds__(PK_THREADS, 2)
+    k_cycle(const PPhase *__restrict__ ph, int nph, const int *__restrict__ deps, int ntask,
+            int *ctr, int *err, unsigned long long wait_ns, int hold) {
+    __shared__ int s_task, s_phase;
+    __shared__ int snb[27];
+    int *next = ctr, *abort_flag = ctr + 1, *done = ctr + 2;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int t = atomicAdd(next, 1);
+            int p = -1;
+            if (t < ntask && !ld_acquire_gpu(abort_flag)) {
+                p = 0;
+                while (p + 1 < nph && ph[p + 1].task0 <= t) ++p;
+                const int dep0 = ph[p].dep0, ndep = ph[p].ndep;
+                for (int k = 0; k < ndep && p >= 0; ++k) {
+                    const int d = deps[dep0 + k];
+                    const int target = hold ? 0x7fffffff : ph[d].ntask;
+                    if (ld_acquire_gpu(done + d) >= target) continue;
+                    const unsigned long long t0 = pk_now_ns();
+                    while (ld_acquire_gpu(done + d) < target) {
+                        if (ld_acquire_gpu(abort_flag)) {
+                            p = -1;
+                            break;
+                        }
+                        if (pk_now_ns() - t0 > wait_ns) {
+                            atomicExch(abort_flag, 1);
+                            if (err) atomicOr(err, 1);
+                            p = -1;
+                            break;
+                        }
+                        __nanosleep(128);
+                    }
+                }
+            }
+            s_task = t;
+            s_phase = p;
+        }
+        __syncthreads();
+        const int p = s_phase;
+        if (p < 0) break;
+        pk_run(ph[p], s_task - ph[p].task0, snb);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();  // this task's stores before its count
+            atomicAdd(done + p, 1);
+        }
+    }
 }
 
 __global__ void k_fill_rest(float *buf, int nslot, int G) {
@@ -1170,10 +1423,281 @@ int capture(Mesh &m, cudaGraphExec_t *out) {
     return st;
 }
 
+
+}  // namespace
+int run_cycles(Mesh *m, int cycles, cudaStream_t s, bool graphs, int *err, unsigned long long wait_ns,
+               int hold);
+namespace {
+
+// --------------------------------------------------------- persistent cycle: the phase plan
+// The phases of one cycle and their dependencies, built by walking the cycle exactly as advance()
+// enqueues it: each level is a stream whose phases depend on the one before (stream order), and
+// the cross-level event waits of advance() become dependencies on the phase recorded there.
+struct PlanBuilder {
+    std::vector<PPhase> ph;
+    std::vector<std::vector<int>> dl;
+    int last[MAXL];
+    // what a stream's next phase waits for besides the stream's last phase
+    std::vector<int> pend[MAXL];
+    // the events of advance(): the phases a wait on them covers (a stream's last phase and the
+    // waits pending on it when the event was recorded, as a CUDA event recorded after a
+    // cudaStreamWaitEvent covers the awaited work)
+    std::vector<int> pre[MAXL], post[MAXL], done[MAXL];
+    PlanBuilder() {
+        for (int l = 0; l < MAXL; ++l) last[l] = -1;
+    }
+    std::vector<int> record(int s) const {
+        std::vector<int> e = pend[s];
+        if (last[s] >= 0) e.push_back(last[s]);
+        return e;
+    }
+    void wait(int s, const std::vector<int> &ev) { pend[s].insert(pend[s].end(), ev.begin(), ev.end()); }
+    void add(int s, PPhase p) {
+        std::vector<int> d = pend[s];
+        pend[s].clear();
+        if (last[s] >= 0) d.push_back(last[s]);
+        std::sort(d.begin(), d.end());
+        d.erase(std::unique(d.begin(), d.end()), d.end());
+        ph.push_back(p);
+        dl.push_back(d);
+        last[s] = (int)ph.size() - 1;
+    }
+};
+
+int step_chunks(int n) {
+    return has_tiled(n) ? (n * n * n / 2 + PK_THREADS - 1) / PK_THREADS
+                        : (n * n * n + PK_THREADS - 1) / PK_THREADS;
+}
+
+void plan_advance(Mesh &m, PlanBuilder &b, int l, float theta) {
+    Level &L = m.lv[l];
+    if (L.nslot == 0) return;
+    if (l > 0) {
+        b.wait(l, theta > 0.f ? b.post[l - 1] : b.pre[l - 1]);
+        if (L.ninterp) {
+            const Level &C = m.lv[l - 1];
+            PPhase p = {};
+            p.kind = theta > 0.f ? PH_INTERPB : PH_INTERP0;
+            p.level = l;
+            p.items = L.interps;
+            p.nitems = L.ninterp;
+            p.ntask = (L.ninterp + PK_THREADS - 1) / PK_THREADS;
+            p.out = L.buf[L.cur];
+            p.in = C.buf[C.cur ^ 1];
+            p.aux = C.buf[C.cur];
+            p.a = step_args(m, l);
+            p.G2 = C.G;
+            p.theta = theta;
+            p.scale = (float)((L.tau - 1.0) / (2.0 * (C.tau - 1.0)));
+            b.add(l, p);
+        }
+    }
+    PPhase z = {};
+    z.kind = PH_ZERO;
+    z.level = l;
+    z.ntask = 1;
+    z.kmax = L.kmax;
+    z.nslot = L.nslot;
+    b.add(l, z);
+    b.pre[l] = b.record(l);
+    PPhase st = {};
+    st.level = l;
+    st.in = L.buf[L.cur];
+    st.out = L.buf[L.cur ^ 1];
+    st.nbr = L.nbr;
+    st.kmax = L.kmax;
+    st.a = step_args(m, l);
+    if (L.fuse_brick && theta > 0.f) {
+        const Level &C = m.lv[l - 1];
+        st.kind = PH_BRICK;
+        st.chunks = ((L.n / 2) * (L.n / 2) * (L.n / 2) + PK_THREADS - 1) / PK_THREADS;
+        st.coarse = C.buf[C.cur];
+        st.cslot = L.cslot;
+        st.Gc = C.G;
+        st.scale = (float)(2.0 * (C.tau - 1.0) / (L.tau - 1.0));
+    } else {
+        st.kind = PH_STEP;
+        st.chunks = step_chunks(L.n);
+    }
+    st.ntask = L.nslot * st.chunks;
+    b.add(l, st);
+    L.cur ^= 1;
+    b.post[l] = b.record(l);
+    if (l < m.lmax) {
+        plan_advance(m, b, l + 1, 0.f);
+        plan_advance(m, b, l + 1, 0.5f);
+        const Level &F = m.lv[l + 1];
+        if (F.nslot > 0) b.wait(l, b.done[l + 1]);
+        if (L.nrestrict && !F.fuse && !F.fuse_brick) {
+            PPhase r = {};
+            r.kind = PH_RESTRICT;
+            r.level = l;
+            r.items = L.restricts;
+            r.nitems = L.nrestrict;
+            r.ntask = (L.nrestrict + PK_THREADS - 1) / PK_THREADS;
+            r.out = L.buf[L.cur];
+            r.in = F.buf[F.cur];
+            r.a = step_args(m, l);
+            r.G2 = F.G;
+            r.P2 = F.P;
+            r.plane2 = F.plane;
+            r.scale = (float)(2.0 * (L.tau - 1.0) / (F.tau - 1.0));
+            b.add(l, r);
+        }
+    }
+    b.done[l] = b.record(l);
+}
+
+// Build and upload the plan of a cycle starting at the current buffer parities (restored after).
+int build_plan(Mesh &m, Mesh::Plan *out) {
+    int saved[MAXL];
+    for (int l = 0; l <= m.lmax; ++l) saved[l] = m.lv[l].cur;
+    PlanBuilder b;
+    plan_advance(m, b, 0, 0.f);
+    for (int l = 0; l <= m.lmax; ++l) m.lv[l].cur = saved[l];
+    std::vector<int> flat;
+    int task = 0;
+    for (size_t k = 0; k < b.ph.size(); ++k) {
+        b.ph[k].task0 = task;
+        task += b.ph[k].ntask;
+        b.ph[k].dep0 = (int)flat.size();
+        b.ph[k].ndep = (int)b.dl[k].size();
+        for (int d : b.dl[k]) flat.push_back(d);
+    }
+    out->nph = (int)b.ph.size();
+    out->ntask = task;
+    if (flat.empty()) flat.push_back(0);
+    MLCK(lbm::dev_alloc(&out->phases, sizeof(PPhase) * b.ph.size()), "cudaMalloc(plan)");
+    MLCK(cudaMemcpy(out->phases, b.ph.data(), sizeof(PPhase) * b.ph.size(), cudaMemcpyHostToDevice),
+         "cudaMemcpy(plan)");
+    MLCK(lbm::dev_alloc(&out->deps, sizeof(int) * flat.size()), "cudaMalloc(plan deps)");
+    MLCK(cudaMemcpy(out->deps, flat.data(), sizeof(int) * flat.size(), cudaMemcpyHostToDevice),
+         "cudaMemcpy(plan deps)");
+    if (2 + out->nph > m.pctr_len) {
+        cudaFree(m.pctr);
+        m.pctr = nullptr;
+        m.pctr_len = 0;
+        MLCK(lbm::dev_alloc(&m.pctr, sizeof(int) * (2 + out->nph)), "cudaMalloc(plan counters)");
+        m.pctr_len = 2 + out->nph;
+    }
+    return LBM_OK;
+}
+
+// The plan of the current level-0 parity and the launch width, made before any stream capture
+// (they allocate and copy).
+int ensure_plan(Mesh &m) {
+    Mesh::Plan &P = m.plan[m.lv[0].cur];
+    if (!P.phases) {
+        const int st = build_plan(m, &P);
+        if (st != LBM_OK) return st;
+    }
+    if (!m.pk_grid) {
+        int per_sm = 0, dev = 0, nsm = 0;
+        MLCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cycle, PK_THREADS, 0),
+             "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+        MLCK(cudaGetDevice(&dev), "cudaGetDevice");
+        MLCK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "sm count");
+        m.pk_grid = std::max(1, per_sm * nsm);
+    }
+    return LBM_OK;
+}
+
+// The persistent form of one cycle at the current level-0 parity: clear the counters, one launch.
+int persistent_cycle(Mesh &m, cudaStream_t s) {
+    const int st = ensure_plan(m);
+    if (st != LBM_OK) return st;
+    Mesh::Plan &P = m.plan[m.lv[0].cur];
+    MLCK(cudaMemsetAsync(m.pctr, 0, sizeof(int) * (2 + P.nph), s), "memset(plan counters)");
+    k_cycle<<<std::min(m.pk_grid, std::max(P.ntask, 1)), PK_THREADS, 0, s>>>(
+        static_cast<const PPhase *>(P.phases), P.nph, P.deps, P.ntask, m.pctr, m.err,
+        m.wait_ns ? m.wait_ns : PK_WAIT_NS, m.hold);
+    MLCK(cudaGetLastError(), "persistent cycle");
+    // the launch covers a whole cycle: level 0 flips once, the finer levels an even number of times
+    m.lv[0].cur ^= 1;
+    return LBM_OK;
+}
+
+int capture_persistent(Mesh &m, cudaGraphExec_t *out) {
+    const int pst = ensure_plan(m);
+    if (pst != LBM_OK) return pst;
+    cudaStream_t cap;
+    MLCK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "cudaStreamCreate");
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    int st = LBM_OK;
+    if (e == cudaSuccess) {
+        const int cur0 = m.lv[0].cur;
+        st = persistent_cycle(m, cap);
+        m.lv[0].cur = cur0;
+        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        if (e2 != cudaSuccess && st == LBM_OK) st = report_cuda_error(e2, "graph capture");
+    } else {
+        st = report_cuda_error(e, "graph capture");
+    }
+    if (st == LBM_OK) {
+        e = cudaGraphInstantiate(out, g, 0);
+        if (e != cudaSuccess) st = report_cuda_error(e, "cudaGraphInstantiate");
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    return st;
+}
+
+void drop_cycle_graphs(Mesh &m) {
+    for (int k = 0; k < 2; ++k) {
+        if (m.graph[k]) cudaGraphExecDestroy(m.graph[k]);
+        m.graph[k] = nullptr;
+    }
+}
+
+// Time a few cycles in each form (graph of separate launches, persistent kernel) and keep the
+// faster, unless the schedule setting forces one; the persistent form needs a restriction that is
+// a separate kernel or the brick form (not the tiled fused form).
+int choose_schedule(Mesh &m, cudaStream_t s) {
+    bool can = true;
+    for (int l = 0; l <= m.lmax; ++l)
+        if (m.lv[l].fuse) can = false;
+    if (m.schedule == 1 || !can) {
+        m.persistent = false;
+        return LBM_OK;
+    }
+    if (m.schedule == 2) {
+        m.persistent = true;
+        return LBM_OK;
+    }
+    cudaEvent_t e0, e1;
+    MLCK(cudaEventCreate(&e0), "cudaEventCreate");
+    MLCK(cudaEventCreate(&e1), "cudaEventCreate");
+    float ms[2] = {0.f, 0.f};
+    int st = LBM_OK;
+    for (int form = 0; form < 2 && st == LBM_OK; ++form) {
+        m.persistent = form == 1;
+        drop_cycle_graphs(m);
+        for (int k = 0; k < 5 && st == LBM_OK; ++k) {
+            if (k == 2) MLCK(cudaEventRecord(e0, s), "cudaEventRecord");
+            st = run_cycles(&m, 1, s, true, nullptr, 0, 0);
+        }
+        if (st != LBM_OK) break;
+        MLCK(cudaEventRecord(e1, s), "cudaEventRecord");
+        MLCK(cudaEventSynchronize(e1), "cudaEventSynchronize");
+        MLCK(cudaEventElapsedTime(&ms[form], e0, e1), "cudaEventElapsedTime");
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != LBM_OK) return st;
+    m.persistent = ms[1] < ms[0];
+    drop_cycle_graphs(m);
+    return LBM_OK;
+}
 }  // namespace
 
 void destroy(Mesh *m) {
     if (!m) return;
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(m->plan[k].phases);
+        cudaFree(m->plan[k].deps);
+    }
+    cudaFree(m->pctr);
     for (int k = 0; k < 2; ++k)
         if (m->graph[k]) cudaGraphExecDestroy(m->graph[k]);
     if (m->ev_fork) cudaEventDestroy(m->ev_fork);
@@ -1201,7 +1725,8 @@ bool same_layout(const Mesh *m, const int nb[3], int edge, int lmax, const int8_
 }
 
 int build(Mesh **out, const int nb[3], int edge, int lmax, const int8_t *leaf, double tau_fine,
-          const double lid[3], int periodic, int fusion, int step_form, cudaStream_t s) {
+          const double lid[3], int periodic, int fusion, int step_form, int schedule,
+          cudaStream_t s) {
     *out = nullptr;
     if (lmax < 0 || lmax >= MAXL) return report_error(LBM_EINVAL, "lmax must be 0, 1 or 2");
     if (edge < 1 || edge % (1 << lmax) != 0 || edge / (1 << lmax) < 2)
@@ -1276,6 +1801,10 @@ int build(Mesh **out, const int nb[3], int edge, int lmax, const int8_t *leaf, d
     for (int l = 0; l <= lmax && st == LBM_OK; ++l) st = build_tasks(*m, l);
     for (int l = 0; l <= lmax && st == LBM_OK; ++l) st = autotune(*m, l, s);
     if (st == LBM_OK) {
+        m->schedule = schedule;
+        st = choose_schedule(*m, s);
+    }
+    if (st == LBM_OK) {
         // the state at build time is rest, f_i = w_i everywhere (the trial steps are overwritten)
         for (int l = 0; l <= lmax; ++l) {
             if (m->lv[l].nslot == 0) continue;
@@ -1295,14 +1824,23 @@ int build(Mesh **out, const int nb[3], int edge, int lmax, const int8_t *leaf, d
     return LBM_OK;
 }
 
-int run_cycles(Mesh *m, int cycles, cudaStream_t s, bool graphs) {
+int run_cycles(Mesh *m, int cycles, cudaStream_t s, bool graphs, int *err, unsigned long long wait_ns,
+               int hold) {
+    if (err != m->err || wait_ns != m->wait_ns || hold != m->hold) {
+        // the persistent kernel takes these as launch arguments: captured graphs are stale
+        m->err = err;
+        m->wait_ns = wait_ns;
+        m->hold = hold;
+        if (m->persistent) drop_cycle_graphs(*m);
+    }
     for (int c = 0; c < cycles; ++c) {
         if (graphs) {
             const int par = m->lv[0].cur;
             if (!m->graph[par]) {
                 int saved[MAXL];
                 for (int l = 0; l <= m->lmax; ++l) saved[l] = m->lv[l].cur;
-                const int st = capture(*m, &m->graph[par]);
+                const int st = m->persistent ? capture_persistent(*m, &m->graph[par])
+                                             : capture(*m, &m->graph[par]);
                 for (int l = 0; l <= m->lmax; ++l) m->lv[l].cur = saved[l];
                 if (st != LBM_OK) return st;
             }
@@ -1310,13 +1848,15 @@ int run_cycles(Mesh *m, int cycles, cudaStream_t s, bool graphs) {
             // a cycle flips level 0 once; finer levels step an even number of times
             m->lv[0].cur ^= 1;
         } else {
-            const int st = cycle(*m, s);
+            const int st = m->persistent ? persistent_cycle(*m, s) : cycle(*m, s);
             if (st != LBM_OK) return st;
         }
         m->cycles += 1;
     }
     return LBM_OK;
 }
+
+bool uses_persistent(const Mesh *m) { return m->persistent; }
 
 int block_max(Mesh *m, double *out_host, cudaStream_t s) {
     std::vector<int> ls(m->nblk), ll(m->nblk);

@@ -96,6 +96,8 @@ _SIGS = {
     "lbm_block_features": (_i, [_h, _i, _vp]),
     "lbm_blocks_set_fusion": (_i, [_h, _i]),
     "lbm_blocks_set_step_form": (_i, [_h, _i]),
+    "lbm_blocks_set_schedule": (_i, [_h, _i]),
+    "lbm_blocks_cycle_form": (_i, [_h]),
     "lbm_blocks_schedule": (_i, [_h, _i, ctypes.POINTER(_i), ctypes.POINTER(_i),
                                  ctypes.POINTER(_i)]),
     "lbm_net_create": (_vp, [_i, _i]),
@@ -364,6 +366,14 @@ def lbm_blocks_set_step_form(h, form: int) -> int:
     return _ck(_lib.lbm_blocks_set_step_form(h, int(form)), "lbm_blocks_set_step_form")
 
 
+def lbm_blocks_set_schedule(h, mode: int) -> int:
+    return _ck(_lib.lbm_blocks_set_schedule(h, int(mode)), "lbm_blocks_set_schedule")
+
+
+def lbm_blocks_cycle_form(h) -> int:
+    return _ck(_lib.lbm_blocks_cycle_form(h), "lbm_blocks_cycle_form")
+
+
 def lbm_blocks_schedule(h, level: int):
     """(form, planes, fused planes) of a level's step schedule; form 0 flat, 1 tiled, 2 flat with
     the address-select gather, 3 two cells per thread."""
@@ -566,7 +576,7 @@ class BlockMesh:
     """Multi-level block mesh on a handle: leaf[nbz, nby, nbx] leaf levels, block edge `edge`."""
 
     def __init__(self, leaf, edge, lmax, tau_fine, lid=(0.0, 0.0), periodic=0, graphs=True,
-                 fusion=None, step_form=None):
+                 fusion=None, step_form=None, schedule=None):
         import torch  # noqa: F401  (the caller's CUDA context)
 
         self.leaf = np.ascontiguousarray(leaf, dtype=np.int8)
@@ -581,7 +591,13 @@ class BlockMesh:
             lbm_blocks_set_fusion(self.h, int(fusion))
         if step_form is not None:
             lbm_blocks_set_step_form(self.h, int(step_form))
+        if schedule is not None:
+            lbm_blocks_set_schedule(self.h, int(schedule))
         self.step(0)
+
+    def cycle_form(self):
+        """LBM_SCHEDULE_GRAPH or LBM_SCHEDULE_PERSISTENT: how this mesh runs a cycle."""
+        return lbm_blocks_cycle_form(self.h)
 
     def schedule(self, level):
         return lbm_blocks_schedule(self.h, level)

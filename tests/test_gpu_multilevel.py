@@ -234,3 +234,83 @@ def test_brick_restriction_three_levels(L, edge):
         assert rel(g.leaf_field(level), o.leaf_field(level)) < 2e-6, level
     assert rel(bm, o.block_max()) < 1e-4
     g.close()
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+@pytest.mark.parametrize("fusion", ["SEPARATE", "BRICK"])
+def test_persistent_cycle_matches_oracle(L, graphs, fusion):
+    """One persistent launch per cycle (LBM_SCHEDULE_PERSISTENT): the cycle's ghost fills, level
+    steps and restrictions as tasks of one kernel, ordered by device-side counters.  The 3-level
+    lid-driven mesh (finest blocks of 16 cells, so the brick form applies) against the FP64 oracle
+    after 10 cycles, replayed from a captured graph and launched directly."""
+    leaf = three_level_leaf()
+    edge, lmax, tau, cycles = 16, 2, 0.6, 10
+    g = L.BlockMesh(leaf, edge, lmax, tau, lid=(0.1, 0.02), graphs=graphs,
+                    fusion=getattr(L, "LBM_FUSION_" + fusion), schedule=L.LBM_SCHEDULE_PERSISTENT)
+    assert g.cycle_form() == L.LBM_SCHEDULE_PERSISTENT
+    o = O.MultiLevel(leaf, edge, lmax, tau, lid=(0.1, 0.0, 0.02))
+    bm = g.step(cycles, block_max=True)
+    o.cycles(cycles)
+    for level in range(lmax + 1):
+        assert rel(g.leaf_field(level), o.leaf_field(level)) < 2e-6, level
+    assert rel(bm, o.block_max()) < 1e-4
+    g.close()
+
+
+def test_persistent_cycle_bench_mesh_one_cycle(L):
+    """The full-size multi-level benchmark mesh run by the persistent cycle: every block of every
+    level from a seeded perturbed state, one cycle, against the FP64 oracle (2e-6)."""
+    import bench
+    from tests import seeded
+
+    w = bench.WORKLOADS["d3q19_blocks_512_3level"]
+    leaf = bench.block_placement(w, L)
+    tau = bench.tau_of(w)
+    g = L.BlockMesh(leaf, w["block"], w["lmax"], tau, lid=(w["u"], 0.0),
+                    schedule=L.LBM_SCHEDULE_PERSISTENT)
+    o = O.MultiLevel(leaf, w["block"], w["lmax"], tau, lid=(w["u"], 0.0, 0.0))
+    _, wts, _ = O.lattice(19)
+    rng = seeded.rng(4097)
+    flat = leaf.reshape(-1)
+    for level in range(w["lmax"] + 1):
+        n = g.info(level)[0]
+        for b in np.where(flat >= level)[0]:
+            f = wts[:, None, None, None] * (1.0 + rng.uniform(-0.01, 0.01, size=(19, n, n, n)))
+            g.set_block(level, int(b), f)
+            o.set_block(level, int(b), f)
+    g.step(1)
+    o.cycles(1)
+    worst = 0.0
+    for level in range(w["lmax"] + 1):
+        for b in np.where(flat >= level)[0]:
+            ref = o.get_block(level, int(b))
+            worst = max(worst, float(np.abs(g.get_block(level, int(b)) - ref).max() /
+                                     np.abs(ref).max()))
+    assert worst < 2e-6, worst
+    g.close()
+
+
+def test_persistent_cycle_wait_runs_out(L):
+    """A bounded device wait of the persistent cycle that runs out: lbm_debug_hold_copies makes every
+    dependency wait unreachable (nothing faults; the waiting CTA gives up after the limit, raises
+    the abort flag and every CTA stops claiming tasks), so lbm_blocks_step with block maxima returns
+    LBM_ETIMEOUT.  After a rebuild the mesh runs correctly again on the same context."""
+    leaf = three_level_leaf()
+    edge, lmax, tau = 8, 2, 0.6
+    g = L.BlockMesh(leaf, edge, lmax, tau, lid=(0.1, 0.02), schedule=L.LBM_SCHEDULE_PERSISTENT)
+    L.lbm_debug_set_wait_limit(g.h, 1_000_000)  # 1 ms
+    L.lbm_debug_hold_copies(g.h, 1)
+    with pytest.raises(L.LbmError) as ei:
+        g.step(1, block_max=True)
+    assert ei.value.status == L.LBM_ETIMEOUT
+    L.lbm_debug_hold_copies(g.h, 0)
+    L.lbm_debug_set_wait_limit(g.h, 0)
+    L.lbm_reset(g.h)  # clears the error word
+    L.lbm_blocks_set_schedule(g.h, L.LBM_SCHEDULE_PERSISTENT)  # discards the mesh
+    bm = g.step(6, block_max=True)  # rebuilt from rest
+    o = O.MultiLevel(leaf, edge, lmax, tau, lid=(0.1, 0.0, 0.02))
+    o.cycles(6)
+    for level in range(lmax + 1):
+        assert rel(g.leaf_field(level), o.leaf_field(level)) < 2e-6, level
+    assert rel(bm, o.block_max()) < 1e-4
+    g.close()
