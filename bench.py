@@ -354,7 +354,9 @@ def run_blocks(args, w, ws, rank, local):
     sampler = ClockSampler(None)
     sampler.start()
     time.sleep(0.3)
+    nvtx_push("timed")  # lets a profiler capture the timed loop alone (ncu --nvtx-include timed/)
     reps = timed_repeats(lambda: mesh.step(args.steps), stream, ws, sampler, args.min_time)
+    nvtx_pop()
     clocks = sampler.stop()
     ms = reduce_max(statistics.median(reps), ws)  # one repeat of args.steps cycles
     value = updates * args.steps * ws / (ms / 1e3) / 1e6

@@ -107,6 +107,7 @@ struct Level {
     // or the two-cell brick form (k_step_pair_restrict) with its own launch shape
     bool fuse_brick = false;
     int brick_threads = 256, brick_cpt = 1;
+    bool brick_smem = false;  // the brick sums in shared memory (k_step_pair_restrict_s)
     int *cslot = nullptr;  // device: per slot, the slot of the same block one level coarser
 };
 
@@ -548,24 +549,42 @@ struct RestrictArgs {
 // One brick of k_step_pair_restrict: brick b (coarse-block order) of the fine block whose source
 // and destination are src / dst, its coarse cell written to `coarse` (the coarse block); returns
 // the largest sensor bits of its 8 cells.
-template <int NT, class LD = LdPlain>
+// SACC: the 19 sums in this thread's column of a shared-memory array, sacc[i * stride] (fewer
+// registers, so more CTAs per SM), instead of registers.
+template <int NT, class LD = LdPlain, bool SACC = false>
 __device__ __forceinline__ int brick_one(const float *__restrict__ in, const float *src, float *dst,
                                          const int *snb, bool top, const StepArgs &a, int b,
-                                         float *coarse, int Gc, float scale) {
+                                         float *coarse, int Gc, float scale,
+                                         float *sacc = nullptr, int stride = 0) {
     constexpr int NC = NT / 2;
     const int xc = b % NC;
     int yc, zc;
     face_row_order<NC>(b / NC, yc, zc);
     float acc[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) acc[i] = 0.f;
     int km = 0;
+    if constexpr (SACC) {
 #pragma unroll 1
-    for (int q4 = 0; q4 < 4; ++q4) {
-        const float2 K = pair_row_step<NT, LD>(in, src, dst, snb, top, a, 2 * xc, 2 * yc + (q4 & 1),
-                                               2 * zc + (q4 >> 1),
-                                               [&](int i, float2 v) { acc[i] += v.x + v.y; });
-        km = max(km, max(__float_as_int(K.x), __float_as_int(K.y)));
+        for (int q4 = 0; q4 < 4; ++q4) {
+            const float2 K = pair_row_step<NT, LD>(
+                in, src, dst, snb, top, a, 2 * xc, 2 * yc + (q4 & 1), 2 * zc + (q4 >> 1),
+                [&](int i, float2 v) {
+                    float &c = sacc[i * stride];
+                    c = q4 ? c + (v.x + v.y) : v.x + v.y;
+                });
+            km = max(km, max(__float_as_int(K.x), __float_as_int(K.y)));
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) acc[i] = sacc[i * stride];
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) acc[i] = 0.f;
+#pragma unroll 1
+        for (int q4 = 0; q4 < 4; ++q4) {
+            const float2 K = pair_row_step<NT, LD>(
+                in, src, dst, snb, top, a, 2 * xc, 2 * yc + (q4 & 1), 2 * zc + (q4 >> 1),
+                [&](int i, float2 v) { acc[i] += v.x + v.y; });
+            km = max(km, max(__float_as_int(K.x), __float_as_int(K.y)));
+        }
     }
 #pragma unroll
     for (int i = 0; i < Q; ++i) acc[i] *= 0.125f;
@@ -599,6 +618,33 @@ __global__ void __launch_bounds__(256, 2)
         const int b = (blockIdx.y * cpt + k) * blockDim.x + threadIdx.x;
         if (b >= nbrick) break;
         km = max(km, brick_one<NT>(in, src, dst, snb, top, a, b, coarse, r.Gc, r.scale));
+    }
+    block_max_flush(km, kmax, slot, threadIdx.x & 31);
+}
+
+// The same with the 19 sums of each brick in shared memory (19 x blockDim floats), so that three
+// CTAs of 256 threads fit an SM without spilling.
+template <int NT>
+__global__ void __launch_bounds__(256, 3)
+    k_step_pair_restrict_s(const float *__restrict__ in, float *__restrict__ out,
+                           const int *__restrict__ nbr, const StepArgs a, int cpt, float *kmax,
+                           const RestrictArgs r) {
+    __shared__ int snb[27];
+    extern __shared__ float sacc[];
+    const int slot = blockIdx.x;
+    if (threadIdx.x < 27) snb[threadIdx.x] = nbr[27 * slot + threadIdx.x];
+    __syncthreads();
+    constexpr int NC = NT / 2, nbrick = NC * NC * NC;
+    const bool top = snb[NB_TOP] == NB_WALL;
+    const float *src = in + (size_t)slot * Q * a.G;
+    float *dst = out + (size_t)slot * Q * a.G;
+    float *coarse = r.coarse + (size_t)r.cslot[slot] * Q * r.Gc;
+    int km = 0;
+    for (int k = 0; k < cpt; ++k) {
+        const int b = (blockIdx.y * cpt + k) * blockDim.x + threadIdx.x;
+        if (b >= nbrick) break;
+        km = max(km, brick_one<NT, LdPlain, true>(in, src, dst, snb, top, a, b, coarse, r.Gc,
+                                                  r.scale, sacc + threadIdx.x, blockDim.x));
     }
     block_max_flush(km, kmax, slot, threadIdx.x & 31);
 }
@@ -1169,7 +1215,8 @@ cudaError_t launch_step_restrict(const Mesh &m, int l, int zc, cudaStream_t s, i
 }
 
 template <int NT>
-cudaError_t launch_brick(const Mesh &m, int l, int threads, int cpt, cudaStream_t s, int src) {
+cudaError_t launch_brick(const Mesh &m, int l, int threads, int cpt, bool smem, cudaStream_t s,
+                         int src) {
     const Level &L = m.lv[l], &C = m.lv[l - 1];
     RestrictArgs r;
     r.coarse = C.buf[C.cur];
@@ -1178,19 +1225,23 @@ cudaError_t launch_brick(const Mesh &m, int l, int threads, int cpt, cudaStream_
     r.scale = (float)(2.0 * (C.tau - 1.0) / (L.tau - 1.0));
     const int nbrick = (NT / 2) * (NT / 2) * (NT / 2);
     const dim3 grid(L.nslot, (nbrick + threads * cpt - 1) / (threads * cpt));
-    k_step_pair_restrict<NT><<<grid, threads, 0, s>>>(L.buf[src], L.buf[src ^ 1], L.nbr,
-                                                       step_args(m, l), cpt, L.kmax, r);
+    if (smem)
+        k_step_pair_restrict_s<NT><<<grid, threads, sizeof(float) * Q * threads, s>>>(
+            L.buf[src], L.buf[src ^ 1], L.nbr, step_args(m, l), cpt, L.kmax, r);
+    else
+        k_step_pair_restrict<NT><<<grid, threads, 0, s>>>(L.buf[src], L.buf[src ^ 1], L.nbr,
+                                                           step_args(m, l), cpt, L.kmax, r);
     return cudaGetLastError();
 }
 
 // The brick form of the fused step + restriction of level l onto l - 1 (n = 8, 16, 32, 64).
-cudaError_t launch_step_restrict_brick(const Mesh &m, int l, int threads, int cpt, cudaStream_t s,
-                                       int src) {
+cudaError_t launch_step_restrict_brick(const Mesh &m, int l, int threads, int cpt, bool smem,
+                                       cudaStream_t s, int src) {
     switch (m.lv[l].n) {
-        case 8: return launch_brick<8>(m, l, threads, cpt, s, src);
-        case 16: return launch_brick<16>(m, l, threads, cpt, s, src);
-        case 32: return launch_brick<32>(m, l, threads, cpt, s, src);
-        case 64: return launch_brick<64>(m, l, threads, cpt, s, src);
+        case 8: return launch_brick<8>(m, l, threads, cpt, smem, s, src);
+        case 16: return launch_brick<16>(m, l, threads, cpt, smem, s, src);
+        case 32: return launch_brick<32>(m, l, threads, cpt, smem, s, src);
+        case 64: return launch_brick<64>(m, l, threads, cpt, smem, s, src);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1247,7 +1298,7 @@ int advance(Mesh &m, int l, float theta, cudaStream_t *ss) {
     MLCK(cudaMemsetAsync(L.kmax, 0, sizeof(float) * L.nslot, s), "memset(kmax)");
     MLCK(cudaEventRecord(m.ev_pre[l], s), "cudaEventRecord");
     if (L.fuse_brick && theta > 0.f)  // the finest level's second sub-step restricts as it steps
-        MLCK(launch_step_restrict_brick(m, l, L.brick_threads, L.brick_cpt, s, L.cur),
+        MLCK(launch_step_restrict_brick(m, l, L.brick_threads, L.brick_cpt, L.brick_smem, s, L.cur),
              "level step + restriction");
     else if (L.fuse && theta > 0.f)
         MLCK(launch_step_restrict(m, l, L.fuse_zc, s, L.cur), "level step + restriction");
@@ -1382,18 +1433,23 @@ int autotune(Mesh &m, int l, cudaStream_t s) {
         float bestb = 1e30f;
         const int nbrick = (L.n / 2) * (L.n / 2) * (L.n / 2);
         const int shapes[][2] = {{128, 1}, {128, 2}, {256, 1}, {256, 2}};
-        for (const auto &c : shapes) {
-            if (c[0] * c[1] > 2 * nbrick && !(c[0] == 128 && c[1] == 1)) continue;
-            float ms = 0.f;
-            st = time_it([&]() { return launch_step_restrict_brick(m, l, c[0], c[1], s, L.cur); },
-                         &ms);
-            if (st != LBM_OK) return st;
-            if (ms < bestb) {
-                bestb = ms;
-                L.brick_threads = c[0];
-                L.brick_cpt = c[1];
+        for (int sm = 0; sm < 2; ++sm)
+            for (const auto &c : shapes) {
+                if (c[0] * c[1] > 2 * nbrick && !(c[0] == 128 && c[1] == 1)) continue;
+                float ms = 0.f;
+                st = time_it(
+                    [&]() {
+                        return launch_step_restrict_brick(m, l, c[0], c[1], sm == 1, s, L.cur);
+                    },
+                    &ms);
+                if (st != LBM_OK) return st;
+                if (ms < bestb) {
+                    bestb = ms;
+                    L.brick_threads = c[0];
+                    L.brick_cpt = c[1];
+                    L.brick_smem = sm == 1;
+                }
             }
-        }
         L.fuse_brick = m.fusion == 3 || bestb < sep;
     }
     cudaEventDestroy(e0);

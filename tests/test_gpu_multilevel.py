@@ -94,11 +94,17 @@ def test_step_forms_match_oracle(L, form, periodic):
     g.close()
 
 
-def test_graph_replay_is_bitwise_direct_launches(L):
+@pytest.mark.parametrize("schedule", ["GRAPH", "PERSISTENT"])
+def test_graph_replay_is_bitwise_direct_launches(L, schedule):
+    """Replaying a cycle from its captured graph gives the same bits as launching it directly.
+    The step form, the restriction and the schedule are fixed, so that both builds run the same
+    arithmetic (the autotuner may otherwise pick different forms in the two builds)."""
     leaf = three_level_leaf()
     out = []
     for graphs in (True, False):
-        g = L.BlockMesh(leaf, 8, 2, 0.6, lid=(0.1, 0.0), graphs=graphs)
+        g = L.BlockMesh(leaf, 8, 2, 0.6, lid=(0.1, 0.0), graphs=graphs,
+                        step_form=L.LBM_STEP_FORM_PAIR, fusion=L.LBM_FUSION_SEPARATE,
+                        schedule=getattr(L, "LBM_SCHEDULE_" + schedule))
         g.step(5)
         out.append([g.leaf_field(level) for level in range(3)])
         g.close()
