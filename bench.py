@@ -528,7 +528,8 @@ def run_learned(args, w, ws, rank, local):
     judged = []
     for (f, k, tau) in traces[w["train_seeds"]:]:
         judged.append(LN.judge(net, f, k, LN.threshold(tau, w["u"], n), w["fallback_below"]))
-    summary = {key: float(np.mean([j[key] for j in judged])) for key in judged[0]}
+    summary = {key: float(np.mean([j[key] for j in judged])) for key in judged[0]
+               if key != "per_regrid"}
 
     # timed loop on a fresh cavity at the mean Reynolds number of the range
     re = 0.5 * (w["re_range"][0] + w["re_range"][1])

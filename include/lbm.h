@@ -548,6 +548,31 @@ LBM_API int lbm_net_log_targets(const double *kmax_dev, long long n, float offse
 LBM_API int lbm_net_to_maxima(const float *y_dev, long long n, float offset, double *kmax_dev,
                               void *stream);
 /*
+ * Judge and fallback of a regrid driven by predicted flags (not in the paper; the exact sensor of
+ * Sec. 3.2 stays the judge).  lbm_flags_agreement writes to *out_dev the fraction of the n blocks
+ * whose flags in a_dev and b_dev are equal (1 for n = 0).  lbm_flags_judge_select takes the flags
+ * the previous regrid predicted for now (pred_prev_dev, or NULL at the first regrid), the exact
+ * flags now (exact_now_dev) and the flags predicted now for the next interval (pred_next_dev): the
+ * agreement of pred_prev with exact_now goes to *agreement_dev (NaN without pred_prev) and decides
+ * the flags written to used_dev -- pred_next if the agreement is at least min_agreement or there is
+ * no previous prediction, else exact_now, with *fell_back_dev = 1 (agreement_dev and fell_back_dev
+ * may be NULL).  All pointers are device memory; both calls queue one kernel on `stream`.
+ *
+ * lbm_gather_rows copies rows idx_dev[0..count) of src_dev (nrows rows of row_bytes bytes, a
+ * multiple of 4) to consecutive rows of dst_dev, e.g. the minibatch of a training step; an index
+ * outside [0, nrows) is not read and sets *bad_dev to 1 (the caller clears it beforehand).
+ */
+LBM_API int lbm_flags_agreement(const int8_t *a_dev, const int8_t *b_dev, int n, double *out_dev,
+                                void *stream);
+LBM_API int lbm_flags_judge_select(const int8_t *pred_prev_dev, const int8_t *exact_now_dev,
+                                   const int8_t *pred_next_dev, int n, double min_agreement,
+                                   int8_t *used_dev, double *agreement_dev, int *fell_back_dev,
+                                   void *stream);
+LBM_API int lbm_gather_rows(const void *src_dev, long long nrows, size_t row_bytes,
+                            const int *idx_dev, int count, void *dst_dev, int *bad_dev,
+                            void *stream);
+
+/*
  * Intermediate buffers of the last lbm_net_forward / lbm_net_backward call, copied to host memory
  * (synchronises): for inspection and for checking each layer on its own.  `which`:
  *   LBM_NET_BUF_PARAMS_BF16  the BF16 parameters the kernels read (lbm_net_param_count values);

@@ -291,6 +291,71 @@ __global__ void k_to_maxima(const float *__restrict__ y, long long n, float offs
     out[k] = exp10((double)y[k] + (double)offset);
 }
 
+// Fraction of equal flags, counted by one CTA of 1024 threads (the flag arrays of a regrid hold a
+// few thousand blocks).
+constexpr int JUDGE_THREADS = 1024;
+
+__device__ __forceinline__ double cta_agreement(const int8_t *a, const int8_t *b, int n,
+                                                int *red) {
+    int c = 0;
+    for (int k = threadIdx.x; k < n; k += JUDGE_THREADS) c += a[k] == b[k];
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        c = red[threadIdx.x];
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+        if (threadIdx.x == 0) red[0] = c;
+    }
+    __syncthreads();
+    const double r = n > 0 ? (double)red[0] / (double)n : 1.0;
+    __syncthreads();  // red is reused by the caller
+    return r;
+}
+
+__global__ void __launch_bounds__(JUDGE_THREADS)
+    k_flags_agreement(const int8_t *a, const int8_t *b, int n, double *out) {
+    __shared__ int red[JUDGE_THREADS / 32];
+    const double r = cta_agreement(a, b, n, red);
+    if (threadIdx.x == 0) *out = r;
+}
+
+// The judge and fallback of a predicted regrid: the agreement of the previous regrid's predicted
+// flags with the exact flags now decides the flags used now -- the prediction for the next
+// interval if it reached min_agree (or if there is no previous prediction), else the exact flags.
+__global__ void __launch_bounds__(JUDGE_THREADS)
+    k_judge_select(const int8_t *pred_prev, const int8_t *exact_now, const int8_t *pred_next,
+                   int n, double min_agree, int8_t *used, double *agree_out, int *fell_out) {
+    __shared__ int red[JUDGE_THREADS / 32];
+    double r = __longlong_as_double(0x7ff8000000000000ll);  // no previous prediction: NaN
+    if (pred_prev) r = cta_agreement(pred_prev, exact_now, n, red);
+    const bool exact = pred_prev && !(r >= min_agree);
+    for (int k = threadIdx.x; k < n; k += JUDGE_THREADS) used[k] = exact ? exact_now[k] : pred_next[k];
+    if (threadIdx.x == 0) {
+        if (agree_out) *agree_out = r;
+        if (fell_out) *fell_out = exact ? 1 : 0;
+    }
+}
+
+// dst row k = src row idx[k] (rows of `words` 32-bit words)
+__global__ void k_gather_rows(const uint32_t *__restrict__ src, size_t words,
+                              const int *__restrict__ idx, int count, long long nrows,
+                              uint32_t *__restrict__ dst, int *bad) {
+    const size_t total = words * (size_t)count;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+         k += (size_t)gridDim.x * blockDim.x) {
+        const size_t row = k / words, w = k % words;
+        const int r = idx[row];
+        if (r < 0 || r >= nrows) {  // an index outside the source: flagged, nothing read
+            if (w == 0) atomicOr(bad, 1);
+            continue;
+        }
+        dst[k] = src[(size_t)r * words + w];
+    }
+}
+
 inline unsigned grid_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 #define NETCK(call, what)                                          \
@@ -661,6 +726,51 @@ LBM_API int lbm_net_log_targets(const double *kmax_dev, long long n, float offse
     k_log_targets<<<grid_for(n, NT), NT, 0, (cudaStream_t)stream>>>(kmax_dev, n, offset, floor_k,
                                                                      t_dev);
     NETCK(cudaGetLastError(), "lbm_net_log_targets");
+    return LBM_OK;
+}
+
+LBM_API int lbm_flags_agreement(const int8_t *a_dev, const int8_t *b_dev, int n, double *out_dev,
+                                void *stream) {
+    lbm::clear_error();
+    if (n < 0 || (n > 0 && (!a_dev || !b_dev)) || !out_dev)
+        return lbm::report_error(LBM_EINVAL, "lbm_flags_agreement: bad arguments");
+    k_flags_agreement<<<1, JUDGE_THREADS, 0, (cudaStream_t)stream>>>(a_dev, b_dev, n, out_dev);
+    NETCK(cudaGetLastError(), "lbm_flags_agreement");
+    return LBM_OK;
+}
+
+LBM_API int lbm_flags_judge_select(const int8_t *pred_prev_dev, const int8_t *exact_now_dev,
+                                   const int8_t *pred_next_dev, int n, double min_agreement,
+                                   int8_t *used_dev, double *agreement_dev, int *fell_back_dev,
+                                   void *stream) {
+    lbm::clear_error();
+    if (n < 0 || (n > 0 && (!exact_now_dev || !pred_next_dev || !used_dev)) ||
+        !(min_agreement >= 0.0 && min_agreement <= 1.0))
+        return lbm::report_error(LBM_EINVAL, "lbm_flags_judge_select: bad arguments");
+    k_judge_select<<<1, JUDGE_THREADS, 0, (cudaStream_t)stream>>>(
+        pred_prev_dev, exact_now_dev, pred_next_dev, n, min_agreement, used_dev, agreement_dev,
+        fell_back_dev);
+    NETCK(cudaGetLastError(), "lbm_flags_judge_select");
+    return LBM_OK;
+}
+
+LBM_API int lbm_gather_rows(const void *src_dev, long long nrows, size_t row_bytes,
+                            const int *idx_dev, int count, void *dst_dev, int *bad_dev,
+                            void *stream) {
+    lbm::clear_error();
+    if (nrows < 0 || count < 0 || row_bytes % 4 != 0 ||
+        (count > 0 && (!src_dev || !idx_dev || !dst_dev || !bad_dev)))
+        return lbm::report_error(LBM_EINVAL, "lbm_gather_rows: bad arguments (rows of a multiple "
+                                             "of 4 bytes)");
+    if (count == 0 || row_bytes == 0) return LBM_OK;
+    const size_t words = row_bytes / 4;
+    long long total = (long long)words * count;
+    unsigned g = grid_for(total, NT);
+    if (g > 4096) g = 4096;
+    k_gather_rows<<<g, NT, 0, (cudaStream_t)stream>>>(static_cast<const uint32_t *>(src_dev), words,
+                                                       idx_dev, count, nrows,
+                                                       static_cast<uint32_t *>(dst_dev), bad_dev);
+    NETCK(cudaGetLastError(), "lbm_gather_rows");
     return LBM_OK;
 }
 

@@ -116,6 +116,9 @@ _SIGS = {
     "lbm_net_log_targets": (_i, [_vp, _ll, ctypes.c_float, ctypes.c_float, _vp, _vp]),
     "lbm_net_to_maxima": (_i, [_vp, _ll, ctypes.c_float, _vp, _vp]),
     "lbm_net_get_buffer": (_i, [_vp, _i, _vp, _sz]),
+    "lbm_flags_agreement": (_i, [_vp, _vp, _i, _vp, _vp]),
+    "lbm_flags_judge_select": (_i, [_vp, _vp, _vp, _i, _d, _vp, _vp, _vp, _vp]),
+    "lbm_gather_rows": (_i, [_vp, _ll, _sz, _vp, _i, _vp, _vp, _vp]),
     "lbm_checkpoint_save": (_i, [_h, ctypes.c_char_p]),
     "lbm_checkpoint_load": (_i, [_h, ctypes.c_char_p]),
     "lbm_debug_fail_alloc": (_i, [_i]),
@@ -454,6 +457,34 @@ def lbm_net_get_params(n, host) -> int:
 
 def lbm_net_get_grads(n, host) -> int:
     return _ck(_lib.lbm_net_get_grads(n, _ptr(host)), "lbm_net_get_grads")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def lbm_flags_agreement(a_dev, b_dev, n: int, out_dev, stream=None) -> int:
+    return _ck(_lib.lbm_flags_agreement(_ptr(a_dev), _ptr(b_dev), int(n), _ptr(out_dev),
+                                        _stream_handle(stream)), "lbm_flags_agreement")
+
+
+def lbm_flags_judge_select(pred_prev_dev, exact_now_dev, pred_next_dev, n: int,
+                           min_agreement: float, used_dev, agreement_dev=None, fell_back_dev=None,
+                           stream=None) -> int:
+    return _ck(_lib.lbm_flags_judge_select(_ptr(pred_prev_dev), _ptr(exact_now_dev),
+                                           _ptr(pred_next_dev), int(n), float(min_agreement),
+                                           _ptr(used_dev), _ptr(agreement_dev),
+                                           _ptr(fell_back_dev), _stream_handle(stream)),
+               "lbm_flags_judge_select")
+
+
+def lbm_gather_rows(src_dev, nrows: int, row_bytes: int, idx_dev, count: int, dst_dev, bad_dev,
+                    stream=None) -> int:
+    return _ck(_lib.lbm_gather_rows(_ptr(src_dev), int(nrows), int(row_bytes), _ptr(idx_dev),
+                                    int(count), _ptr(dst_dev), _ptr(bad_dev),
+                                    _stream_handle(stream)), "lbm_gather_rows")
 
 
 def lbm_net_get_buffer(n, which: int, out) -> int:

@@ -70,22 +70,31 @@ def pairs(feats, kmax):
 
 
 def train(net, X, T, epochs: int, batch: int, lr: float, seed: int):
-    """Adam on shuffled minibatches; returns the per-epoch mean losses."""
+    """Adam on shuffled minibatches; returns the per-epoch mean losses.  The order of the samples
+    is drawn on the host from a seeded generator; each minibatch is gathered on the device by
+    lbm_gather_rows (torch only holds the buffers)."""
     import torch
 
-    g = torch.Generator(device="cpu")
-    g.manual_seed(seed)
+    g = np.random.default_rng(np.random.SeedSequence(seed))
     n = X.shape[0]
+    xb = torch.empty((batch,) + tuple(X.shape[1:]), dtype=X.dtype, device="cuda")
+    tb = torch.empty((batch,) + tuple(T.shape[1:]), dtype=T.dtype, device="cuda")
+    xrow, trow = X[0].numel() * X.element_size(), T[0].numel() * T.element_size()
+    bad = torch.zeros(1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
     losses = []
     for _ in range(epochs):
-        perm = torch.randperm(n, generator=g).cuda()
+        perm = torch.from_numpy(g.permutation(n).astype(np.int32)).cuda()
         tot, cnt = 0.0, 0
         for s in range(0, n - batch + 1, batch):
             idx = perm[s:s + batch]
-            xb, tb = X.index_select(0, idx).contiguous(), T.index_select(0, idx).contiguous()
+            L.lbm_gather_rows(X, n, xrow, idx, batch, xb, bad, stream)
+            L.lbm_gather_rows(T, n, trow, idx, batch, tb, bad, stream)
             tot += net.train_step(xb, tb, lr)
             cnt += 1
         losses.append(tot / max(cnt, 1))
+    if int(bad.item()):
+        raise RuntimeError("minibatch index outside the training set")
     return losses
 
 
@@ -108,29 +117,34 @@ def flags(maxima_row, T):
 
 
 def judge(net, feats, kmax, T, fallback_below: float):
-    """Run the regrid decisions over a trace: at every snapshot k the predicted flags for k + 1
-    (from the features at k) are compared with the exact flags at k + 1.  Returns a dict with the
-    mean agreement of the predicted flags, of the persistence baseline (exact flags at k used for
-    k + 1), of the flags actually used (predicted, or exact when the previous prediction's agreement
-    fell below `fallback_below`), and the fraction of regrids that fell back."""
+    """Run the regrid decisions over a trace of S + 1 snapshots.  At regrid k the exact flags E_k
+    of the sensor now and the flags P_k predicted from the features now for snapshot k + 1 are
+    formed; lbm_flags_judge_select compares the previous prediction P_{k-1} with E_k and uses P_k
+    for the coming interval if they agreed on at least `fallback_below` of the blocks, else E_k.
+    Each choice is judged against the exact flags E_{k+1}, as are P_k alone and the persistence
+    baseline E_k.  Everything runs on the device; the S agreements of each kind come back once.
+    Returns the means, the fraction of regrids that fell back, and the per-regrid agreements
+    ("per_regrid": predicted, persistence, used)."""
+    import torch
+
+    S = kmax.shape[0] - 1
+    nb = kmax.shape[1]
     pred = predicted_maxima(net, feats[:-1].contiguous())
-    agree_pred, agree_pers, agree_used, fell = [], [], [], 0
-    last = 1.0
-    for k in range(kmax.shape[0] - 1):
-        # the flags are compared on the host (a few thousand bytes per regrid)
-        exact_next = flags(kmax[k + 1], T).cpu().numpy()
-        fp = flags(pred[k].contiguous(), T).cpu().numpy()
-        fe = flags(kmax[k], T).cpu().numpy()
-        a_pred = float(np.mean(fp == exact_next))
-        a_pers = float(np.mean(fe == exact_next))
-        use_exact = last < fallback_below
-        fell += int(use_exact)
-        agree_used.append(a_pers if use_exact else a_pred)
-        agree_pred.append(a_pred)
-        agree_pers.append(a_pers)
-        last = a_pred
-    m = len(agree_pred)
-    return {"agreement_predicted": float(np.mean(agree_pred)),
-            "agreement_persistence": float(np.mean(agree_pers)),
-            "agreement_used": float(np.mean(agree_used)),
-            "fallback_fraction": fell / max(m, 1), "regrids": m}
+    E = [flags(kmax[k].contiguous(), T) for k in range(S + 1)]
+    P = [flags(pred[k].contiguous(), T) for k in range(S)]
+    used = torch.empty(nb, dtype=torch.int8, device="cuda")
+    res = torch.empty((3, S), dtype=torch.float64, device="cuda")
+    fell = torch.zeros(S, dtype=torch.int32, device="cuda")
+    for k in range(S):
+        L.lbm_flags_judge_select(P[k - 1] if k else None, E[k], P[k], nb, fallback_below, used,
+                                 None, fell[k:k + 1])
+        L.lbm_flags_agreement(P[k], E[k + 1], nb, res[0, k:k + 1])
+        L.lbm_flags_agreement(E[k], E[k + 1], nb, res[1, k:k + 1])
+        L.lbm_flags_agreement(used, E[k + 1], nb, res[2, k:k + 1])
+    r = res.cpu().numpy()
+    f = fell.cpu().numpy()
+    return {"agreement_predicted": float(r[0].mean()),
+            "agreement_persistence": float(r[1].mean()),
+            "agreement_used": float(r[2].mean()),
+            "fallback_fraction": float(f.mean()), "regrids": S,
+            "per_regrid": r}

@@ -57,3 +57,47 @@ def test_predictor_learns_from_solver_traces(L):
         assert 0.0 <= j[k] <= 1.0
     print(j, losses[0], losses[-1], mse, np.var(te))
     net.close()
+
+
+def test_judge_select_agreement_and_gather_kernels(L):
+    """The regrid judge, the flag agreement and the minibatch gather on the device against their
+    plain definitions: agreement = fraction of equal flags; the flags used are the new prediction
+    when the previous prediction agreed with the exact flags on at least the set fraction (or
+    there is no previous prediction), else the exact flags; gathered row k = source row idx[k],
+    with an index outside the source flagged and not read."""
+    import torch
+
+    rng = np.random.default_rng(12)
+    n = 4096
+    a = torch.from_numpy(rng.integers(-1, 2, n).astype(np.int8)).cuda()
+    b = a.clone()
+    flip = rng.choice(n, 300, replace=False)
+    b[torch.from_numpy(flip).cuda()] = torch.from_numpy(
+        ((a.cpu().numpy()[flip] + 2) % 3 - 1).astype(np.int8)).cuda()
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    L.lbm_flags_agreement(a, b, n, out)
+    assert out.item() == pytest.approx((n - 300) / n, abs=0)
+    L.lbm_flags_agreement(a, b, 0, out)
+    assert out.item() == 1.0
+    nxt = torch.from_numpy(rng.integers(-1, 2, n).astype(np.int8)).cuda()
+    used = torch.empty(n, dtype=torch.int8, device="cuda")
+    agree = torch.zeros(1, dtype=torch.float64, device="cuda")
+    fell = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for thr, expect_exact in ((0.9, False), (0.95, True)):  # agreement 0.9268
+        L.lbm_flags_judge_select(a, b, nxt, n, thr, used, agree, fell)
+        assert agree.item() == pytest.approx((n - 300) / n, abs=0)
+        assert fell.item() == int(expect_exact)
+        assert torch.equal(used, b if expect_exact else nxt)
+    L.lbm_flags_judge_select(None, b, nxt, n, 0.99, used, agree, fell)  # first regrid
+    assert np.isnan(agree.item()) and fell.item() == 0 and torch.equal(used, nxt)
+    with pytest.raises(L.LbmError):
+        L.lbm_flags_judge_select(a, b, nxt, n, 1.5, used)
+    src = torch.from_numpy(rng.normal(size=(37, 3, 5, 7)).astype(np.float32)).cuda()
+    idx = torch.from_numpy(np.array([5, 0, 36, 5, 12], np.int32)).cuda()
+    dst = torch.full((5, 3, 5, 7), -1.0, device="cuda")
+    bad = torch.zeros(1, dtype=torch.int32, device="cuda")
+    L.lbm_gather_rows(src, 37, 3 * 5 * 7 * 4, idx, 5, dst, bad)
+    assert torch.equal(dst, src[idx.long()]) and bad.item() == 0
+    idx[2] = 37
+    L.lbm_gather_rows(src, 37, 3 * 5 * 7 * 4, idx, 5, dst, bad)
+    assert bad.item() == 1
