@@ -273,6 +273,46 @@ LBM_API int lbm_get_sensor_field(lbm_t *h, double *out_host);
 LBM_API int lbm_conservation(lbm_t *h, double *mass, double *mom3);
 
 /*
+ * Slabs of a lattice cut along its slowest axis (z for D3Q19, y for D2Q9), one handle per slab,
+ * e.g. one per GPU.  The fused step of Sec. 2.2 pulls each population from the nearest neighbour
+ * along its velocity, so a slab needs, per step, one plane of its neighbour's previous
+ * post-collision state, and only the populations whose velocity crosses the cut: 5 per face for
+ * D3Q19, 3 for D2Q9 (no counterpart in the paper, whose runs are on one machine).
+ *
+ * lbm_set_halo(h, faces): faces = LBM_HALO_LO and / or LBM_HALO_HI (0 restores walls on both)
+ * makes the low / high face of the slab axis a cut instead of a wall.  A cell on a halo face then
+ * pulls the crossing populations from the face's halo plane wherever the rest of the pull source
+ * lies inside the lattice (or wraps on a periodic x / y axis); sources outside along another axis
+ * are wall ghosts as before.  On a D2Q9 slab the high y face, where the lid is, carries no lid
+ * term once it is a halo.  The slab axis must not be periodic (LBM_EINVAL either way round).  The
+ * halos live on the device, start as fluid at rest, keep their content until the next import and
+ * are read by every following step; lbm_reset leaves them as they are.  Set the storage type
+ * first: it cannot change once halos exist.  A slab with halo faces runs the one-cell kernel
+ * (LBM_KERNEL_AUTO or LBM_KERNEL_CELL; the other variants are refused either way round).
+ *
+ * lbm_halo_size: elements (and bytes) of one halo message: k planes of nx (D2Q9) or nx * ny
+ * (D3Q19) values in the storage type, k = 3 (D2Q9) or 5 (D3Q19); plane j holds the j-th crossing
+ * direction in the library's population order, cells x fastest.
+ *
+ * lbm_halo_export(h, face, out, on_device): writes the populations leaving through the face --
+ * velocity component -1 along the slab axis on the low face, +1 on the high face -- of the
+ * boundary plane of the current (post-collision) state.  lbm_halo_import(h, face, in, on_device):
+ * sets the face's halo to the populations arriving through it -- +1 on the low face, -1 on the high
+ * face -- so the neighbour below exports its high face into this slab's low face and the one above
+ * its low face into the high face.  on_device = 0: `out` / `in` are host memory and the call
+ * synchronises; 1: device memory, used asynchronously on the handle's stream.  Per step: export
+ * both faces, exchange, import, lbm_step(h, 1).  Bytes are copied as stored, so a slab run is bit
+ * for bit the single-domain run wherever the same kernel relaxes each cell.  LBM_ESTATE for a face
+ * without a halo.
+ */
+#define LBM_HALO_LO 1
+#define LBM_HALO_HI 2
+LBM_API int lbm_set_halo(lbm_t *h, int faces);
+LBM_API int lbm_halo_size(const lbm_t *h, long long *elems, long long *bytes);
+LBM_API int lbm_halo_export(lbm_t *h, int face, void *out, int on_device);
+LBM_API int lbm_halo_import(lbm_t *h, int face, const void *in, int on_device);
+
+/*
  * Checkpoint files (no counterpart in the paper; resuming a long run).  lbm_checkpoint_save writes
  * an 88-byte header -- magic "LBMCKPT\0", version 1, lattice, nx, ny, nz, storage type, periodic
  * mask, tau, lid (x, z), step counter, payload size and the 64-bit FNV-1a checksum of the payload,

@@ -20,7 +20,7 @@ LIB = os.path.join(BUILD, "liblbm.so")
 SOURCES = ["lbm_api.cu", "lbm_aux.cu", "lbm_step_d2q9.cu", "lbm_step_d3q19.cu", "lbm_noalloc.cu",
            "lbm_multilevel.cu", "lbm_regrid.cu", "lbm_net.cu"]
 HEADERS = ["lbm_traits.cuh", "lbm_step.cuh", "lbm_step_pair.cuh", "lbm_step_tma.cuh",
-           "lbm_internal.h"]
+           "lbm_step_tma_pair.cuh", "lbm_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr",
          "-Xcompiler", "-fPIC,-fvisibility=hidden", "-I", os.path.join(ROOT, "include")]

@@ -105,6 +105,12 @@ struct lbm_s {
     double *tile_sum = nullptr;
     double *tile_avg = nullptr;
 
+    // halo planes of a slab cut along the slowest axis (lbm_set_halo): q x plane values each, and
+    // a compact message buffer for host transfers
+    void *halo[2] = {nullptr, nullptr};
+    void *halo_msg = nullptr;
+    int halo_faces = 0;
+
     // profiling
     int profiling = 0;
     unsigned long long wait_ns = 0;  // lbm_debug_set_wait_limit (0: the kernels' default)
@@ -127,6 +133,10 @@ struct lbm_s {
     int rtype() const { return dtype == LBM_F64 ? LBM_F64 : LBM_F32; }
     size_t rsize() const { return dtype == LBM_F64 ? 8 : 4; }
     size_t pop_bytes() const { return (size_t)q * N * elem_size(dtype); }
+    // the slab axis is the slowest one: z for D3Q19, y for D2Q9
+    int slab_axis_bit() const { return dim == 3 ? 4 : 2; }
+    size_t halo_plane() const { return dim == 3 ? (size_t)nx * ny : (size_t)nx; }
+    int slab_extent() const { return dim == 3 ? nz : ny; }
 };
 
 namespace {
@@ -159,6 +169,8 @@ StepParams params_of(const lbm_t *h) {
     p.tile_zero = nullptr;
     p.wait_ns = h->wait_ns;
     p.hold_copies = h->hold_copies;
+    p.halo_lo = (h->halo_faces & LBM_HALO_LO) ? h->halo[0] : nullptr;
+    p.halo_hi = (h->halo_faces & LBM_HALO_HI) ? h->halo[1] : nullptr;
     return p;
 }
 
@@ -487,6 +499,9 @@ LBM_API int lbm_destroy(lbm_t *h) {
     cudaFree(h->staging);
     cudaFree(h->tile_sum);
     cudaFree(h->tile_avg);
+    cudaFree(h->halo[0]);
+    cudaFree(h->halo[1]);
+    cudaFree(h->halo_msg);
     if (h->err_host) cudaFreeHost(h->err_host);
     lbm::ml::destroy(h->mesh);
     delete h;
@@ -496,7 +511,7 @@ LBM_API int lbm_destroy(lbm_t *h) {
 LBM_API int lbm_set_dtype(lbm_t *h, int dtype) {
     CHECK_H(h);
     if (elem_size(dtype) == 0) return fail(LBM_EINVAL, "unknown storage type %d", dtype);
-    if (h->buf[0] || h->scratch_ready)
+    if (h->buf[0] || h->scratch_ready || h->halo[0] || h->halo[1])
         return fail(LBM_ESTATE, "storage type must be set before the buffers exist");
     h->dtype = dtype;
     return LBM_OK;
@@ -515,6 +530,8 @@ LBM_API int lbm_set_lid(lbm_t *h, double ux, double uz) {
 LBM_API int lbm_set_periodic(lbm_t *h, int axis_mask) {
     CHECK_H(h);
     if (axis_mask & ~7) return fail(LBM_EINVAL, "periodic mask %d has unknown bits", axis_mask);
+    if (h->halo_faces && (axis_mask & h->slab_axis_bit()))
+        return fail(LBM_EINVAL, "the slab axis has halo faces: it cannot also be periodic");
     h->periodic = (h->dim == 2) ? (axis_mask & 3) : axis_mask;
     drop_graphs(h);
     return LBM_OK;
@@ -585,6 +602,8 @@ LBM_API int lbm_set_kernel_variant(lbm_t *h, int variant) {
         return fail(LBM_EINVAL,
                     "the TMA kernel needs D3Q19, 16- or 32-bit storage and rows of a multiple of "
                     "16 bytes");
+    if (h->halo_faces && variant != LBM_KERNEL_AUTO && variant != LBM_KERNEL_CELL)
+        return fail(LBM_EINVAL, "a slab with halo faces runs the one-cell kernel only");
     h->variant = variant;
     drop_graphs(h);
     return LBM_OK;
@@ -847,6 +866,120 @@ LBM_API int lbm_set_raw(lbm_t *h, const void *in_host, size_t bytes) {
     if (st != LBM_OK) return st;
     CK(cudaMemcpyAsync(h->buf[h->cur], in_host, bytes, cudaMemcpyHostToDevice, h->stream),
        "cudaMemcpyAsync");
+    return sync(h);
+}
+
+// ------------------------------------------------------------------------------ slab halos
+namespace {
+
+// directions whose velocity component along the slab axis is `sign`, in index order
+lbm::HaloDirs slab_dirs(const lbm_t *h, int sign) {
+    lbm::HaloDirs d{};
+    d.k = 0;
+    for (int i = 0; i < h->q; ++i) {
+        const int c = (h->q == LBM_D3Q19) ? lbm::D3Q19::cz(i) : lbm::D2Q9::cy(i);
+        if (c == sign) d.dir[d.k++] = i;
+    }
+    return d;
+}
+
+int check_face(const lbm_t *h, int face) {
+    if (face != LBM_HALO_LO && face != LBM_HALO_HI)
+        return fail(LBM_EINVAL, "face must be LBM_HALO_LO or LBM_HALO_HI (got %d)", face);
+    if (!(h->halo_faces & face)) return fail(LBM_ESTATE, "face %d has no halo (lbm_set_halo)", face);
+    return LBM_OK;
+}
+
+int ensure_halo_msg(lbm_t *h) {
+    if (h->halo_msg) return LBM_OK;
+    const size_t bytes = (size_t)slab_dirs(h, 1).k * h->halo_plane() * elem_size(h->dtype);
+    CK(lbm::dev_alloc(&h->halo_msg, bytes), "cudaMalloc(halo message)");
+    return LBM_OK;
+}
+
+}  // namespace
+
+LBM_API int lbm_set_halo(lbm_t *h, int faces) {
+    CHECK_H(h);
+    if (faces & ~(LBM_HALO_LO | LBM_HALO_HI))
+        return fail(LBM_EINVAL, "halo faces %d have unknown bits", faces);
+    if (faces && (h->periodic & h->slab_axis_bit()))
+        return fail(LBM_EINVAL, "the slab axis is periodic: it cannot have halo faces");
+    if (faces && h->variant != lbm::KERNEL_AUTO && h->variant != lbm::KERNEL_CELL)
+        return fail(LBM_EINVAL, "halo faces need the one-cell kernel (LBM_KERNEL_AUTO or _CELL)");
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    const size_t plane = h->halo_plane();
+    const size_t bytes = (size_t)h->q * plane * elem_size(h->dtype);
+    for (int f = 0; f < 2; ++f) {
+        if (!((faces >> f) & 1) || h->halo[f]) continue;
+        CK(lbm::dev_alloc(&h->halo[f], bytes), "cudaMalloc(halo)");
+        // until the first import the halo holds fluid at rest
+        CK(lbm::init_rest(h->q, h->dtype, h->halo[f], plane, h->stream), "init_rest(halo)");
+    }
+    h->halo_faces = faces;
+    drop_graphs(h);
+    return LBM_OK;
+}
+
+LBM_API int lbm_halo_size(const lbm_t *h, long long *elems, long long *bytes) {
+    CHECK_H(h);
+    const long long n = (long long)slab_dirs(h, 1).k * (long long)h->halo_plane();
+    if (elems) *elems = n;
+    if (bytes) *bytes = n * (long long)elem_size(h->dtype);
+    return LBM_OK;
+}
+
+LBM_API int lbm_halo_export(lbm_t *h, int face, void *out, int on_device) {
+    CHECK_H(h);
+    int st = check_face(h, face);
+    if (st != LBM_OK) return st;
+    if (!out) return fail(LBM_EINVAL, "NULL output");
+    CHECK_PENDING("lbm_halo_export");
+    st = ensure_buffers(h);
+    if (st == LBM_OK && !on_device) st = ensure_halo_msg(h);
+    if (st != LBM_OK) return st;
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    // the populations leaving the slab through the face: velocity component -1 along the slab
+    // axis on the low face, +1 on the high face, from the boundary plane of the current state
+    const lbm::HaloDirs d = slab_dirs(h, face == LBM_HALO_LO ? -1 : 1);
+    const size_t plane = h->halo_plane();
+    const size_t off = (face == LBM_HALO_LO) ? 0 : (size_t)(h->slab_extent() - 1) * plane;
+    const int elem = (int)elem_size(h->dtype);
+    void *dst = on_device ? out : h->halo_msg;
+    CK(lbm::halo_pack(elem, h->buf[h->cur], h->N, off, plane, d, dst, h->stream), "halo_pack");
+    if (on_device) return LBM_OK;
+    CK(cudaMemcpyAsync(out, h->halo_msg, (size_t)d.k * plane * elem, cudaMemcpyDeviceToHost,
+                       h->stream),
+       "cudaMemcpyAsync");
+    return sync(h);
+}
+
+LBM_API int lbm_halo_import(lbm_t *h, int face, const void *in, int on_device) {
+    CHECK_H(h);
+    int st = check_face(h, face);
+    if (st != LBM_OK) return st;
+    if (!in) return fail(LBM_EINVAL, "NULL input");
+    CHECK_PENDING("lbm_halo_import");
+    if (!on_device) {
+        st = ensure_halo_msg(h);
+        if (st != LBM_OK) return st;
+    }
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    // the populations arriving through the face: velocity component +1 along the slab axis on
+    // the low face, -1 on the high face
+    const lbm::HaloDirs d = slab_dirs(h, face == LBM_HALO_LO ? 1 : -1);
+    const size_t plane = h->halo_plane();
+    const int elem = (int)elem_size(h->dtype);
+    const void *src = in;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(h->halo_msg, in, (size_t)d.k * plane * elem, cudaMemcpyHostToDevice,
+                           h->stream),
+           "cudaMemcpyAsync");
+        src = h->halo_msg;
+    }
+    CK(lbm::halo_unpack(elem, src, plane, d, h->halo[face == LBM_HALO_LO ? 0 : 1], h->stream),
+       "halo_unpack");
+    if (on_device) return LBM_OK;
     return sync(h);
 }
 

@@ -599,6 +599,73 @@ cudaError_t init_rest(int q, int dtype, void *f, size_t N, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+namespace {
+
+// Halo messages: plain copies of whole population planes, by element size (the storage types
+// are copied bit for bit).
+template <class E>
+__global__ void k_halo_pack(const E *__restrict__ f, size_t N, size_t plane_off, size_t plane,
+                            HaloDirs d, E *__restrict__ msg) {
+    const int j = blockIdx.y;
+    const E *src = f + (size_t)d.dir[j] * N + plane_off;
+    E *dst = msg + (size_t)j * plane;
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < plane;
+         c += (size_t)gridDim.x * blockDim.x)
+        dst[c] = src[c];
+}
+
+template <class E>
+__global__ void k_halo_unpack(const E *__restrict__ msg, size_t plane, HaloDirs d,
+                              E *__restrict__ halo) {
+    const int j = blockIdx.y;
+    const E *src = msg + (size_t)j * plane;
+    E *dst = halo + (size_t)d.dir[j] * plane;
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < plane;
+         c += (size_t)gridDim.x * blockDim.x)
+        dst[c] = src[c];
+}
+
+template <class E>
+cudaError_t halo_pack_t(const void *f, size_t N, size_t plane_off, size_t plane, const HaloDirs &d,
+                        void *msg, cudaStream_t s) {
+    k_halo_pack<E><<<ew_grid(plane, d.k), EW_THREADS, 0, s>>>(static_cast<const E *>(f), N,
+                                                               plane_off, plane, d,
+                                                               static_cast<E *>(msg));
+    return cudaGetLastError();
+}
+
+template <class E>
+cudaError_t halo_unpack_t(const void *msg, size_t plane, const HaloDirs &d, void *halo,
+                          cudaStream_t s) {
+    k_halo_unpack<E><<<ew_grid(plane, d.k), EW_THREADS, 0, s>>>(static_cast<const E *>(msg), plane,
+                                                                 d, static_cast<E *>(halo));
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t halo_pack(int elem, const void *f, size_t N, size_t plane_off, size_t plane,
+                      const HaloDirs &d, void *msg, cudaStream_t s) {
+    if (d.k < 1 || d.k > HALO_MAX_DIRS || plane == 0) return cudaErrorInvalidValue;
+    switch (elem) {
+        case 2: return halo_pack_t<unsigned short>(f, N, plane_off, plane, d, msg, s);
+        case 4: return halo_pack_t<unsigned>(f, N, plane_off, plane, d, msg, s);
+        case 8: return halo_pack_t<unsigned long long>(f, N, plane_off, plane, d, msg, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t halo_unpack(int elem, const void *msg, size_t plane, const HaloDirs &d, void *halo,
+                        cudaStream_t s) {
+    if (d.k < 1 || d.k > HALO_MAX_DIRS || plane == 0) return cudaErrorInvalidValue;
+    switch (elem) {
+        case 2: return halo_unpack_t<unsigned short>(msg, plane, d, halo, s);
+        case 4: return halo_unpack_t<unsigned>(msg, plane, d, halo, s);
+        case 8: return halo_unpack_t<unsigned long long>(msg, plane, d, halo, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t f64_to_storage(int q, int dtype, int i0, int nq, const double *in, void *out, size_t N,
                            cudaStream_t s) {
     LBM_DISPATCH(q, dtype, (k_from_f64<L, DT><<<ew_grid(N, nq), EW_THREADS, 0, s>>>(

@@ -32,6 +32,19 @@ cudaError_t step_d3q19(int dtype, const void *fin, void *fout, const StepParams 
 
 // Population helpers (lbm_aux.cu).
 cudaError_t init_rest(int q, int dtype, void *f, size_t N, cudaStream_t s);
+// Halo planes of a slab (StepParams::halo_lo / halo_hi).  A halo message holds k population
+// planes of `plane` values in the storage type (elem bytes each), for the directions dirs[0..k).
+// halo_pack: message[j] = population dirs[j] of the lattice plane starting at cell plane_off
+// (N cells per population); halo_unpack: halo plane dirs[j] (of a q x plane halo) = message[j].
+constexpr int HALO_MAX_DIRS = 8;
+struct HaloDirs {
+    int k;
+    int dir[HALO_MAX_DIRS];
+};
+cudaError_t halo_pack(int elem, const void *f, size_t N, size_t plane_off, size_t plane,
+                      const HaloDirs &d, void *msg, cudaStream_t s);
+cudaError_t halo_unpack(int elem, const void *msg, size_t plane, const HaloDirs &d, void *halo,
+                        cudaStream_t s);
 // Conversions of populations [i0, i0 + nq); in / out point at population i0 (N values each).
 cudaError_t f64_to_storage(int q, int dtype, int i0, int nq, const double *in, void *out, size_t N,
                            cudaStream_t s);

@@ -107,8 +107,13 @@ __device__ __forceinline__ void store_pop(T *p, T v) {
 
 // Pull-gather of cell (x, y, z) in the general case (walls with moving-lid bounce-back, periodic
 // wrap): writes the deviations from rest df_i = f_i - w_i of the populations arriving at the cell
-// to df[i * STRIDE] (STRIDE 2 fills one lane of an array of pairs).
-template <class L, int DT, int STRIDE = 1>
+// to df[i * STRIDE] (STRIDE 2 fills one lane of an array of pairs).  HALO: the faces of the slowest
+// axis (z in 3-D, y in 2-D) may be cuts of a slab (StepParams::halo_lo / halo_hi); a source beyond
+// such a face and inside the lattice along the other axes (or wrapped) is the neighbouring slab's
+// cell, whose population i sits in the halo plane.  A source outside along another axis stays a
+// wall ghost, and a 2-D slab whose high y face is a cut has no lid there.  The kernels without
+// halos are instantiated with HALO = false and do not carry this code.
+template <class L, int DT, int STRIDE = 1, bool HALO = false>
 __device__ __forceinline__ void gather_cell(const typename Storage<DT>::T *__restrict__ fin,
                                             const StepParams &p, size_t N, int x, int y, int z,
                                             typename Storage<DT>::R *df) {
@@ -144,11 +149,28 @@ __device__ __forceinline__ void gather_cell(const typename Storage<DT>::T *__res
         const bool valid = (cx == 1 ? vxm : (cx == -1 ? vxp : true)) &&
                            (cy == 1 ? vym : (cy == -1 ? vyp : true)) &&
                            (cz == 1 ? vzm : (cz == -1 ? vzp : true));
-        const size_t src = valid ? (size_t)i * N + (size_t)((sz * ny + sy) * nx + sx)
-                                 : (size_t)L::opp(i) * N + (size_t)idx;
-        R v = S::to_r(load_pop(fin + src));
+        size_t src = valid ? (size_t)i * N + (size_t)((sz * ny + sy) * nx + sx)
+                           : (size_t)L::opp(i) * N + (size_t)idx;
+        const typename S::T *from = fin;
+        bool lid = cy == -1 && !vyp;
+        if constexpr (HALO) {
+            const bool okx = cx == 1 ? vxm : (cx == -1 ? vxp : true);
+            const bool oky = cy == 1 ? vym : (cy == -1 ? vyp : true);
+            const bool okz = cz == 1 ? vzm : (cz == -1 ? vzp : true);
+            const int cs = (L::D == 3) ? cz : cy;  // component along the slab axis
+            const bool beyond = (L::D == 3) ? (cz != 0 && !okz && okx && oky)
+                                            : (cy != 0 && !oky && okx);
+            const void *hv = cs == 1 ? p.halo_lo : (cs == -1 ? p.halo_hi : nullptr);
+            if (beyond && hv != nullptr) {
+                from = static_cast<const typename S::T *>(hv);
+                src = (L::D == 3) ? (size_t)i * ((size_t)nx * ny) + (size_t)(sy * nx + sx)
+                                  : (size_t)i * nx + (size_t)sx;
+            }
+            if (L::D == 2 && p.halo_hi != nullptr) lid = false;
+        }
+        R v = S::to_r(load_pop(from + src));
         if (!S::SHIFTED) v -= weight<L, R>(i);  // w_opp(i) == w_i
-        if (cy == -1 && !vyp) {
+        if (lid) {
             // moving lid: + 2 w_i (c_i . u_lid) / c_s^2, wall density 1
             v += R(6) * weight<L, R>(i) * (R(cx) * lidx + R(cz) * lidz);
         }
@@ -271,8 +293,9 @@ __device__ __forceinline__ typename Storage<DT>::R relax_store_cell(
     });
 }
 
-// MODE 0: no sensor.  MODE 1: sensor and per-tile max.  MODE 2: MODE 1 plus per-cell K.
-template <class L, int DT, int MODE>
+// MODE 0: no sensor.  MODE 1: sensor and per-tile max.  MODE 2: MODE 1 plus per-cell K.  HALO:
+// the faces of the slowest axis may be cuts of a slab (gather_cell).
+template <class L, int DT, int MODE, bool HALO = false>
 __global__ void __launch_bounds__(CTA_X *CTA_Y, LBM_STEP_MIN_BLOCKS)
     fused_step_kernel(const typename Storage<DT>::T *__restrict__ fin,
                       typename Storage<DT>::T *__restrict__ fout, const StepParams p,
@@ -322,7 +345,7 @@ __global__ void __launch_bounds__(CTA_X *CTA_Y, LBM_STEP_MIN_BLOCKS)
             else if (LBM_XSEL_PATH && inner_yz)
                 gather_xsel<L, DT>(fin, N, nx, nx * ny, (size_t)idx, x, p.periodic & 1, df);
             else
-                gather_cell<L, DT>(fin, p, N, x, y, z, df);
+                gather_cell<L, DT, 1, HALO>(fin, p, N, x, y, z, df);
             const R K = relax_store_cell<L, DT, MODE>(df, omega, fout, N, idx);
             if (MODE != 0) {
                 const B kb = max_bits(K);
@@ -355,7 +378,7 @@ __global__ void __launch_bounds__(CTA_X *CTA_Y, LBM_STEP_MIN_BLOCKS)
     }
 }
 
-template <class L, int DT>
+template <class L, int DT, bool HALO = false>
 cudaError_t launch_fused_step(const void *fin, void *fout, const StepParams &p, int mode,
                               void *tile_max, void *k_field, cudaStream_t stream) {
     using T = typename Storage<DT>::T;
@@ -368,12 +391,16 @@ cudaError_t launch_fused_step(const void *fin, void *fout, const StepParams &p, 
     R *tm = static_cast<R *>(tile_max);
     R *kf = static_cast<R *>(k_field);
     if (mode == 0)
-        fused_step_kernel<L, DT, 0><<<grid, block, 0, stream>>>(a, b, p, tm, kf);
+        fused_step_kernel<L, DT, 0, HALO><<<grid, block, 0, stream>>>(a, b, p, tm, kf);
     else if (mode == 1)
-        fused_step_kernel<L, DT, 1><<<grid, block, 0, stream>>>(a, b, p, tm, kf);
+        fused_step_kernel<L, DT, 1, HALO><<<grid, block, 0, stream>>>(a, b, p, tm, kf);
     else
-        fused_step_kernel<L, DT, 2><<<grid, block, 0, stream>>>(a, b, p, tm, kf);
+        fused_step_kernel<L, DT, 2, HALO><<<grid, block, 0, stream>>>(a, b, p, tm, kf);
     return cudaGetLastError();
 }
+
+// A slab with halo faces (StepParams::halo_lo / halo_hi) runs the one-cell kernel with the halo
+// gather; the other kernels do not take halos.
+inline bool has_halo(const StepParams &p) { return p.halo_lo != nullptr || p.halo_hi != nullptr; }
 
 }  // namespace lbm

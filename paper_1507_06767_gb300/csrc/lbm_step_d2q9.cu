@@ -17,6 +17,16 @@ cudaError_t step_d2q9(int dtype, const void *fin, void *fout, const StepParams &
     const bool pair = pair_ok && (variant == KERNEL_PAIR ||
                                   (variant == KERNEL_AUTO && (dtype >= 2 || big)));
     if ((variant == KERNEL_PAIR && !pair_ok) || variant == KERNEL_TMA) return cudaErrorInvalidValue;
+    if (has_halo(p)) {
+        if (variant != KERNEL_AUTO && variant != KERNEL_CELL) return cudaErrorInvalidValue;
+        switch (dtype) {
+            case 0: return launch_fused_step<D2Q9, 0, true>(fin, fout, p, mode, tile_max, k_field, s);
+            case 1: return launch_fused_step<D2Q9, 1, true>(fin, fout, p, mode, tile_max, k_field, s);
+            case 2: return launch_fused_step<D2Q9, 2, true>(fin, fout, p, mode, tile_max, k_field, s);
+            case 3: return launch_fused_step<D2Q9, 3, true>(fin, fout, p, mode, tile_max, k_field, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (dtype) {
         case 0: return launch_fused_step<D2Q9, 0>(fin, fout, p, mode, tile_max, k_field, s);
         case 1:

@@ -183,6 +183,16 @@ cudaError_t step_d3q19(int dtype, const void *fin, void *fout, const StepParams 
     if ((variant == KERNEL_PAIR && !pair_ok) || (variant == KERNEL_TMA && !tma) ||
         (variant == KERNEL_TMA_PAIR && !tma_pair))
         return cudaErrorInvalidValue;
+    if (has_halo(p)) {  // a slab with cut faces: the one-cell kernel with the halo gather
+        if (variant != KERNEL_AUTO && variant != KERNEL_CELL) return cudaErrorInvalidValue;
+        switch (dtype) {
+            case 0: return launch_fused_step<D3Q19, 0, true>(fin, fout, p, mode, tile_max, k_field, s);
+            case 1: return launch_fused_step<D3Q19, 1, true>(fin, fout, p, mode, tile_max, k_field, s);
+            case 2: return launch_fused_step<D3Q19, 2, true>(fin, fout, p, mode, tile_max, k_field, s);
+            case 3: return launch_fused_step<D3Q19, 3, true>(fin, fout, p, mode, tile_max, k_field, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     if (tma_pair) {
         if (dtype == 2) return launch_fused_step_tma_pair<2>(fin, fout, p, mode, tile_max, k_field, s);
         return launch_fused_step_tma_pair<3>(fin, fout, p, mode, tile_max, k_field, s);

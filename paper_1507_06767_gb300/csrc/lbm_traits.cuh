@@ -137,6 +137,14 @@ struct StepParams {
     // test hook: the producer warps of the TMA-staged kernels issue no copies, so the consumers'
     // first wait can only run out (no copy is in flight when they give up)
     int hold_copies = 0;
+    // halo planes of a slab cut along the slowest axis (z for D3Q19, y for D2Q9), or null for a
+    // wall: the neighbouring slab's boundary plane of the previous post-collision state, as q
+    // population planes of nx (D2Q9) or nx * ny (D3Q19) values in the storage type.  A cell on the
+    // low face pulls the populations with a velocity component +1 along that axis from halo_lo,
+    // one on the high face those with -1 from halo_hi, wherever the other coordinates of the pull
+    // source lie inside the lattice (else the source is a wall ghost, as without a halo).
+    const void *halo_lo = nullptr;
+    const void *halo_hi = nullptr;
 };
 
 // The relaxation rate and lid velocity in the kernel's arithmetic type.

@@ -124,6 +124,10 @@ _SIGS = {
     "lbm_debug_fail_alloc": (_i, [_i]),
     "lbm_debug_set_wait_limit": (_i, [_h, _ll]),
     "lbm_debug_hold_copies": (_i, [_h, _i]),
+    "lbm_set_halo": (_i, [_h, _i]),
+    "lbm_halo_size": (_i, [_h, ctypes.POINTER(_ll), ctypes.POINTER(_ll)]),
+    "lbm_halo_export": (_i, [_h, _i, _vp, _i]),
+    "lbm_halo_import": (_i, [_h, _i, _vp, _i]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -211,6 +215,31 @@ lbm_step = _wrap("lbm_step")
 lbm_debug_fail_alloc = _wrap("lbm_debug_fail_alloc")
 lbm_debug_set_wait_limit = _wrap("lbm_debug_set_wait_limit")
 lbm_debug_hold_copies = _wrap("lbm_debug_hold_copies")
+
+
+lbm_set_halo = _wrap("lbm_set_halo")
+
+
+def lbm_halo_size(h):
+    """(elements, bytes) of one halo message."""
+    n, b = ctypes.c_longlong(), ctypes.c_longlong()
+    _ck(_lib.lbm_halo_size(h, ctypes.byref(n), ctypes.byref(b)), "lbm_halo_size")
+    return n.value, b.value
+
+
+def _on_device(a) -> int:
+    return int(bool(getattr(a, "is_cuda", False)))
+
+
+def lbm_halo_export(h, face: int, out) -> int:
+    """Writes the populations leaving through `face` into `out` (a numpy array or a host tensor:
+    synchronous; a CUDA tensor: asynchronous on the handle's stream)."""
+    return _ck(_lib.lbm_halo_export(h, face, _ptr(out), _on_device(out)), "lbm_halo_export")
+
+
+def lbm_halo_import(h, face: int, arr) -> int:
+    """Sets the halo of `face` from `arr` (host memory: synchronous; a CUDA tensor: asynchronous)."""
+    return _ck(_lib.lbm_halo_import(h, face, _ptr(arr), _on_device(arr)), "lbm_halo_import")
 
 
 def lbm_checkpoint_save(h, path) -> int:
@@ -869,3 +898,20 @@ class Lattice:
     def set_raw(self, raw):
         raw = np.ascontiguousarray(raw, dtype=np.uint8)
         lbm_set_raw(self.h, raw, raw.nbytes)
+
+    # slab halos (lbm_set_halo): messages as raw storage bytes
+    def set_halo(self, faces):
+        lbm_set_halo(self.h, int(faces))
+
+    def halo_export(self, face):
+        _, nbytes = lbm_halo_size(self.h)
+        out = np.empty(nbytes, dtype=np.uint8)
+        lbm_halo_export(self.h, int(face), out)
+        return out
+
+    def halo_import(self, face, msg):
+        msg = np.ascontiguousarray(msg, dtype=np.uint8)
+        _, nbytes = lbm_halo_size(self.h)
+        if msg.nbytes != nbytes:
+            raise ValueError(f"halo message of {msg.nbytes} bytes, expected {nbytes}")
+        lbm_halo_import(self.h, int(face), msg)

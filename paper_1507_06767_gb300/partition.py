@@ -8,10 +8,12 @@ face for D3Q19, 3 for D2Q9).  Block maxima stay local when the cuts fall on bloc
 top-fraction flags need the maxima of all blocks (an all-gather), and the conservation sums an
 all-reduce.
 
-Every run in this repository uses one GPU, so the library has no multi-GPU data path; this module
-holds the plan (which ranks own which planes, what crosses each cut) and the collective calls,
-written against torch.distributed so that the same code moves CPU tensors over gloo (the tests
-emulate the ranks on CPU) or CUDA tensors over NCCL.
+The library steps a slab through its halo faces (lbm_set_halo / lbm_halo_export /
+lbm_halo_import in include/lbm.h): a handle per slab whose cut faces read the neighbour's boundary
+plane from a halo instead of a wall.  This module holds the plan (which ranks own which planes,
+what crosses each cut) and the exchanges, written against torch.distributed so that the same code
+moves CPU tensors over gloo or CUDA tensors over NCCL: `exchange_lattice_halos` for library slabs
+(host-staged messages), `exchange_halos` for a slab stored with ghost planes in a tensor.
 """
 from __future__ import annotations
 
@@ -96,6 +98,55 @@ def exchange_halos(f_ext, q: int, slab: Slab, group=None):
         r.wait()
     for idx, plane, buf in recv:
         f_ext[idx, plane] = buf
+
+
+def halo_faces(slab: Slab) -> int:
+    """lbm_set_halo faces of a slab: the low face is cut where a rank lies below, the high face
+    where one lies above."""
+    from . import lbm as L
+
+    return (L.LBM_HALO_LO if slab.below is not None else 0) | \
+        (L.LBM_HALO_HI if slab.above is not None else 0)
+
+
+def exchange_lattice_halos(lat, slab: Slab, group=None):
+    """One halo exchange of a library slab (a `Lattice` whose cut faces have halos): the
+    populations leaving through each cut face go to the neighbour across it, and the neighbour's go
+    into the face's halo, through host memory as point-to-point messages of raw storage bytes
+    (tag 1 travels up, tag 2 down, as in `exchange_halos`).  A slab that is its own neighbour (one
+    rank, periodic slab axis) takes its own messages.  Call it between steps."""
+    import torch
+    import torch.distributed as dist
+
+    from . import lbm as L
+
+    me = dist.get_rank(group) if group is not None else dist.get_rank()
+    out = {}
+    if slab.above is not None:
+        out["up"] = lat.halo_export(L.LBM_HALO_HI)
+    if slab.below is not None:
+        out["down"] = lat.halo_export(L.LBM_HALO_LO)
+    reqs, recv = [], []
+    if slab.above is not None:
+        if slab.above == me:
+            recv.append((L.LBM_HALO_HI, out["down"]))
+        else:
+            reqs.append(dist.isend(torch.from_numpy(out["up"]), slab.above, group=group, tag=1))
+            buf = torch.empty(out["up"].size, dtype=torch.uint8)
+            reqs.append(dist.irecv(buf, slab.above, group=group, tag=2))
+            recv.append((L.LBM_HALO_HI, buf))
+    if slab.below is not None:
+        if slab.below == me:
+            recv.append((L.LBM_HALO_LO, out["up"]))
+        else:
+            reqs.append(dist.isend(torch.from_numpy(out["down"]), slab.below, group=group, tag=2))
+            buf = torch.empty(out["down"].size, dtype=torch.uint8)
+            reqs.append(dist.irecv(buf, slab.below, group=group, tag=1))
+            recv.append((L.LBM_HALO_LO, buf))
+    for r in reqs:
+        r.wait()
+    for face, buf in recv:
+        lat.halo_import(face, buf.numpy() if hasattr(buf, "numpy") else buf)
 
 
 def gather_maxima(local, group=None):
