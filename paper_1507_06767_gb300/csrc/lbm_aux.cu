@@ -801,6 +801,19 @@ cudaError_t flags_top(int rtype, const void *maxima, int n, int k, int8_t *out, 
         k_fill_i8<<<small_grid(n, 256), 256, 0, s>>>(out, n, k <= 0 ? int8_t(0) : int8_t(1));
         return cudaGetLastError();
     }
+    // keys in shared memory where they fit the default 48 KB of a launch, else the select that
+    // reads the maxima from global memory on every pass
+    const size_t key_bytes = rtype == 0 ? sizeof(unsigned long long) : sizeof(uint32_t);
+    if ((size_t)n * key_bytes <= 48 * 1024) {
+        const size_t smem = (size_t)n * key_bytes;
+        if (rtype == 0)
+            k_flags_top_keys<double, unsigned long long><<<1, TOP_THREADS, smem, s>>>(
+                static_cast<const double *>(maxima), n, k, out);
+        else
+            k_flags_top_keys<float, uint32_t><<<1, TOP_THREADS, smem, s>>>(
+                static_cast<const float *>(maxima), n, k, out);
+        return cudaGetLastError();
+    }
     if (rtype == 0)
         k_flags_top<double, unsigned long long><<<1, TOP_THREADS, 0, s>>>(
             static_cast<const double *>(maxima), n, k, out);
