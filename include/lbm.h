@@ -585,6 +585,17 @@ LBM_API int lbm_net_train_step(lbm_net *n, const float *x_dev, const float *targ
                                int h, int w, float lr, double *loss_host);
 LBM_API int lbm_net_log_targets(const double *kmax_dev, long long n, float offset, float floor_k,
                                 float *t_dev, void *stream);
+/*
+ * Residual form of the targets (the predictor reads the sensor now as a fourth input channel and
+ * predicts how it changes): lbm_net_log_residual writes t = log10(max(K_next, floor_k)) -
+ * log10(max(K_now, floor_k)) for n block maxima, lbm_net_to_maxima_residual K = max(K_now,
+ * floor_k) * 10^y; NaN in a maximum gives NaN (a refine flag downstream).  Device pointers,
+ * asynchronous on `stream`.
+ */
+LBM_API int lbm_net_log_residual(const double *kmax_next_dev, const double *kmax_now_dev,
+                                 long long n, float floor_k, float *t_dev, void *stream);
+LBM_API int lbm_net_to_maxima_residual(const float *y_dev, const double *kmax_now_dev, long long n,
+                                       float floor_k, double *kmax_dev, void *stream);
 LBM_API int lbm_net_to_maxima(const float *y_dev, long long n, float offset, double *kmax_dev,
                               void *stream);
 /*

@@ -291,6 +291,28 @@ __global__ void k_to_maxima(const float *__restrict__ y, long long n, float offs
     out[k] = exp10((double)y[k] + (double)offset);
 }
 
+// Residual form: targets are the change of log10 K over the horizon, predictions are added to
+// the log of the maximum now.  NaN in either maximum gives NaN.
+__global__ void k_log_residual(const double *__restrict__ next, const double *__restrict__ now,
+                               long long n, float floor_k, float *__restrict__ t) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double a = next[k], b = now[k], f = (double)floor_k;
+    if (a != a || b != b) {
+        t[k] = __int_as_float(0x7fc00000);
+        return;
+    }
+    t[k] = (float)(log10(a > f ? a : f) - log10(b > f ? b : f));
+}
+
+__global__ void k_to_maxima_residual(const float *__restrict__ y, const double *__restrict__ now,
+                                     long long n, float floor_k, double *__restrict__ out) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double b = now[k], f = (double)floor_k;
+    out[k] = (b != b) ? b : exp10((double)y[k] + log10(b > f ? b : f));
+}
+
 // Fraction of equal flags, counted by one CTA of 1024 threads (the flag arrays of a regrid hold a
 // few thousand blocks).
 constexpr int JUDGE_THREADS = 1024;
@@ -771,6 +793,30 @@ LBM_API int lbm_gather_rows(const void *src_dev, long long nrows, size_t row_byt
                                                        idx_dev, count, nrows,
                                                        static_cast<uint32_t *>(dst_dev), bad_dev);
     NETCK(cudaGetLastError(), "lbm_gather_rows");
+    return LBM_OK;
+}
+
+LBM_API int lbm_net_log_residual(const double *kmax_next_dev, const double *kmax_now_dev,
+                                 long long n, float floor_k, float *t_dev, void *stream) {
+    lbm::clear_error();
+    if (!kmax_next_dev || !kmax_now_dev || !t_dev || n < 0 || !(floor_k > 0.f))
+        return lbm::report_error(LBM_EINVAL, "lbm_net_log_residual: bad arguments");
+    if (n == 0) return LBM_OK;
+    k_log_residual<<<grid_for(n, NT), NT, 0, (cudaStream_t)stream>>>(kmax_next_dev, kmax_now_dev, n,
+                                                                      floor_k, t_dev);
+    NETCK(cudaGetLastError(), "lbm_net_log_residual");
+    return LBM_OK;
+}
+
+LBM_API int lbm_net_to_maxima_residual(const float *y_dev, const double *kmax_now_dev, long long n,
+                                       float floor_k, double *kmax_dev, void *stream) {
+    lbm::clear_error();
+    if (!y_dev || !kmax_now_dev || !kmax_dev || n < 0 || !(floor_k > 0.f))
+        return lbm::report_error(LBM_EINVAL, "lbm_net_to_maxima_residual: bad arguments");
+    if (n == 0) return LBM_OK;
+    k_to_maxima_residual<<<grid_for(n, NT), NT, 0, (cudaStream_t)stream>>>(y_dev, kmax_now_dev, n,
+                                                                            floor_k, kmax_dev);
+    NETCK(cudaGetLastError(), "lbm_net_to_maxima_residual");
     return LBM_OK;
 }
 

@@ -115,6 +115,8 @@ _SIGS = {
     "lbm_net_train_step": (_i, [_vp, _vp, _vp, _i, _i, _i, ctypes.c_float, _dp]),
     "lbm_net_log_targets": (_i, [_vp, _ll, ctypes.c_float, ctypes.c_float, _vp, _vp]),
     "lbm_net_to_maxima": (_i, [_vp, _ll, ctypes.c_float, _vp, _vp]),
+    "lbm_net_log_residual": (_i, [_vp, _vp, _ll, ctypes.c_float, _vp, _vp]),
+    "lbm_net_to_maxima_residual": (_i, [_vp, _vp, _ll, ctypes.c_float, _vp, _vp]),
     "lbm_net_get_buffer": (_i, [_vp, _i, _vp, _sz]),
     "lbm_flags_agreement": (_i, [_vp, _vp, _i, _vp, _vp]),
     "lbm_flags_judge_select": (_i, [_vp, _vp, _vp, _i, _d, _vp, _vp, _vp, _vp]),
@@ -450,6 +452,18 @@ def lbm_net_log_targets(kmax_dev, n: int, offset: float, floor_k: float, t_dev, 
 def lbm_net_to_maxima(y_dev, n: int, offset: float, kmax_dev, stream=None):
     return _ck(_lib.lbm_net_to_maxima(_ptr(y_dev), int(n), float(offset), _ptr(kmax_dev), stream),
                "lbm_net_to_maxima")
+
+
+def lbm_net_log_residual(kmax_next_dev, kmax_now_dev, n: int, floor_k: float, t_dev, stream=None):
+    return _ck(_lib.lbm_net_log_residual(_ptr(kmax_next_dev), _ptr(kmax_now_dev), int(n),
+                                         float(floor_k), _ptr(t_dev), stream),
+               "lbm_net_log_residual")
+
+
+def lbm_net_to_maxima_residual(y_dev, kmax_now_dev, n: int, floor_k: float, kmax_dev, stream=None):
+    return _ck(_lib.lbm_net_to_maxima_residual(_ptr(y_dev), _ptr(kmax_now_dev), int(n),
+                                               float(floor_k), _ptr(kmax_dev), stream),
+               "lbm_net_to_maxima_residual")
 
 
 def lbm_net_create(cin: int, hidden: int):

@@ -10,6 +10,11 @@ Here the network reads the block-averaged (rho, u_x, u_y) at time t and predicts
 block's sensor maximum at t + horizon; a regrid can then refine where the flow is going.  The
 exact sensor at t + horizon judges the predicted flags, and a regrid falls back to the exact flags
 whenever the agreement of the last judged prediction fell below a set fraction.
+
+Two forms: `with_sensor=False` reads the three block means only; `with_sensor=True` also reads the
+block's sensor maximum now, log10(K) - LOG_OFFSET as a fourth channel, and predicts the change of
+log10 K over the horizon (the residual form), so that "no change" -- reusing the current sensor --
+is the network's zero output.
 """
 from __future__ import annotations
 
@@ -22,9 +27,10 @@ LOG_OFFSET = -3.0   # targets are log10(K) - LOG_OFFSET
 FLOOR_K = 1e-12
 
 
-def normalisation(u_lid: float):
-    return np.array([1.0, 0.0, 0.0], np.float32), np.array([100.0, 1.0 / u_lid, 1.0 / u_lid],
-                                                           np.float32)
+def normalisation(u_lid: float, with_sensor: bool = False):
+    shift = [1.0, 0.0, 0.0] + ([0.0] if with_sensor else [])
+    scale = [100.0, 1.0 / u_lid, 1.0 / u_lid] + ([1.0] if with_sensor else [])
+    return np.array(shift, np.float32), np.array(scale, np.float32)
 
 
 def threshold(tau: float, u_lid: float, n: int) -> float:
@@ -33,11 +39,12 @@ def threshold(tau: float, u_lid: float, n: int) -> float:
 
 
 def cavity_trace(n: int, re: float, u_lid: float, block: int, warm: int, snapshots: int,
-                 horizon: int, dtype=None):
+                 horizon: int, dtype=None, with_sensor: bool = False):
     """D2Q9 cavity of n^2 cells at Reynolds number re from rest: after `warm` steps, snapshots
-    spaced `horizon` steps apart.  Returns (features [S+1, 3, nb, nb] float32, block maxima
+    spaced `horizon` steps apart.  Returns (features [S+1, C, nb, nb] float32, block maxima
     [S+1, nb*nb] float64, tau), all on the GPU; features[k] and maxima[k] belong to the same step
-    (the sensor of the last step)."""
+    (the sensor of the last step).  C = 3 (rho, u_x, u_y), or 4 with the log sensor maximum as the
+    last channel (with_sensor)."""
     import torch
 
     tau = 3.0 * u_lid * n / re + 0.5
@@ -46,26 +53,33 @@ def cavity_trace(n: int, re: float, u_lid: float, block: int, warm: int, snapsho
     L.lbm_set_sensor_every(lat.h, 0)  # the sensor on the last step of every lbm_step call
     nb = L.lbm_nblocks(lat.h, block)
     side = -(-n // block)
-    feats = torch.empty((snapshots + 1, 3, side, side), dtype=torch.float32, device="cuda")
+    feats = torch.empty((snapshots + 1, 4 if with_sensor else 3, side, side), dtype=torch.float32,
+                        device="cuda")
     kmax = torch.empty((snapshots + 1, nb), dtype=torch.float64, device="cuda")
     lat.step(warm)
     for k in range(snapshots + 1):
         if k:
             lat.step(horizon)
         L.lbm_sensor_dev(lat.h, block, kmax[k])
-        L.lbm_block_features(lat.h, block, feats[k])
+        L.lbm_block_features(lat.h, block, feats[k])  # channels 0..2
+        if with_sensor:
+            L.lbm_net_log_targets(kmax[k], nb, LOG_OFFSET, FLOOR_K, feats[k, 3])
     torch.cuda.synchronize()
     lat.close()
     return feats, kmax, tau
 
 
 def pairs(feats, kmax):
-    """(inputs at t, targets at t + horizon in log units) from a trace."""
+    """(inputs at t, targets at t + horizon in log units) from a trace; with the sensor channel
+    (4 input channels) the targets are the change of log10 K (residual form)."""
     import torch
 
     t = torch.empty((kmax.shape[0] - 1, 1) + tuple(feats.shape[2:]), dtype=torch.float32,
                     device="cuda")
-    L.lbm_net_log_targets(kmax[1:], t.numel(), LOG_OFFSET, FLOOR_K, t)
+    if feats.shape[1] == 4:
+        L.lbm_net_log_residual(kmax[1:].contiguous(), kmax[:-1].contiguous(), t.numel(), FLOOR_K, t)
+    else:
+        L.lbm_net_log_targets(kmax[1:], t.numel(), LOG_OFFSET, FLOOR_K, t)
     return feats[:-1].contiguous(), t
 
 
@@ -98,12 +112,17 @@ def train(net, X, T, epochs: int, batch: int, lr: float, seed: int):
     return losses
 
 
-def predicted_maxima(net, X):
+def predicted_maxima(net, X, kmax_now=None):
+    """Predicted block maxima at t + horizon; with the sensor channel (residual form) the maxima
+    now, kmax_now, are the base the predicted change applies to."""
     import torch
 
     y = net.forward(X)
     out = torch.empty(y.numel(), dtype=torch.float64, device="cuda")
-    L.lbm_net_to_maxima(y, y.numel(), LOG_OFFSET, out)
+    if X.shape[1] == 4:
+        L.lbm_net_to_maxima_residual(y, kmax_now.contiguous(), y.numel(), FLOOR_K, out)
+    else:
+        L.lbm_net_to_maxima(y, y.numel(), LOG_OFFSET, out)
     return out.view(X.shape[0], -1)
 
 
@@ -129,7 +148,7 @@ def judge(net, feats, kmax, T, fallback_below: float):
 
     S = kmax.shape[0] - 1
     nb = kmax.shape[1]
-    pred = predicted_maxima(net, feats[:-1].contiguous())
+    pred = predicted_maxima(net, feats[:-1].contiguous(), kmax[:-1])
     E = [flags(kmax[k].contiguous(), T) for k in range(S + 1)]
     P = [flags(pred[k].contiguous(), T) for k in range(S)]
     used = torch.empty(nb, dtype=torch.int8, device="cuda")
