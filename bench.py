@@ -397,15 +397,15 @@ def run_blocks(args, w, ws, rank, local):
                                "not counted)"},
         "e2e": {"value": round(updates / e2e_s / 1e6, 1), "unit": "MLUPS",
                 "h2d_bytes_per_step": int(leaf.size), "d2h_bytes_per_step": int(8 * bm.size)},
-        # per cycle: level l takes 2^l steps, each finer one a ghost fill before every step,
-        # and 2^l restrictions onto level l from the level below it
         "repeats": len(reps),
         # per cycle, graph form: level l takes 2^l steps, a finer one a ghost fill before every
-        # step, and 2^l restrictions onto level l unless the finer level's second sub-step does
-        # them (brick or tiled fused form); persistent form: one launch per cycle
+        # pair of its steps (one launch fills the ghosts of both), and 2^l restrictions onto
+        # level l unless the finer level's second sub-step does them (brick or tiled fused form);
+        # persistent form: one launch per cycle
         "gpu_launches": len(reps) * args.steps if persistent else len(reps) * args.steps * sum(
-            (1 << l) * (1 + (l > 0)) + ((1 << l) if l < w["lmax"] and info[l + 1][2] > 0
-                                        and mesh.schedule(l + 1)[2] == 0 else 0)
+            (1 << l) + ((1 << (l - 1)) if l > 0 else 0)
+            + ((1 << l) if l < w["lmax"] and info[l + 1][2] > 0
+               and mesh.schedule(l + 1)[2] == 0 else 0)
             for l in range(w["lmax"] + 1) if info[l][2] > 0),
         "clocks": clocks,
     }

@@ -24,8 +24,9 @@
 // Device layout of a level: one buffer of nslot blocks x 19 populations x (n + 2)^3 ghosted cells
 // (block-major, then population, then z, y, x), two buffers (ping-pong); only the ghost cells that
 // face a coarser neighbour are used.  The interpolation and restriction work is precomputed on the
-// host as task lists (flat element offsets and weights), so those kernels are plain gathers.  A cycle is captured once per level-0 buffer parity as a CUDA graph
-// and replayed.  The launch shape of each level's step kernel (threads per CTA and cells per
+// host as task lists (flat element offsets; for the interpolation, chunks of ghost cells with the
+// coarse cells their stencils touch, which a CTA stages in shared memory).  A cycle is captured
+// once per level-0 buffer parity as a CUDA graph and replayed.  The launch shape of each level's step kernel (threads per CTA and cells per
 // thread) is chosen by timing the candidates once when the mesh is built.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -33,6 +34,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <unordered_set>
 #include <vector>
 
 #include "../../include/lbm.h"
@@ -65,17 +67,32 @@ __host__ __device__ __forceinline__ int cell_index(int n, int x, int y, int z) {
     return ((z + 1) * (n + 2) + (y + 1)) * n + x;
 }
 
+// Brick forms of the fused step + restriction: the 19 sums in registers (BRICK_REG) or in a
+// shared-memory column per thread (BRICK_SMEM)
+constexpr int BRICK_REG = 0, BRICK_SMEM = 1;
+
 // Forms of a level's step kernel (also the values lbm_blocks_schedule reports):
 constexpr int FORM_FLAT = 0;    // k_step: one cell per thread, x-fastest
 constexpr int FORM_TILED = 1;   // k_step_tiled: bricks of whole rows walking z planes
 constexpr int FORM_SELECT = 2;  // k_step<XSEL>: flat, address-select gather for y/z-inner rows
 constexpr int FORM_PAIR = 3;    // k_step_pair: two cells per thread, packed FP32 arithmetic
 
-struct InterpTask {
-    int dst;
-    int src[8];
-    float w[8];
+// Coarse -> fine ghost fill, in chunks.  The ghost cells of a level that face a coarser level are
+// grouped (host side) into chunks of at most IC_TASKS cells whose trilinear stencils together touch
+// at most IC_WIN coarse cells, the chunk's window.  A CTA copies the window's 19 populations into
+// shared memory in one round of independent loads, then each thread fills one ghost cell from it:
+// one round of memory latency per chunk instead of one per population and thread.
+constexpr int IC_TASKS = 128;
+constexpr int IC_WIN = 320;
+struct InterpChunk {
+    int task0, ntask;  // ghost cells [task0, task0 + ntask) of the level's task list
+    int win0, nwin;    // coarse cells [win0, win0 + nwin) of the level's window list
 };
+// A ghost cell's task is two words, read with vector loads: its flat offset (population 0) in the
+// fine level's buffer, and its stencil's 8 coarse cells as 16-bit indices into the chunk's window
+// (cell k = x bit 0, y bit 1, z bit 2 of k; low half of a word first), whose bit 15 in the entries
+// of cells 0, 1, 2 says that axis 0, 1, 2 extrapolates (weights 5/4, -1/4 instead of 3/4, 1/4).
+constexpr unsigned IC_EXTRAP = 0x8000u;
 struct RestrictTask {
     int dst;   // coarse cell, population 0
     int fine;  // fine cell (2x, 2y, 2z), population 0
@@ -91,8 +108,11 @@ struct Level {
     float *buf[2] = {nullptr, nullptr};
     int cur = 0;
     int *nbr = nullptr;  // device: 27 entries per slot (slot, NB_GHOST or NB_WALL)
-    InterpTask *interps = nullptr;  // from level - 1
-    int ninterp = 0;
+    InterpChunk *ichunks = nullptr;  // ghost fill from level - 1: chunks, tasks, window cells
+    int *idst = nullptr;
+    uint4 *isrc = nullptr;
+    int *iwin = nullptr;
+    int ninterp = 0, nichunk = 0;
     RestrictTask *restricts = nullptr;  // level cells under level + 1
     int nrestrict = 0;
     float *kmax = nullptr;  // device: per-slot sensor max of the level's last step (int bits)
@@ -107,7 +127,7 @@ struct Level {
     // or the two-cell brick form (k_step_pair_restrict) with its own launch shape
     bool fuse_brick = false;
     int brick_threads = 256, brick_cpt = 1;
-    bool brick_smem = false;  // the brick sums in shared memory (k_step_pair_restrict_s)
+    int brick_mode = 0;  // BRICK_*
     int *cslot = nullptr;  // device: per slot, the slot of the same block one level coarser
 };
 
@@ -187,26 +207,56 @@ struct LdL2 {
     }
 };
 
-// coarse -> fine ghost: interpolate in space and time, rescale the non-equilibrium part.  BLEND:
-// theta > 0 (the coarse states before and after its step are mixed); without it only the state
-// before the coarse step is read.
-template <bool BLEND, class LD = LdPlain>
-__device__ __forceinline__ void interp_one(const InterpTask &it, float *fine, int Gf,
-                                           const float *cprev, const float *ccur, int Gc,
-                                           float theta, float scale) {
-    const LD ld;
+// Linear blend in time of a coarse population before (p) and after (c) its step, rounded the same
+// way on every path that fills ghosts.
+__device__ __forceinline__ float time_blend(float p, float c, float theta) {
+    return __fmaf_rn(theta, c, __fmul_rn(1.f - theta, p));
+}
+
+__device__ __forceinline__ void cp_async4(float *sdst, const float *gsrc) {
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(sdst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Ghost fills of a chunk: FILL_PREV the state before the coarse step (theta 0) into fine0;
+// FILL_BLEND the blend at theta into fine1; FILL_BOTH both, from one copy of the window (the graph
+// form fills the ghosts of both fine sub-steps once the coarse step is done).
+constexpr int FILL_PREV = 0, FILL_BLEND = 1, FILL_BOTH = 2;
+
+// The trilinear weights of a task from its extrapolation bits, as products in axis order.
+__device__ __forceinline__ void stencil(const uint4 sv, int src[8], float w[8]) {
+    const unsigned h[8] = {sv.x & 0xffffu, sv.x >> 16, sv.y & 0xffffu, sv.y >> 16,
+                           sv.z & 0xffffu, sv.z >> 16, sv.w & 0xffffu, sv.w >> 16};
+    float f0[3], f1[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const bool ex = h[a] & IC_EXTRAP;
+        f0[a] = ex ? 1.25f : 0.75f;
+        f1[a] = ex ? -0.25f : 0.25f;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        src[k] = (int)(h[k] & (IC_EXTRAP - 1u));
+        float wt = 1.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) wt *= ((k >> a) & 1) ? f1[a] : f0[a];
+        w[k] = wt;
+    }
+}
+
+// Interpolate one ghost cell from a staged window (sw: population i at sw[i * IC_WIN + cell]),
+// rescale the non-equilibrium part and store its 19 populations at fine + dst.
+__device__ __forceinline__ void fill_ghost(const float *sw, const int src[8], const float w[8],
+                                           float *fine, int dst, int Gf, float scale) {
     float acc[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         float a = 0.f;
 #pragma unroll
-        for (int s = 0; s < 8; ++s) {
-            const int o = it.src[s] + i * Gc;
-            if (BLEND)
-                a += it.w[s] * ((1.f - theta) * ld(cprev + o) + theta * ld(ccur + o));
-            else
-                a += it.w[s] * ld(cprev + o);
-        }
+        for (int s = 0; s < 8; ++s) a = __fmaf_rn(w[s], sw[i * IC_WIN + src[s]], a);
         acc[i] = a;
     }
     float rho, ux, uy, uz;
@@ -214,16 +264,97 @@ __device__ __forceinline__ void interp_one(const InterpTask &it, float *fine, in
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const float fe = feq19(i, rho, ux, uy, uz);
-        fine[it.dst + i * Gf] = fe + scale * (acc[i] - fe);
+        fine[dst + (size_t)i * Gf] = fe + scale * (acc[i] - fe);
     }
 }
 
-template <bool BLEND>
-__global__ void k_interp(const InterpTask *t, int n, float *fine, int Gf, const float *cprev,
-                         const float *ccur, int Gc, float theta, float scale) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    interp_one<BLEND>(t[k], fine, Gf, cprev, ccur, Gc, theta, scale);
+// One chunk of the coarse -> fine ghost fill: interpolate in space (the chunk's window staged in
+// shared memory) and linearly in time, rescale the non-equilibrium part.  FILL (above) says which
+// states are read and written.  ASYNC: the window is copied with cp.async (buffers no CTA of the
+// launch writes; sw2 receives the second state); otherwise by loads through L2 (the persistent
+// cycle, whose other CTAs wrote the coarse level earlier in the launch; FILL_PREV or FILL_BLEND
+// only).  NTH threads, all of which must call this; with FILL_BOTH a thread fills one of the two
+// states of a ghost cell.
+template <int FILL, bool ASYNC, int NTH>
+__device__ __forceinline__ void interp_chunk(const InterpChunk &c, const int *__restrict__ idst,
+                                             const uint4 *__restrict__ isrc,
+                                             const int *__restrict__ win, float *fine0,
+                                             float *fine1, int Gf, const float *cprev,
+                                             const float *ccur, int Gc, float theta, float scale,
+                                             float *sw, float *sw2) {
+    static_assert(ASYNC || FILL != FILL_BOTH, "the L2 path fills one state");
+    constexpr int R = (IC_WIN + NTH - 1) / NTH;
+    const int tid = threadIdx.x, nw = c.nwin;
+    int off[R];  // the window cells this thread copies, loaded before any copy is issued
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int j = tid + r * NTH;
+        off[r] = j < nw ? win[c.win0 + j] : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int j = tid + r * NTH;
+        if (j >= nw) break;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const size_t e = (size_t)off[r] + (size_t)i * Gc;
+            if (ASYNC) {
+                cp_async4(sw + i * IC_WIN + j, cprev + e);
+                if (FILL != FILL_PREV) cp_async4(sw2 + i * IC_WIN + j, ccur + e);
+            } else {
+                float v = __ldcg(cprev + e);
+                if (FILL == FILL_BLEND) v = time_blend(v, __ldcg(ccur + e), theta);
+                sw[i * IC_WIN + j] = v;
+            }
+        }
+    }
+    if (ASYNC) {
+        cp_async_wait_all();  // this thread's copies; it blends the same elements it copied
+        if (FILL != FILL_PREV)
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int j = tid + r * NTH;
+                if (j >= nw) break;
+#pragma unroll
+                for (int i = 0; i < Q; ++i)
+                    sw2[i * IC_WIN + j] =
+                        time_blend(sw[i * IC_WIN + j], sw2[i * IC_WIN + j], theta);
+            }
+    }
+    __syncthreads();
+    constexpr int NF = FILL == FILL_BOTH ? 2 : 1;
+    for (int e = tid; e < NF * c.ntask; e += NTH) {
+        const bool second = NF == 2 && e >= c.ntask;
+        const int k = second ? e - c.ntask : e;
+        int src[8];
+        float w[8];
+        stencil(isrc[c.task0 + k], src, w);
+        const int dst = idst[c.task0 + k];
+        if (FILL == FILL_PREV)
+            fill_ghost(sw, src, w, fine0, dst, Gf, scale);
+        else if (FILL == FILL_BLEND)
+            fill_ghost(ASYNC ? sw2 : sw, src, w, fine1, dst, Gf, scale);
+        else
+            fill_ghost(second ? sw2 : sw, src, w, second ? fine1 : fine0, dst, Gf, scale);
+    }
+}
+
+// one CTA per chunk, a thread per ghost cell and state; dynamic shared memory: the window, twice
+// unless FILL_PREV
+template <int FILL>
+__global__ void __launch_bounds__(FILL == FILL_BOTH ? 2 * IC_TASKS : IC_TASKS)
+    k_interp(const InterpChunk *__restrict__ ch, const int *__restrict__ idst,
+             const uint4 *__restrict__ isrc, const int *__restrict__ win, float *fine0,
+             float *fine1, int Gf, const float *cprev, const float *ccur, int Gc, float theta,
+             float scale) {
+    extern __shared__ float sw[];
+    interp_chunk<FILL, true, FILL == FILL_BOTH ? 2 * IC_TASKS : IC_TASKS>(
+        ch[blockIdx.x], idst, isrc, win, fine0, fine1, Gf, cprev, ccur, Gc, theta, scale, sw,
+        sw + Q * IC_WIN);
+}
+constexpr int interp_threads(int fill) { return fill == FILL_BOTH ? 2 * IC_TASKS : IC_TASKS; }
+constexpr size_t interp_smem(int fill) {
+    return (fill == FILL_PREV ? 1 : 2) * sizeof(float) * Q * IC_WIN;
 }
 
 // level cells under the finer level: average of 8 fine cells, non-equilibrium part rescaled
@@ -746,8 +877,11 @@ struct PPhase {
     const float *aux;    // ghost fill: the coarse state after its step
     const int *nbr;      // step / brick: neighbour table
     float *kmax;         // step / brick / zero: per-slot sensor maxima
-    const void *items;   // ghost fill / restriction: task list
+    const void *items;   // ghost fill: chunks; restriction: task list
     int nitems;
+    const int *idst;     // ghost fill: the chunks' tasks and window cells
+    const uint4 *isrc;
+    const int *iwin;
     int G2, P2, plane2;  // ghost fill: coarse G; restriction: finer G, row pitch, plane size
     float theta, scale;
     StepArgs a;          // the level's step arguments (a.G: the level's G)
@@ -808,20 +942,20 @@ __device__ __forceinline__ void pk_brick(const PPhase &P, int slot, int chunk, c
     block_max_flush(km, P.kmax, slot, threadIdx.x & 31);
 }
 
-__device__ __forceinline__ void pk_run(const PPhase &P, int k, int *snb) {
+__device__ __forceinline__ void pk_run(const PPhase &P, int k, int *snb, float *swin) {
     const int tid = threadIdx.x;
     if (P.kind == PH_ZERO) {
         for (int i = tid; i < P.nslot; i += PK_THREADS) P.kmax[i] = 0.f;
         return;
     }
-    if (P.kind == PH_INTERP0 || P.kind == PH_INTERPB) {
-        const int j = k * PK_THREADS + tid;
-        if (j >= P.nitems) return;
-        const InterpTask &it = static_cast<const InterpTask *>(P.items)[j];
+    if (P.kind == PH_INTERP0 || P.kind == PH_INTERPB) {  // one chunk per task
+        const InterpChunk c = static_cast<const InterpChunk *>(P.items)[k];
         if (P.kind == PH_INTERPB)
-            interp_one<true, LdL2>(it, P.out, P.a.G, P.in, P.aux, P.G2, P.theta, P.scale);
+            interp_chunk<FILL_BLEND, false, PK_THREADS>(c, P.idst, P.isrc, P.iwin, nullptr, P.out, P.a.G,
+                                            P.in, P.aux, P.G2, P.theta, P.scale, swin, nullptr);
         else
-            interp_one<false, LdL2>(it, P.out, P.a.G, P.in, P.aux, P.G2, P.theta, P.scale);
+            interp_chunk<FILL_PREV, false, PK_THREADS>(c, P.idst, P.isrc, P.iwin, P.out, nullptr, P.a.G, P.in,
+                                           P.aux, P.G2, P.theta, P.scale, swin, nullptr);
         return;
     }
     if (P.kind == PH_RESTRICT) {
@@ -860,6 +994,7 @@ __global__ void __launch_bounds__(PK_THREADS, 2)
             int *ctr, int *err, unsigned long long wait_ns, int hold) {
     __shared__ int s_task, s_phase;
     __shared__ int snb[27];
+    __shared__ float swin[Q * IC_WIN];  // a ghost-fill chunk's window
     int *next = ctr, *abort_flag = ctr + 1, *done = ctr + 2;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -895,7 +1030,7 @@ __global__ void __launch_bounds__(PK_THREADS, 2)
         __syncthreads();
         const int p = s_phase;
         if (p < 0) break;
-        pk_run(ph[p], s_task - ph[p].task0, snb);
+        pk_run(ph[p], s_task - ph[p].task0, snb, swin);
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();  // this task's stores before its count
@@ -992,10 +1127,62 @@ int cell_offset(const Mesh &m, int l, const int g[3], int *slot_out) {
     return s * Q * L.G + gidx(L, loc[0], loc[1], loc[2]);
 }
 
+// One ghost cell's trilinear stencil in the coarser level, before chunking: flat offsets
+// (population 0) of the 8 coarse cells.  face orders the ghost cells of a block by the face they lie
+// on (x low / high, then y, then z), then z, y, x within it, so that consecutive cells of a chunk
+// are neighbours on one face and share most of their coarse cells.
+struct GhostStencil {
+    int dst, src[8];
+    int extrap;     // bit a: axis a extrapolates (weights 5/4, -1/4)
+    long long key;  // slot, face, z, y, x
+};
+
+// Group consecutive stencils into chunks of at most IC_TASKS ghost cells touching at most IC_WIN
+// coarse cells; the window of a chunk lists those cells by ascending offset (rows of a coarse block
+// are contiguous, so the copy of a window coalesces).
+void chunk_stencils(const std::vector<GhostStencil> &gs, std::vector<InterpChunk> &ch,
+                    std::vector<int> &dst, std::vector<uint4> &src, std::vector<int> &win) {
+    size_t k = 0;
+    std::vector<int> cells;
+    std::unordered_set<int> inwin;
+    while (k < gs.size()) {
+        inwin.clear();
+        size_t e = k;
+        while (e < gs.size() && e - k < (size_t)IC_TASKS) {
+            int fresh[8], nf = 0;
+            for (int s = 0; s < 8; ++s) {
+                const int o = gs[e].src[s];
+                if (inwin.count(o) || std::find(fresh, fresh + nf, o) != fresh + nf) continue;
+                fresh[nf++] = o;
+            }
+            if (inwin.size() + nf > (size_t)IC_WIN) break;  // this cell starts the next chunk
+            inwin.insert(fresh, fresh + nf);
+            ++e;
+        }
+        cells.assign(inwin.begin(), inwin.end());
+        std::sort(cells.begin(), cells.end());
+        InterpChunk c = {(int)dst.size(), (int)(e - k), (int)win.size(), (int)cells.size()};
+        for (size_t t = k; t < e; ++t) {
+            unsigned h[8];
+            for (int s = 0; s < 8; ++s)
+                h[s] = (unsigned)(std::lower_bound(cells.begin(), cells.end(), gs[t].src[s]) -
+                                  cells.begin());
+            for (int a = 0; a < 3; ++a)
+                if (gs[t].extrap & (1 << a)) h[a] |= IC_EXTRAP;
+            dst.push_back(gs[t].dst);
+            src.push_back(make_uint4(h[0] | h[1] << 16, h[2] | h[3] << 16, h[4] | h[5] << 16,
+                                     h[6] | h[7] << 16));
+        }
+        win.insert(win.end(), cells.begin(), cells.end());
+        ch.push_back(c);
+        k = e;
+    }
+}
+
 int build_tasks(Mesh &m, int l) {
     Level &L = m.lv[l];
     std::vector<int> nbr;
-    std::vector<InterpTask> interps;
+    std::vector<GhostStencil> stencils;
     const int n = L.n;
     for (int b = 0; b < m.nblk; ++b) {
         const int s = L.slot[b];
@@ -1022,8 +1209,7 @@ int build_tasks(Mesh &m, int l) {
                     // ghost centre (g + 1/2) h_l lies at g/2 + 1/4 coarse cells: coarse cell
                     // g >> 1, offset -1/4 (g even) or +1/4 (g odd)
                     const Level &C = m.lv[l - 1];
-                    int c0[3], c1[3];
-                    float w0[3], w1[3];
+                    int c0[3], c1[3], extrap = 0;
                     for (int a = 0; a < 3; ++a) {
                         const int c = g[a] >> 1;
                         const int dir = (g[a] & 1) ? 1 : -1;
@@ -1032,33 +1218,31 @@ int build_tasks(Mesh &m, int l) {
                         if (nbr >= 0) {
                             c0[a] = c;
                             c1[a] = nbr;
-                            w0[a] = 0.75f;
-                            w1[a] = 0.25f;
                         } else {
                             c0[a] = c;
                             c1[a] = wrap(c - dir, C.cells[a], per);
-                            w0[a] = 1.25f;
-                            w1[a] = -0.25f;
+                            extrap |= 1 << a;
                         }
                     }
-                    InterpTask it;
+                    GhostStencil it;
                     it.dst = dst;
+                    it.extrap = extrap;
+                    {
+                        const int face = x < 0 ? 0 : x >= n ? 1 : y < 0 ? 2 : y >= n ? 3
+                                                                  : z < 0 ? 4 : 5;
+                        it.key = ((((long long)s * 6 + face) * (n + 2) + (z + 1)) * (n + 2) +
+                                  (y + 1)) * (n + 2) + (x + 1);
+                    }
                     for (int k = 0; k < 8; ++k) {
                         int cc[3];
-                        float wt = 1.f;
-                        for (int a = 0; a < 3; ++a) {
-                            const int bit = (k >> a) & 1;
-                            cc[a] = bit ? c1[a] : c0[a];
-                            wt *= bit ? w1[a] : w0[a];
-                        }
+                        for (int a = 0; a < 3; ++a) cc[a] = ((k >> a) & 1) ? c1[a] : c0[a];
                         int cs;
                         it.src[k] = cell_offset(m, l - 1, cc, &cs);
                         if (cs < 0)
                             return report_error(LBM_EINVAL,
                                                 "interpolation stencil outside the coarser level");
-                        it.w[k] = wt;
                     }
-                    interps.push_back(it);
+                    stencils.push_back(it);
                 }
     }
     // neighbour table: for each slot and each of the 27 offsets, the slot of the neighbouring
@@ -1090,9 +1274,19 @@ int build_tasks(Mesh &m, int l) {
         st = upload(&L.cslot, cs);
         if (st != LBM_OK) return st;
     }
-    st = upload(&L.interps, interps);
+    std::stable_sort(stencils.begin(), stencils.end(),
+                     [](const GhostStencil &a, const GhostStencil &b) { return a.key < b.key; });
+    std::vector<InterpChunk> chunks;
+    std::vector<int> idst, win;
+    std::vector<uint4> isrc;
+    chunk_stencils(stencils, chunks, idst, isrc, win);
+    st = upload(&L.ichunks, chunks);
+    if (st == LBM_OK) st = upload(&L.idst, idst);
+    if (st == LBM_OK) st = upload(&L.isrc, isrc);
+    if (st == LBM_OK) st = upload(&L.iwin, win);
     if (st != LBM_OK) return st;
-    L.ninterp = (int)interps.size();
+    L.ninterp = (int)idst.size();
+    L.nichunk = (int)chunks.size();
     if (l < m.lmax) {
         const Level &F = m.lv[l + 1];
         std::vector<RestrictTask> rs;
@@ -1215,7 +1409,7 @@ cudaError_t launch_step_restrict(const Mesh &m, int l, int zc, cudaStream_t s, i
 }
 
 template <int NT>
-cudaError_t launch_brick(const Mesh &m, int l, int threads, int cpt, bool smem, cudaStream_t s,
+cudaError_t launch_brick(const Mesh &m, int l, int threads, int cpt, int mode, cudaStream_t s,
                          int src) {
     const Level &L = m.lv[l], &C = m.lv[l - 1];
     RestrictArgs r;
@@ -1225,7 +1419,7 @@ cudaError_t launch_brick(const Mesh &m, int l, int threads, int cpt, bool smem, 
     r.scale = (float)(2.0 * (C.tau - 1.0) / (L.tau - 1.0));
     const int nbrick = (NT / 2) * (NT / 2) * (NT / 2);
     const dim3 grid(L.nslot, (nbrick + threads * cpt - 1) / (threads * cpt));
-    if (smem)
+    if (mode == BRICK_SMEM)
         k_step_pair_restrict_s<NT><<<grid, threads, sizeof(float) * Q * threads, s>>>(
             L.buf[src], L.buf[src ^ 1], L.nbr, step_args(m, l), cpt, L.kmax, r);
     else
@@ -1235,13 +1429,13 @@ cudaError_t launch_brick(const Mesh &m, int l, int threads, int cpt, bool smem, 
 }
 
 // The brick form of the fused step + restriction of level l onto l - 1 (n = 8, 16, 32, 64).
-cudaError_t launch_step_restrict_brick(const Mesh &m, int l, int threads, int cpt, bool smem,
+cudaError_t launch_step_restrict_brick(const Mesh &m, int l, int threads, int cpt, int mode,
                                        cudaStream_t s, int src) {
     switch (m.lv[l].n) {
-        case 8: return launch_brick<8>(m, l, threads, cpt, smem, s, src);
-        case 16: return launch_brick<16>(m, l, threads, cpt, smem, s, src);
-        case 32: return launch_brick<32>(m, l, threads, cpt, smem, s, src);
-        case 64: return launch_brick<64>(m, l, threads, cpt, smem, s, src);
+        case 8: return launch_brick<8>(m, l, threads, cpt, mode, s, src);
+        case 16: return launch_brick<16>(m, l, threads, cpt, mode, s, src);
+        case 32: return launch_brick<32>(m, l, threads, cpt, mode, s, src);
+        case 64: return launch_brick<64>(m, l, threads, cpt, mode, s, src);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1267,38 +1461,36 @@ int brick_depth(int n) {
 
 inline unsigned blocks_for(int n, int t) { return (unsigned)((n + t - 1) / t); }
 
-// One level-l step with its ghost fill at time fraction theta, then the two sub-steps of the finer
-// level and the restriction onto this one.  Level l's work goes to stream ss[l].  Dependencies
-// between levels are events: a finer level's first sub-step (theta 0) reads the coarser state
-// from before the coarser step, so its ghost fill and step run beside that step; its second
-// sub-step (theta 1/2) waits for the coarser step; the restriction onto level l waits for the
-// finer level's second sub-step and the restriction onto the finer level.  The coarser level's
-// next step waits for that restriction, which covers every read of the buffer it overwrites.
+// One level-l step (the first of a pair, theta 0, also fills the ghosts of both), then the two
+// sub-steps of the finer level and the restriction onto this one.  Level l's work goes to stream
+// ss[l].  Dependencies between levels are events: a finer level's ghost fill waits for the
+// coarser step (its first sub-step's ghosts come from the coarser state before that step, its
+// second's from the blend of before and after); the restriction onto level l waits for the finer
+// level's second sub-step and the restriction onto the finer level.  The coarser level's next
+// step waits for that restriction, which covers every read of the buffer it overwrites.
 int advance(Mesh &m, int l, float theta, cudaStream_t *ss) {
     Level &L = m.lv[l];
     if (L.nslot == 0) return LBM_OK;  // no block reaches this level (nor a finer one)
     cudaStream_t s = ss[l];
     if (l > 0) {
-        MLCK(cudaStreamWaitEvent(s, theta > 0.f ? m.ev_post[l - 1] : m.ev_pre[l - 1], 0),
-             "cudaStreamWaitEvent");
-        if (L.ninterp) {
+        // the ghosts of both sub-steps are filled once the coarser step is done, from one copy of
+        // the coarse window: theta 0 into this buffer and theta 1/2 into the other, which the
+        // first sub-step writes only inside the blocks
+        MLCK(cudaStreamWaitEvent(s, m.ev_post[l - 1], 0), "cudaStreamWaitEvent");
+        if (L.ninterp && theta == 0.f) {
             const Level &C = m.lv[l - 1];
             const float scale = (float)((L.tau - 1.0) / (2.0 * (C.tau - 1.0)));
-            if (theta > 0.f)
-                k_interp<true><<<blocks_for(L.ninterp, 128), 128, 0, s>>>(
-                    L.interps, L.ninterp, L.buf[L.cur], L.G, C.buf[C.cur ^ 1], C.buf[C.cur], C.G,
-                    theta, scale);
-            else  // the coarser step (enqueued, maybe still running) leaves this buffer unchanged
-                k_interp<false><<<blocks_for(L.ninterp, 128), 128, 0, s>>>(
-                    L.interps, L.ninterp, L.buf[L.cur], L.G, C.buf[C.cur ^ 1], C.buf[C.cur], C.G,
-                    theta, scale);
+            k_interp<FILL_BOTH><<<L.nichunk, interp_threads(FILL_BOTH), interp_smem(FILL_BOTH),
+                                   s>>>(
+                L.ichunks, L.idst, L.isrc, L.iwin, L.buf[L.cur], L.buf[L.cur ^ 1], L.G,
+                C.buf[C.cur ^ 1], C.buf[C.cur], C.G, 0.5f, scale);
         }
     }
     MLCK(cudaGetLastError(), "ghost fill");
     MLCK(cudaMemsetAsync(L.kmax, 0, sizeof(float) * L.nslot, s), "memset(kmax)");
     MLCK(cudaEventRecord(m.ev_pre[l], s), "cudaEventRecord");
     if (L.fuse_brick && theta > 0.f)  // the finest level's second sub-step restricts as it steps
-        MLCK(launch_step_restrict_brick(m, l, L.brick_threads, L.brick_cpt, L.brick_smem, s, L.cur),
+        MLCK(launch_step_restrict_brick(m, l, L.brick_threads, L.brick_cpt, L.brick_mode, s, L.cur),
              "level step + restriction");
     else if (L.fuse && theta > 0.f)
         MLCK(launch_step_restrict(m, l, L.fuse_zc, s, L.cur), "level step + restriction");
@@ -1433,13 +1625,13 @@ int autotune(Mesh &m, int l, cudaStream_t s) {
         float bestb = 1e30f;
         const int nbrick = (L.n / 2) * (L.n / 2) * (L.n / 2);
         const int shapes[][2] = {{128, 1}, {128, 2}, {256, 1}, {256, 2}};
-        for (int sm = 0; sm < 2; ++sm)
+        for (int sm = BRICK_REG; sm <= BRICK_SMEM; ++sm)
             for (const auto &c : shapes) {
                 if (c[0] * c[1] > 2 * nbrick && !(c[0] == 128 && c[1] == 1)) continue;
                 float ms = 0.f;
                 st = time_it(
                     [&]() {
-                        return launch_step_restrict_brick(m, l, c[0], c[1], sm == 1, s, L.cur);
+                        return launch_step_restrict_brick(m, l, c[0], c[1], sm, s, L.cur);
                     },
                     &ms);
                 if (st != LBM_OK) return st;
@@ -1447,7 +1639,7 @@ int autotune(Mesh &m, int l, cudaStream_t s) {
                     bestb = ms;
                     L.brick_threads = c[0];
                     L.brick_cpt = c[1];
-                    L.brick_smem = sm == 1;
+                    L.brick_mode = sm;
                 }
             }
         L.fuse_brick = m.fusion == 3 || bestb < sep;
@@ -1535,9 +1727,12 @@ void plan_advance(Mesh &m, PlanBuilder &b, int l, float theta) {
             PPhase p = {};
             p.kind = theta > 0.f ? PH_INTERPB : PH_INTERP0;
             p.level = l;
-            p.items = L.interps;
-            p.nitems = L.ninterp;
-            p.ntask = (L.ninterp + PK_THREADS - 1) / PK_THREADS;
+            p.items = L.ichunks;
+            p.nitems = L.nichunk;
+            p.idst = L.idst;
+            p.isrc = L.isrc;
+            p.iwin = L.iwin;
+            p.ntask = L.nichunk;
             p.out = L.buf[L.cur];
             p.in = C.buf[C.cur ^ 1];
             p.aux = C.buf[C.cur];
@@ -1766,7 +1961,10 @@ void destroy(Mesh *m) {
         cudaFree(L.buf[1]);
         cudaFree(L.nbr);
         cudaFree(L.cslot);
-        cudaFree(L.interps);
+        cudaFree(L.ichunks);
+        cudaFree(L.idst);
+        cudaFree(L.isrc);
+        cudaFree(L.iwin);
         cudaFree(L.restricts);
         cudaFree(L.kmax);
     }
