@@ -847,8 +847,9 @@ __global__ void __launch_bounds__(256, 4)
 // ------------------------------------------------------------------ persistent cycle kernel
 // One launch runs a whole cycle: the work of the graph form (ghost fills, level steps, restrictions,
 // the zeroing of each level's sensor maxima) as a list of phases in the order the graph enqueues
-// them, each split into tasks of 256 threads.  Persistent CTAs claim tasks in index order with an
-// atomic counter; a task first waits until every phase it depends on has completed all its tasks
+// them, each split into tasks (a ghost-fill chunk, or several units of 256 threads of a step,
+// brick or restriction).  Persistent CTAs claim tasks in index order with an atomic counter; a
+// task first waits until every phase it depends on has completed all its tasks
 // (per-phase counters, read with acquire), then runs, then counts itself complete (fence, atomic
 // add).  The dependencies are those of the graph form: each level's phases in order (its stream)
 // and the cross-level waits on a coarser level's state before or after its step and on the
@@ -864,10 +865,13 @@ constexpr int PH_STEP = 3;      // level step
 constexpr int PH_BRICK = 4;     // finest level's second sub-step with the restriction fused
 constexpr int PH_RESTRICT = 5;  // restriction onto the level from the next finer one
 constexpr int PK_THREADS = 256;
+constexpr int PK_TASKS_PER_CTA = 16, PK_MAX_PER = 32;
 constexpr unsigned long long PK_WAIT_NS = 1000000000ull;
 
 struct PPhase {
     int kind, level, ntask, task0, dep0, ndep;
+    int nunit, per;      // step / brick / restriction: work units (chunks of 256 threads) and
+                         // units per task, so that a task outlasts the claim and the waits
     int chunks;          // step / brick: tasks per slot
     int nslot;           // zero: slots
     const float *in;     // step / brick: source buffer; ghost fill: coarse state before its step;
@@ -893,6 +897,12 @@ struct PPhase {
 __device__ __forceinline__ int ld_acquire_gpu(const int *p) {
     int v;
     asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_relaxed_gpu(const int *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
 
@@ -959,30 +969,41 @@ __device__ __forceinline__ void pk_run(const PPhase &P, int k, int *snb, float *
         return;
     }
     if (P.kind == PH_RESTRICT) {
-        const int j = k * PK_THREADS + tid;
-        if (j >= P.nitems) return;
-        restrict_one<LdL2>(static_cast<const RestrictTask *>(P.items)[j], P.out, P.a.G, P.in, P.P2,
-                           P.plane2, P.G2, P.scale);
+        for (int u = 0; u < P.per; ++u) {
+            const int j = (k * P.per + u) * PK_THREADS + tid;
+            if (j >= P.nitems) break;
+            restrict_one<LdL2>(static_cast<const RestrictTask *>(P.items)[j], P.out, P.a.G, P.in,
+                               P.P2, P.plane2, P.G2, P.scale);
+        }
         return;
     }
-    // step or brick: the block's neighbour table in shared memory
-    const int slot = k / P.chunks, chunk = k % P.chunks;
-    if (tid < 27) snb[tid] = P.nbr[27 * slot + tid];
-    __syncthreads();
-    if (P.kind == PH_STEP) {
-        switch (P.a.n) {
-            case 8: pk_step<8>(P, slot, chunk, snb); break;
-            case 16: pk_step<16>(P, slot, chunk, snb); break;
-            case 32: pk_step<32>(P, slot, chunk, snb); break;
-            case 64: pk_step<64>(P, slot, chunk, snb); break;
-            default: pk_step<0>(P, slot, chunk, snb); break;
+    // step or brick: units in slot-major order, the block's neighbour table in shared memory
+    int last = -1;
+    for (int u = 0; u < P.per; ++u) {
+        const int kk = k * P.per + u;
+        if (kk >= P.nunit) break;
+        const int slot = kk / P.chunks, chunk = kk - slot * P.chunks;
+        if (slot != last) {
+            if (last >= 0) __syncthreads();  // every thread is done with the previous table
+            if (tid < 27) snb[tid] = P.nbr[27 * slot + tid];
+            __syncthreads();
+            last = slot;
         }
-    } else {
-        switch (P.a.n) {
-            case 8: pk_brick<8>(P, slot, chunk, snb); break;
-            case 16: pk_brick<16>(P, slot, chunk, snb); break;
-            case 32: pk_brick<32>(P, slot, chunk, snb); break;
-            default: pk_brick<64>(P, slot, chunk, snb); break;
+        if (P.kind == PH_STEP) {
+            switch (P.a.n) {
+                case 8: pk_step<8>(P, slot, chunk, snb); break;
+                case 16: pk_step<16>(P, slot, chunk, snb); break;
+                case 32: pk_step<32>(P, slot, chunk, snb); break;
+                case 64: pk_step<64>(P, slot, chunk, snb); break;
+                default: pk_step<0>(P, slot, chunk, snb); break;
+            }
+        } else {
+            switch (P.a.n) {
+                case 8: pk_brick<8>(P, slot, chunk, snb); break;
+                case 16: pk_brick<16>(P, slot, chunk, snb); break;
+                case 32: pk_brick<32>(P, slot, chunk, snb); break;
+                default: pk_brick<64>(P, slot, chunk, snb); break;
+            }
         }
     }
 }
@@ -996,13 +1017,17 @@ __global__ void __launch_bounds__(PK_THREADS, 2)
     __shared__ int snb[27];
     __shared__ float swin[Q * IC_WIN];  // a ghost-fill chunk's window
     int *next = ctr, *abort_flag = ctr + 1, *done = ctr + 2;
+    // thread 0: the phase of the last task (tasks of a CTA come in increasing order, so the phase
+    // search resumes there)
+    int plast = 0;
     for (;;) {
         if (threadIdx.x == 0) {
             const int t = atomicAdd(next, 1);
             int p = -1;
-            if (t < ntask && !ld_acquire_gpu(abort_flag)) {
-                p = 0;
+            if (t < ntask && !ld_relaxed_gpu(abort_flag)) {
+                p = plast;
                 while (p + 1 < nph && ph[p + 1].task0 <= t) ++p;
+                plast = p;
                 const int dep0 = ph[p].dep0, ndep = ph[p].ndep;
                 for (int k = 0; k < ndep && p >= 0; ++k) {
                     const int d = deps[dep0 + k];
@@ -1712,6 +1737,14 @@ struct PlanBuilder {
     }
 };
 
+// Units of 256 threads per task of a step, brick or restriction phase: claiming a task and waiting
+// for its dependencies cost a few microseconds of one thread's latency, which a single unit's work
+// does not cover, so a task takes several; about PK_TASKS_PER_CTA tasks per CTA of the launch keep
+// the phase's tail short.
+int units_per_task(const Mesh &m, int nunit) {
+    return std::max(1, std::min(PK_MAX_PER, nunit / (PK_TASKS_PER_CTA * std::max(m.pk_grid, 1))));
+}
+
 int step_chunks(int n) {
     return has_tiled(n) ? (n * n * n / 2 + PK_THREADS - 1) / PK_THREADS
                         : (n * n * n + PK_THREADS - 1) / PK_THREADS;
@@ -1770,7 +1803,9 @@ void plan_advance(Mesh &m, PlanBuilder &b, int l, float theta) {
         st.kind = PH_STEP;
         st.chunks = step_chunks(L.n);
     }
-    st.ntask = L.nslot * st.chunks;
+    st.nunit = L.nslot * st.chunks;
+    st.per = units_per_task(m, st.nunit);
+    st.ntask = (st.nunit + st.per - 1) / st.per;
     b.add(l, st);
     L.cur ^= 1;
     b.post[l] = b.record(l);
@@ -1785,7 +1820,9 @@ void plan_advance(Mesh &m, PlanBuilder &b, int l, float theta) {
             r.level = l;
             r.items = L.restricts;
             r.nitems = L.nrestrict;
-            r.ntask = (L.nrestrict + PK_THREADS - 1) / PK_THREADS;
+            r.nunit = (L.nrestrict + PK_THREADS - 1) / PK_THREADS;
+            r.per = units_per_task(m, r.nunit);
+            r.ntask = (r.nunit + r.per - 1) / r.per;
             r.out = L.buf[L.cur];
             r.in = F.buf[F.cur];
             r.a = step_args(m, l);
@@ -1837,18 +1874,18 @@ int build_plan(Mesh &m, Mesh::Plan *out) {
 // The plan of the current level-0 parity and the launch width, made before any stream capture
 // (they allocate and copy).
 int ensure_plan(Mesh &m) {
-    Mesh::Plan &P = m.plan[m.lv[0].cur];
-    if (!P.phases) {
-        const int st = build_plan(m, &P);
-        if (st != LBM_OK) return st;
-    }
-    if (!m.pk_grid) {
+    if (!m.pk_grid) {  // the launch width, which also sizes the plan's tasks
         int per_sm = 0, dev = 0, nsm = 0;
         MLCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cycle, PK_THREADS, 0),
              "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
         MLCK(cudaGetDevice(&dev), "cudaGetDevice");
         MLCK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "sm count");
         m.pk_grid = std::max(1, per_sm * nsm);
+    }
+    Mesh::Plan &P = m.plan[m.lv[0].cur];
+    if (!P.phases) {
+        const int st = build_plan(m, &P);
+        if (st != LBM_OK) return st;
     }
     return LBM_OK;
 }
