@@ -143,6 +143,37 @@ def recorded_traffic(workload, w, variant="auto"):
     return float(m_tr.group(1))
 
 
+# sources of the multi-level cycle's kernels (steps, ghost fills, restrictions)
+CYCLE_SOURCES = ("lbm_multilevel.cu", "lbm_step_pair.cuh", "lbm_step.cuh", "lbm_traits.cuh")
+
+
+def cycle_source_hash():
+    h = hashlib.sha256()
+    for fn in CYCLE_SOURCES:
+        with open(os.path.join(ROOT, "paper_1507_06767_gb300", "csrc", fn), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_cycle_traffic(workload, w, step_form="auto", fusion="auto", schedule="auto",
+                           persistent=False):
+    """DRAM bytes per level-0 cycle of the multi-level mesh (all kernels of the cycle's graph)
+    from the committed ncu summary, if it was taken on the current sources, on the full mesh, with
+    the automatic schedule and the graph form of the cycle; else None."""
+    if (persistent or w["n"] != WORKLOADS[workload]["n"]
+            or (step_form, fusion, schedule) != ("auto", "auto", "auto")):
+        return None
+    path = os.path.join(ROOT, "profiles", f"cycle_dram_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m_src = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    m_tr = re.search(r"dram_bytes_per_cycle:\s*([0-9.eE+]+)", txt)
+    if not m_src or not m_tr or m_src.group(1) != cycle_source_hash():
+        return None
+    return float(m_tr.group(1))
+
+
 def nvtx_push(name):
     """Open an NVTX range on the host thread (a no-op where NVTX is not available)."""
     try:
@@ -392,7 +423,11 @@ def run_blocks(args, w, ws, rank, local):
                               "device time), median"),
                    "l2": "level buffers > 129 MB L2, no flush"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                     "frac": round(achieved / peak, 4),
+                     "traffic": recorded_cycle_traffic(args.workload, w, args.step_form,
+                                                       args.fusion, args.schedule, persistent),
+                     "traffic_unit": "DRAM bytes per cycle, all kernels (ncu)",
+                     "algorithmic_bytes_per_cycle": 152 * updates, "peak_kind": peak_kind,
                      "kernel": "whole cycle (152 B per cell update; ghost and restriction work "
                                "not counted)"},
         "e2e": {"value": round(updates / e2e_s / 1e6, 1), "unit": "MLUPS",

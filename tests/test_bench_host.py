@@ -68,6 +68,24 @@ def test_recorded_traffic_only_for_the_profiled_kernel_and_size():
     assert bench.recorded_traffic("d2q9_1024_learned", bench.WORKLOADS["d2q9_1024_learned"]) is None
 
 
+def test_recorded_cycle_traffic_only_for_the_profiled_schedule():
+    wl = "d3q19_blocks_512_3level"
+    w = dict(bench.WORKLOADS[wl])
+    assert bench.recorded_cycle_traffic(wl, dict(w, n=256)) is None
+    assert bench.recorded_cycle_traffic(wl, w, persistent=True) is None
+    assert bench.recorded_cycle_traffic(wl, w, fusion="separate") is None
+    assert bench.recorded_cycle_traffic(wl, w, step_form="pair") is None
+    got = bench.recorded_cycle_traffic(wl, w)
+    path = os.path.join(bench.ROOT, "profiles", f"cycle_dram_{wl}.md")
+    txt = open(path).read() if os.path.exists(path) else ""
+    if f"kernel_source_sha256_16: {bench.cycle_source_hash()}" in txt:
+        # at least the algorithmic 152 B per cell update of the 57.7 M updates of a cycle, less
+        # what stays in L2 between launches, and not more than twice that
+        assert got is not None and 0.8 * 152 * 57671680 < got < 2.0 * 152 * 57671680
+    else:
+        assert got is None
+
+
 class _Proc:
     def terminate(self):
         pass
