@@ -400,8 +400,9 @@ LBM_API int lbm_step_noalloc(int lattice, int dtype, int nx, int ny, int nz, dou
  * at most, and edge / 2^lmax must be >= 2.  Acoustic scaling: dx / dt is the same on every level,
  * so level l takes 2^l steps per level-0 step ("cycle") and tau_l = 3 nu / 2^(lmax - l) + 1/2 with
  * nu = (tau - 1/2) / 3 of the finest level (Eq. nu_omega); every level needs tau_l != 1.
- * Coupling: one-cell ghost layers, filled by copies inside a level and, at the edge of a level, by
- * trilinear space / linear time interpolation of the next coarser level with the non-equilibrium
+ * Coupling: one-cell ghost layers; inside a level a ghost is the neighbouring block's cell (read
+ * in place), at the edge of a level it is filled by trilinear space / linear time interpolation of
+ * the next coarser level with the non-equilibrium
  * part rescaled by (tau_f - 1) / (2 (tau_c - 1)); after the two sub-steps of a finer level the
  * coarser cells under it take the average of their 8 fine cells, the non-equilibrium part rescaled
  * by 2 (tau_c - 1) / (tau_f - 1).  The sensor K of every cell is evaluated in each level step; the
