@@ -451,8 +451,10 @@ LBM_API int lbm_blocks_set_fusion(lbm_t *h, int mode);
  * persistent CTAs claim the cycle's tasks -- ghost fills, level steps, restrictions -- in the order
  * the graph enqueues them and wait, device-side and bounded, for the phases each task depends on
  * (replayed from a captured graph of that launch when graphs are on).  LBM_SCHEDULE_AUTO (default)
- * times both when the mesh is built and keeps the faster; the persistent form is not available
- * with LBM_FUSION_FUSED.  A wait that runs out (limit: lbm_debug_set_wait_limit, default one
+ * times both when the mesh is built and keeps the faster (the persistent kernel in two forms: with
+ * the finest level's brick phases, or lean, with plain steps and restriction phases at a smaller
+ * register budget; LBM_SCHEDULE_PERSISTENT keeps the faster of the two); the persistent form is
+ * not available with LBM_FUSION_FUSED.  A wait that runs out (limit: lbm_debug_set_wait_limit, default one
  * second; lbm_debug_hold_copies makes every wait run out) stops the launch; the next call that
  * synchronises (lbm_blocks_step with block maxima, lbm_blocks_get) returns LBM_ETIMEOUT and the
  * mesh must be rebuilt.  Applies from the next mesh build: an existing mesh is discarded.

@@ -158,6 +158,9 @@ struct Mesh {
     int pctr_len = 0;
     int pk_grid = 0;
     bool persistent = false;
+    // lean persistent form: no brick phase (the finest level's second sub-step is a plain step and
+    // the restriction a phase of its own), so that the cycle kernel fits 3 CTAs per SM instead of 2
+    bool pk_lean = false;
     int schedule = 0;  // LBM_SCHEDULE_* of the build
     // error word and wait settings the persistent graphs were captured with
     int *err = nullptr;
@@ -952,6 +955,7 @@ __device__ __forceinline__ void pk_brick(const PPhase &P, int slot, int chunk, c
     block_max_flush(km, P.kmax, slot, threadIdx.x & 31);
 }
 
+template <bool BRICK>
 __device__ __forceinline__ void pk_run(const PPhase &P, int k, int *snb, float *swin) {
     const int tid = threadIdx.x;
     if (P.kind == PH_ZERO) {
@@ -997,7 +1001,7 @@ __device__ __forceinline__ void pk_run(const PPhase &P, int k, int *snb, float *
                 case 64: pk_step<64>(P, slot, chunk, snb); break;
                 default: pk_step<0>(P, slot, chunk, snb); break;
             }
-        } else {
+        } else if constexpr (BRICK) {  // a lean plan has no brick phase
             switch (P.a.n) {
                 case 8: pk_brick<8>(P, slot, chunk, snb); break;
                 case 16: pk_brick<16>(P, slot, chunk, snb); break;
@@ -1010,7 +1014,8 @@ __device__ __forceinline__ void pk_run(const PPhase &P, int k, int *snb, float *
 
 // ctr: [0] next task, [1] abort flag, [2 + p] completed tasks of phase p (zeroed before a launch).
 // hold != 0 (a test hook) makes every dependency unreachable, so the first wait runs out.
-__global__ void __launch_bounds__(PK_THREADS, 2)
+template <bool BRICK>
+__global__ void __launch_bounds__(PK_THREADS, BRICK ? 2 : 3)
     k_cycle(const PPhase *__restrict__ ph, int nph, const int *__restrict__ deps, int ntask,
             int *ctr, int *err, unsigned long long wait_ns, int hold) {
     __shared__ int s_task, s_phase;
@@ -1055,7 +1060,7 @@ __global__ void __launch_bounds__(PK_THREADS, 2)
         __syncthreads();
         const int p = s_phase;
         if (p < 0) break;
-        pk_run(ph[p], s_task - ph[p].task0, snb, swin);
+        pk_run<BRICK>(ph[p], s_task - ph[p].task0, snb, swin);
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();  // this task's stores before its count
@@ -1791,7 +1796,7 @@ void plan_advance(Mesh &m, PlanBuilder &b, int l, float theta) {
     st.nbr = L.nbr;
     st.kmax = L.kmax;
     st.a = step_args(m, l);
-    if (L.fuse_brick && theta > 0.f) {
+    if (L.fuse_brick && theta > 0.f && !m.pk_lean) {
         const Level &C = m.lv[l - 1];
         st.kind = PH_BRICK;
         st.chunks = ((L.n / 2) * (L.n / 2) * (L.n / 2) + PK_THREADS - 1) / PK_THREADS;
@@ -1814,7 +1819,7 @@ void plan_advance(Mesh &m, PlanBuilder &b, int l, float theta) {
         plan_advance(m, b, l + 1, 0.5f);
         const Level &F = m.lv[l + 1];
         if (F.nslot > 0) b.wait(l, b.done[l + 1]);
-        if (L.nrestrict && !F.fuse && !F.fuse_brick) {
+        if (L.nrestrict && !F.fuse && (!F.fuse_brick || m.pk_lean)) {
             PPhase r = {};
             r.kind = PH_RESTRICT;
             r.level = l;
@@ -1876,8 +1881,14 @@ int build_plan(Mesh &m, Mesh::Plan *out) {
 int ensure_plan(Mesh &m) {
     if (!m.pk_grid) {  // the launch width, which also sizes the plan's tasks
         int per_sm = 0, dev = 0, nsm = 0;
-        MLCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cycle, PK_THREADS, 0),
-             "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+        if (m.pk_lean)
+            MLCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cycle<false>, PK_THREADS,
+                                                               0),
+                 "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+        else
+            MLCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cycle<true>, PK_THREADS,
+                                                               0),
+                 "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
         MLCK(cudaGetDevice(&dev), "cudaGetDevice");
         MLCK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "sm count");
         m.pk_grid = std::max(1, per_sm * nsm);
@@ -1896,9 +1907,15 @@ int persistent_cycle(Mesh &m, cudaStream_t s) {
     if (st != LBM_OK) return st;
     Mesh::Plan &P = m.plan[m.lv[0].cur];
     MLCK(cudaMemsetAsync(m.pctr, 0, sizeof(int) * (2 + P.nph), s), "memset(plan counters)");
-    k_cycle<<<std::min(m.pk_grid, std::max(P.ntask, 1)), PK_THREADS, 0, s>>>(
-        static_cast<const PPhase *>(P.phases), P.nph, P.deps, P.ntask, m.pctr, m.err,
-        m.wait_ns ? m.wait_ns : PK_WAIT_NS, m.hold);
+    const unsigned grid = (unsigned)std::min(m.pk_grid, std::max(P.ntask, 1));
+    if (m.pk_lean)
+        k_cycle<false><<<grid, PK_THREADS, 0, s>>>(static_cast<const PPhase *>(P.phases), P.nph,
+                                                   P.deps, P.ntask, m.pctr, m.err,
+                                                   m.wait_ns ? m.wait_ns : PK_WAIT_NS, m.hold);
+    else
+        k_cycle<true><<<grid, PK_THREADS, 0, s>>>(static_cast<const PPhase *>(P.phases), P.nph,
+                                                  P.deps, P.ntask, m.pctr, m.err,
+                                                  m.wait_ns ? m.wait_ns : PK_WAIT_NS, m.hold);
     MLCK(cudaGetLastError(), "persistent cycle");
     // the launch covers a whole cycle: level 0 flips once, the finer levels an even number of times
     m.lv[0].cur ^= 1;
@@ -1938,28 +1955,44 @@ void drop_cycle_graphs(Mesh &m) {
     }
 }
 
-// Time a few cycles in each form (graph of separate launches, persistent kernel) and keep the
-// faster, unless the schedule setting forces one; the persistent form needs a restriction that is
-// a separate kernel or the brick form (not the tiled fused form).
+// Switch the persistent form between the cycle kernel with brick phases and the lean one; the
+// plans and the launch width belong to the form, so they are made again when it changes.
+void set_persistent_form(Mesh &m, bool lean) {
+    if (m.pk_lean == lean) return;
+    m.pk_lean = lean;
+    m.pk_grid = 0;
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(m.plan[k].phases);
+        cudaFree(m.plan[k].deps);
+        m.plan[k] = Mesh::Plan();
+    }
+    drop_cycle_graphs(m);
+}
+
+// Time a few cycles in each form (graph of separate launches; persistent kernel with the brick
+// phases of the finest level, or lean: plain steps and restriction phases at 3 CTAs per SM) and
+// keep the fastest, unless the schedule setting forces the graph (LBM_SCHEDULE_GRAPH) or the
+// persistent kernel (LBM_SCHEDULE_PERSISTENT: the faster of its two forms).  The persistent form
+// needs a restriction that is a separate kernel or the brick form (not the tiled fused form).
 int choose_schedule(Mesh &m, cudaStream_t s) {
-    bool can = true;
-    for (int l = 0; l <= m.lmax; ++l)
+    bool can = true, brick = false;
+    for (int l = 0; l <= m.lmax; ++l) {
         if (m.lv[l].fuse) can = false;
+        if (m.lv[l].fuse_brick) brick = true;
+    }
     if (m.schedule == 1 || !can) {
         m.persistent = false;
-        return LBM_OK;
-    }
-    if (m.schedule == 2) {
-        m.persistent = true;
         return LBM_OK;
     }
     cudaEvent_t e0, e1;
     MLCK(cudaEventCreate(&e0), "cudaEventCreate");
     MLCK(cudaEventCreate(&e1), "cudaEventCreate");
-    float ms[2] = {0.f, 0.f};
+    float ms[3] = {1e30f, 1e30f, 1e30f};  // graph, persistent with bricks, lean persistent
     int st = LBM_OK;
-    for (int form = 0; form < 2 && st == LBM_OK; ++form) {
-        m.persistent = form == 1;
+    for (int form = m.schedule == 2 ? 1 : 0; form < 3 && st == LBM_OK; ++form) {
+        if (form == 2 && !brick) continue;  // without brick phases both plans are the same
+        m.persistent = form >= 1;
+        if (form >= 1) set_persistent_form(m, form == 2);
         drop_cycle_graphs(m);
         for (int k = 0; k < 5 && st == LBM_OK; ++k) {
             if (k == 2) MLCK(cudaEventRecord(e0, s), "cudaEventRecord");
@@ -1973,7 +2006,9 @@ int choose_schedule(Mesh &m, cudaStream_t s) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != LBM_OK) return st;
-    m.persistent = ms[1] < ms[0];
+    const int best = (int)(std::min_element(ms, ms + 3) - ms);
+    m.persistent = best >= 1;
+    if (m.persistent) set_persistent_form(m, best == 2);
     drop_cycle_graphs(m);
     return LBM_OK;
 }
