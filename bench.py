@@ -1073,7 +1073,8 @@ def main():
     ap.add_argument("--fusion", default="auto", choices=["auto", "separate", "fused", "brick"],
                     help="multi-level workload: the finest level's restriction as a separate "
                          "kernel or fused into its second sub-step (default: the library's)")
-    ap.add_argument("--schedule", default="auto", choices=["auto", "graph", "persistent"],
+    ap.add_argument("--schedule", default="auto",
+                    choices=["auto", "graph", "persistent", "persistent_brick", "persistent_lean"],
                     help="multi-level workload: a cycle as a graph of separate launches or one "
                          "persistent launch (default: timed at mesh build)")
     ap.add_argument("--step-form", default="auto",

@@ -453,8 +453,8 @@ LBM_API int lbm_blocks_set_fusion(lbm_t *h, int mode);
  * (replayed from a captured graph of that launch when graphs are on).  LBM_SCHEDULE_AUTO (default)
  * times both when the mesh is built and keeps the faster (the persistent kernel in two forms: with
  * the finest level's brick phases, or lean, with plain steps and restriction phases at a smaller
- * register budget; LBM_SCHEDULE_PERSISTENT keeps the faster of the two); the persistent form is
- * not available with LBM_FUSION_FUSED.  A wait that runs out (limit: lbm_debug_set_wait_limit, default one
+ * register budget; LBM_SCHEDULE_PERSISTENT keeps the faster of the two, _PERSISTENT_BRICK and
+ * _PERSISTENT_LEAN force one); the persistent form is not available with LBM_FUSION_FUSED.  A wait that runs out (limit: lbm_debug_set_wait_limit, default one
  * second; lbm_debug_hold_copies makes every wait run out) stops the launch; the next call that
  * synchronises (lbm_blocks_step with block maxima, lbm_blocks_get) returns LBM_ETIMEOUT and the
  * mesh must be rebuilt.  Applies from the next mesh build: an existing mesh is discarded.
@@ -463,6 +463,8 @@ LBM_API int lbm_blocks_set_fusion(lbm_t *h, int mode);
 #define LBM_SCHEDULE_AUTO 0
 #define LBM_SCHEDULE_GRAPH 1
 #define LBM_SCHEDULE_PERSISTENT 2
+#define LBM_SCHEDULE_PERSISTENT_BRICK 3 /* the persistent kernel with brick phases only */
+#define LBM_SCHEDULE_PERSISTENT_LEAN 4  /* the lean persistent kernel only */
 LBM_API int lbm_blocks_set_schedule(lbm_t *h, int mode);
 LBM_API int lbm_blocks_cycle_form(lbm_t *h);
 /* Form of every level's step kernel: LBM_STEP_FORM_AUTO (default) times the candidate forms and

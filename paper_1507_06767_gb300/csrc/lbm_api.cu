@@ -1197,8 +1197,9 @@ LBM_API int lbm_blocks_step(lbm_t *h, const lbm_level_batch *batch) {
 
 LBM_API int lbm_blocks_set_schedule(lbm_t *h, int mode) {
     CHECK_H(h);
-    if (mode < LBM_SCHEDULE_AUTO || mode > LBM_SCHEDULE_PERSISTENT)
-        return fail(LBM_EINVAL, "schedule must be LBM_SCHEDULE_AUTO, _GRAPH or _PERSISTENT");
+    if (mode < LBM_SCHEDULE_AUTO || mode > LBM_SCHEDULE_PERSISTENT_LEAN)
+        return fail(LBM_EINVAL, "schedule must be LBM_SCHEDULE_AUTO, _GRAPH, _PERSISTENT, "
+                                "_PERSISTENT_BRICK or _PERSISTENT_LEAN");
     if (h->mesh) {  // applies to the next build
         CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
         lbm::ml::destroy(h->mesh);

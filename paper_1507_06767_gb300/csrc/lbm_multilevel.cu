@@ -1971,8 +1971,9 @@ void set_persistent_form(Mesh &m, bool lean) {
 
 // Time a few cycles in each form (graph of separate launches; persistent kernel with the brick
 // phases of the finest level, or lean: plain steps and restriction phases at 3 CTAs per SM) and
-// keep the fastest, unless the schedule setting forces the graph (LBM_SCHEDULE_GRAPH) or the
-// persistent kernel (LBM_SCHEDULE_PERSISTENT: the faster of its two forms).  The persistent form
+// keep the fastest, unless the schedule setting forces the graph (LBM_SCHEDULE_GRAPH), the
+// persistent kernel (LBM_SCHEDULE_PERSISTENT: the faster of its two forms) or one of its forms
+// (LBM_SCHEDULE_PERSISTENT_BRICK, _LEAN).  The persistent form
 // needs a restriction that is a separate kernel or the brick form (not the tiled fused form).
 int choose_schedule(Mesh &m, cudaStream_t s) {
     bool can = true, brick = false;
@@ -1980,8 +1981,13 @@ int choose_schedule(Mesh &m, cudaStream_t s) {
         if (m.lv[l].fuse) can = false;
         if (m.lv[l].fuse_brick) brick = true;
     }
-    if (m.schedule == 1 || !can) {
+    if (m.schedule == LBM_SCHEDULE_GRAPH || !can) {
         m.persistent = false;
+        return LBM_OK;
+    }
+    if (m.schedule == LBM_SCHEDULE_PERSISTENT_BRICK || m.schedule == LBM_SCHEDULE_PERSISTENT_LEAN) {
+        m.persistent = true;
+        set_persistent_form(m, m.schedule == LBM_SCHEDULE_PERSISTENT_LEAN);
         return LBM_OK;
     }
     cudaEvent_t e0, e1;
@@ -1989,7 +1995,8 @@ int choose_schedule(Mesh &m, cudaStream_t s) {
     MLCK(cudaEventCreate(&e1), "cudaEventCreate");
     float ms[3] = {1e30f, 1e30f, 1e30f};  // graph, persistent with bricks, lean persistent
     int st = LBM_OK;
-    for (int form = m.schedule == 2 ? 1 : 0; form < 3 && st == LBM_OK; ++form) {
+    for (int form = m.schedule == LBM_SCHEDULE_PERSISTENT ? 1 : 0; form < 3 && st == LBM_OK;
+         ++form) {
         if (form == 2 && !brick) continue;  // without brick phases both plans are the same
         m.persistent = form >= 1;
         if (form >= 1) set_persistent_form(m, form == 2);

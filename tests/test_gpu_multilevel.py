@@ -162,6 +162,10 @@ def test_block_mesh_argument_errors(L):
             with pytest.raises(L.LbmError) as ei:
                 L.lbm_blocks_set_step_form(h, form)
             assert ei.value.status == L.LBM_EINVAL
+        for mode in (-1, L.LBM_SCHEDULE_PERSISTENT_LEAN + 1):
+            with pytest.raises(L.LbmError) as ei:
+                L.lbm_blocks_set_schedule(h, mode)
+            assert ei.value.status == L.LBM_EINVAL
     finally:
         L.lbm_destroy(h)
 
@@ -243,16 +247,20 @@ def test_brick_restriction_three_levels(L, edge):
 
 
 @pytest.mark.parametrize("graphs", [True, False])
-@pytest.mark.parametrize("fusion", ["SEPARATE", "BRICK"])
-def test_persistent_cycle_matches_oracle(L, graphs, fusion):
-    """One persistent launch per cycle (LBM_SCHEDULE_PERSISTENT): the cycle's ghost fills, level
-    steps and restrictions as tasks of one kernel, ordered by device-side counters.  The 3-level
+@pytest.mark.parametrize("fusion,schedule", [("SEPARATE", "PERSISTENT"),
+                                             ("BRICK", "PERSISTENT_BRICK"),
+                                             ("BRICK", "PERSISTENT_LEAN")])
+def test_persistent_cycle_matches_oracle(L, graphs, fusion, schedule):
+    """One persistent launch per cycle: the cycle's ghost fills, level steps and restrictions as
+    tasks of one kernel, ordered by device-side counters; the kernel with the finest level's brick
+    phases and the lean one (plain steps and restriction phases), each forced.  The 3-level
     lid-driven mesh (finest blocks of 16 cells, so the brick form applies) against the FP64 oracle
     after 10 cycles, replayed from a captured graph and launched directly."""
     leaf = three_level_leaf()
     edge, lmax, tau, cycles = 16, 2, 0.6, 10
     g = L.BlockMesh(leaf, edge, lmax, tau, lid=(0.1, 0.02), graphs=graphs,
-                    fusion=getattr(L, "LBM_FUSION_" + fusion), schedule=L.LBM_SCHEDULE_PERSISTENT)
+                    fusion=getattr(L, "LBM_FUSION_" + fusion),
+                    schedule=getattr(L, "LBM_SCHEDULE_" + schedule))
     assert g.cycle_form() == L.LBM_SCHEDULE_PERSISTENT
     o = O.MultiLevel(leaf, edge, lmax, tau, lid=(0.1, 0.0, 0.02))
     bm = g.step(cycles, block_max=True)
