@@ -868,13 +868,15 @@ constexpr int PH_STEP = 3;      // level step
 constexpr int PH_BRICK = 4;     // finest level's second sub-step with the restriction fused
 constexpr int PH_RESTRICT = 5;  // restriction onto the level from the next finer one
 constexpr int PK_THREADS = 256;
-constexpr int PK_TASKS_PER_CTA = 16, PK_MAX_PER = 32;
+constexpr int PK_TASKS_PER_CTA = 8, PK_MAX_PER = 32;
 constexpr unsigned long long PK_WAIT_NS = 1000000000ull;
 
 struct PPhase {
     int kind, level, ntask, task0, dep0, ndep;
-    int nunit, per;      // step / brick / restriction: work units (chunks of 256 threads) and
-                         // units per task, so that a task outlasts the claim and the waits
+    int nunit, per, nbig;  // step / brick / restriction: work units (chunks of 256 threads); the
+                           // first nbig tasks take per units each (a task outlasts the claim and
+                           // the waits), the rest one unit each (a short tail before the next
+                           // phase may start)
     int chunks;          // step / brick: tasks per slot
     int nslot;           // zero: slots
     const float *in;     // step / brick: source buffer; ghost fill: coarse state before its step;
@@ -955,6 +957,18 @@ __device__ __forceinline__ void pk_brick(const PPhase &P, int slot, int chunk, c
     block_max_flush(km, P.kmax, slot, threadIdx.x & 31);
 }
 
+// the units [u0, u1) of task k of a step, brick or restriction phase
+__device__ __forceinline__ void task_units(const PPhase &P, int k, int &u0, int &u1) {
+    if (k < P.nbig) {
+        u0 = k * P.per;
+        u1 = u0 + P.per;
+    } else {
+        u0 = P.nbig * P.per + (k - P.nbig);
+        u1 = u0 + 1;
+    }
+    u1 = min(u1, P.nunit);
+}
+
 template <bool BRICK>
 __device__ __forceinline__ void pk_run(const PPhase &P, int k, int *snb, float *swin) {
     const int tid = threadIdx.x;
@@ -973,8 +987,10 @@ __device__ __forceinline__ void pk_run(const PPhase &P, int k, int *snb, float *
         return;
     }
     if (P.kind == PH_RESTRICT) {
-        for (int u = 0; u < P.per; ++u) {
-            const int j = (k * P.per + u) * PK_THREADS + tid;
+        int u0, u1;
+        task_units(P, k, u0, u1);
+        for (int kk = u0; kk < u1; ++kk) {
+            const int j = kk * PK_THREADS + tid;
             if (j >= P.nitems) break;
             restrict_one<LdL2>(static_cast<const RestrictTask *>(P.items)[j], P.out, P.a.G, P.in,
                                P.P2, P.plane2, P.G2, P.scale);
@@ -983,9 +999,9 @@ __device__ __forceinline__ void pk_run(const PPhase &P, int k, int *snb, float *
     }
     // step or brick: units in slot-major order, the block's neighbour table in shared memory
     int last = -1;
-    for (int u = 0; u < P.per; ++u) {
-        const int kk = k * P.per + u;
-        if (kk >= P.nunit) break;
+    int u0, u1;
+    task_units(P, k, u0, u1);
+    for (int kk = u0; kk < u1; ++kk) {
         const int slot = kk / P.chunks, chunk = kk - slot * P.chunks;
         if (slot != last) {
             if (last >= 0) __syncthreads();  // every thread is done with the previous table
@@ -1750,6 +1766,15 @@ int units_per_task(const Mesh &m, int nunit) {
     return std::max(1, std::min(PK_MAX_PER, nunit / (PK_TASKS_PER_CTA * std::max(m.pk_grid, 1))));
 }
 
+// Tasks of a phase of nunit units: about three quarters of the units in tasks of
+// units_per_task units, the rest in one-unit tasks, which CTAs finishing early pick up while the
+// last large tasks run, so that the phase ends soon after its last large task.
+void split_tasks(const Mesh &m, PPhase &p) {
+    p.per = units_per_task(m, p.nunit);
+    p.nbig = p.per > 1 ? (3 * p.nunit / 4) / p.per : 0;
+    p.ntask = p.nbig + (p.nunit - p.nbig * p.per);
+}
+
 int step_chunks(int n) {
     return has_tiled(n) ? (n * n * n / 2 + PK_THREADS - 1) / PK_THREADS
                         : (n * n * n + PK_THREADS - 1) / PK_THREADS;
@@ -1809,8 +1834,7 @@ void plan_advance(Mesh &m, PlanBuilder &b, int l, float theta) {
         st.chunks = step_chunks(L.n);
     }
     st.nunit = L.nslot * st.chunks;
-    st.per = units_per_task(m, st.nunit);
-    st.ntask = (st.nunit + st.per - 1) / st.per;
+    split_tasks(m, st);
     b.add(l, st);
     L.cur ^= 1;
     b.post[l] = b.record(l);
@@ -1826,8 +1850,7 @@ void plan_advance(Mesh &m, PlanBuilder &b, int l, float theta) {
             r.items = L.restricts;
             r.nitems = L.nrestrict;
             r.nunit = (L.nrestrict + PK_THREADS - 1) / PK_THREADS;
-            r.per = units_per_task(m, r.nunit);
-            r.ntask = (r.nunit + r.per - 1) / r.per;
+            split_tasks(m, r);
             r.out = L.buf[L.cur];
             r.in = F.buf[F.cur];
             r.a = step_args(m, l);
