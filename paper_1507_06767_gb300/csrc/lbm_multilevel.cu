@@ -877,7 +877,7 @@ struct PPhase {
                            // first nbig tasks take per units each (a task outlasts the claim and
                            // the waits), the rest one unit each (a short tail before the next
                            // phase may start)
-    int chunks;          // step / brick: tasks per slot
+    int chunks;          // step / brick: units per slot
     int nslot;           // zero: slots
     const float *in;     // step / brick: source buffer; ghost fill: coarse state before its step;
                          // restriction: the finer level's state
